@@ -1,0 +1,183 @@
+"""Seeded synthetic initial conditions shaped like the paper's test problems.
+
+Every generator draws from `numpy.random.default_rng(seed)` in a fixed order,
+so a (config, seed) pair always yields the same points and states.  The
+recipes (lattice sizes, jitter, spectra, amplitudes) are the workloads the
+hydro update is exercised on:
+
+* `sod_2d`: the two-dimensional shock tube (Sec. 8.2 test family) as a
+  periodic box [0,2]x[0,1] holding two mirrored Riemann problems.
+* `turbulent_3d`: a jittered 3D lattice with a random-phase Gaussian velocity
+  field, P(k) ~ k^-4 on 2 <= |k| <= 8 (units of 2 pi / L), at a given rms Mach
+  number.
+* `lognormal_3d`: log-normal density (sigma_lnrho given), p = rho^gamma, and
+  the same Gaussian velocity spectrum.
+* `ensemble`: many independent periodic boxes of log-uniform size.
+* `contact_3d` / `lattice_*`: the special cases the tests use.
+
+Conserved states are built from primitives with the cell volumes the
+tessellator integrated directly: m = rho V, p = m v, E = V (P/(gamma-1) +
+rho v^2 / 2).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .tess import Tessellation, tessellate
+
+
+@dataclass
+class Problem:
+    name: str
+    dim: int
+    gamma: float
+    tess: Tessellation
+    rho: np.ndarray          # [n]
+    vel: np.ndarray          # [n, dim]
+    pres: np.ndarray         # [n]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self):
+        return self.tess.n_cells
+
+    @property
+    def n_faces(self):
+        return self.tess.n_faces
+
+    def conserved(self):
+        return conserved_from_primitives(self.rho, self.vel, self.pres, self.tess.volume, self.gamma)
+
+
+def conserved_from_primitives(rho, vel, pres, vol, gamma):
+    """Q = (m, p, E) per cell from (rho, v, P) and the cell volume."""
+    m = rho * vol
+    mom = m[:, None] * vel
+    ene = vol * (pres / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=1))
+    return np.concatenate([m[:, None], mom, ene[:, None]], axis=1)
+
+
+def lattice_nodes(dims, box):
+    """Cell-centred lattice nodes, row-major with the last axis fastest."""
+    dims = tuple(int(d) for d in dims)
+    h = np.asarray(box, np.float64) / np.asarray(dims, np.float64)
+    idx = np.stack(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij"), -1).reshape(-1, len(dims))
+    return (idx + 0.5) * h, h
+
+
+def jittered_lattice(dims, box, jitter, rng):
+    """Lattice nodes displaced by U(-jitter*h, +jitter*h) per coordinate."""
+    nodes, h = lattice_nodes(dims, box)
+    pts = nodes + rng.uniform(-1.0, 1.0, nodes.shape) * (jitter * h)
+    box = np.asarray(box, np.float64)
+    pts = np.mod(pts, box)
+    return np.where(pts >= box, pts - box, pts)
+
+
+def gaussian_field(shape, kmin, kmax, slope, rng):
+    """Zero-mean, unit-variance Gaussian random field on a periodic grid.
+
+    White noise filtered in Fourier space by sqrt(P(k)) with P(k) ~ k^slope on
+    kmin <= |k| <= kmax (k in units of the fundamental mode), zero elsewhere.
+    """
+    white = rng.standard_normal(shape)
+    fk = np.fft.rfftn(white)
+    ks = [np.fft.fftfreq(n) * n for n in shape[:-1]] + [np.fft.rfftfreq(shape[-1]) * shape[-1]]
+    grids = np.meshgrid(*ks, indexing="ij", sparse=True)
+    kk = np.sqrt(sum(g * g for g in grids))
+    ksafe = np.where(kk > 0, kk, 1.0)
+    amp = np.where((kk >= kmin) & (kk <= kmax), ksafe ** (0.5 * slope), 0.0)
+    f = np.fft.irfftn(fk * amp, s=shape, axes=tuple(range(len(shape))))
+    f -= f.mean()
+    f /= f.std()
+    return f
+
+
+def velocity_field(dims, rng, rms, kmin=2, kmax=8, slope=-4.0):
+    """Per-component independent Gaussian fields rescaled to rms |v| = rms."""
+    comps = [gaussian_field(tuple(dims), kmin, kmax, slope, rng).reshape(-1) for _ in range(len(dims))]
+    v = np.stack(comps, axis=1)
+    v -= v.mean(axis=0)
+    v *= rms / np.sqrt(np.mean(np.sum(v * v, axis=1)))
+    return v
+
+
+def sod_2d(nx=128, ny=64, jitter=0.1, seed=1, gamma=1.4, nthreads=0):
+    """Periodic [0,2]x[0,1]: rho=1,P=1 for 0.5<x<1.5, rho=0.125,P=0.1 elsewhere, v=0."""
+    rng = np.random.default_rng(seed)
+    box = np.array([2.0, 1.0])
+    pts = jittered_lattice((nx, ny), box, jitter, rng)
+    T = tessellate(pts, box, nthreads)
+    inside = (pts[:, 0] > 0.5) & (pts[:, 0] < 1.5)
+    rho = np.where(inside, 1.0, 0.125)
+    pres = np.where(inside, 1.0, 0.1)
+    vel = np.zeros((len(pts), 2))
+    return Problem("sod_2d", 2, gamma, T, rho, vel, pres,
+                   dict(dims=(nx, ny), jitter=jitter, seed=seed, cfl=0.3, t_end=0.2))
+
+
+def turbulent_3d(n=64, jitter=0.2, seed=2, mach=2.0, gamma=5.0 / 3.0, nthreads=0, box=1.0):
+    """rho=1, P=1, Gaussian velocity field (k^-4, 2<=k<=8) at rms Mach `mach`."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    boxv = np.array([box] * 3, np.float64)
+    pts = jittered_lattice(dims, boxv, jitter, rng)
+    T = tessellate(pts, boxv, nthreads)
+    cs = np.sqrt(gamma * 1.0 / 1.0)
+    vel = velocity_field(dims, rng, mach * cs)
+    rho = np.ones(len(pts))
+    pres = np.ones(len(pts))
+    return Problem("turbulent_3d", 3, gamma, T, rho, vel, pres,
+                   dict(dims=dims, jitter=jitter, seed=seed, mach=mach))
+
+
+def lognormal_3d(n=192, jitter=0.2, seed=3, sigma=1.0, mach=3.0, gamma=5.0 / 3.0, nthreads=0):
+    """ln rho Gaussian (k^-4, 2<=k<=8) with sigma_lnrho, mean rho 1; P = rho^gamma; rms v = mach c_s(rho=1)."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    boxv = np.ones(3)
+    pts = jittered_lattice(dims, boxv, jitter, rng)
+    T = tessellate(pts, boxv, nthreads)
+    g = gaussian_field(dims, 2, 8, -4.0, rng).reshape(-1)
+    rho = np.exp(sigma * g - 0.5 * sigma * sigma)
+    rho /= rho.mean()
+    pres = rho ** gamma
+    cs = np.sqrt(gamma)
+    vel = velocity_field(dims, rng, mach * cs)
+    return Problem("lognormal_3d", 3, gamma, T, rho, vel, pres,
+                   dict(dims=dims, jitter=jitter, seed=seed, sigma=sigma, mach=mach))
+
+
+def contact_3d(n=12, jitter=0.2, seed=7, v=(1.0, 0.5, -0.25), gamma=5.0 / 3.0):
+    """Uniform velocity and pressure P=3/5, density 1 | 2 across x=0.5 (moving contact)."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    boxv = np.ones(3)
+    pts = jittered_lattice(dims, boxv, jitter, rng)
+    T = tessellate(pts, boxv)
+    rho = np.where(pts[:, 0] < 0.5, 1.0, 2.0)
+    pres = np.full(len(pts), 0.6)
+    vel = np.tile(np.asarray(v, np.float64), (len(pts), 1))
+    return Problem("contact_3d", 3, gamma, T, rho, vel, pres, dict(dims=dims, seed=seed))
+
+
+def ensemble_sizes(nboxes=64, seed=5, nmin=16, nmax=96):
+    """Per-box lattice size n_b = round(exp(U(ln nmin, ln nmax))) and rms Mach U[0.5, 4]."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), nboxes))).astype(int)
+    machs = rng.uniform(0.5, 4.0, nboxes)
+    seeds = rng.integers(0, 2**31 - 1, nboxes)
+    return sizes, machs, seeds
+
+
+def ensemble(nboxes=64, seed=5, nmin=16, nmax=96, jitter=0.2, gamma=5.0 / 3.0, nthreads=0):
+    """Independent unit periodic boxes, each a `turbulent_3d` field of its own size and Mach."""
+    sizes, machs, seeds = ensemble_sizes(nboxes, seed, nmin, nmax)
+    return [turbulent_3d(int(n), jitter, int(s), float(m), gamma, nthreads) for n, m, s in zip(sizes, machs, seeds)]
+
+
+def boosted(problem, v0):
+    """The same problem seen from a frame moving with -v0: every fluid velocity gets +v0."""
+    v0 = np.asarray(v0, np.float64)
+    return Problem(problem.name + "_boosted", problem.dim, problem.gamma, problem.tess, problem.rho.copy(),
+                   problem.vel + v0[None, :], problem.pres.copy(), dict(problem.meta, boost=v0.tolist()))

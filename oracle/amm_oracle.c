@@ -1,0 +1,706 @@
+/*
+ * amm_oracle.c -- plain, slow, FP64 CPU oracle of one moving-mesh
+ * MUSCL-Hancock update on a given Voronoi tessellation (Springel 2010,
+ * "E pur si muove", Sec. 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  It shares no code with the CUDA
+ * path and must never be called by it.
+ *
+ * Every function follows one passage of the paper, step by step, in its order
+ * and notation; nothing is blocked, fused or reordered.  Build with
+ * -O2 -ffp-contract=off.
+ *
+ * Conventions.  Face k joins cell L = cells[2k] and cell R = cells[2k+1]; the
+ * right cell's generator is taken in the periodic image
+ * r_R + shift[k] * box, and the face centroid cen[k] is given in the left
+ * cell's frame.  Per-cell arrays: Q = (m, p_1..p_D, E), W = (rho, v_1..v_D, P),
+ * gradients grad[i][var][axis] with var over the D+2 primitives.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NV_MAX 5 /* D + 2 primitives for D <= 3 */
+
+/* ------------------------------------------------------------------ helpers */
+
+static void face_positions(int dim, long k, const double* gen, const int32_t* cells, const int8_t* shift,
+                           const double* box, double* rL, double* rR) {
+  const int L = cells[2 * k], R = cells[2 * k + 1];
+  for (int d = 0; d < dim; d++) {
+    rL[d] = gen[(long)L * dim + d];
+    rR[d] = gen[(long)R * dim + d] + shift[k * dim + d] * box[d];
+  }
+}
+
+/* Cell -> (face, side) incidence lists in face order; side 0 = left, 1 = right. */
+typedef struct {
+  long* off;
+  long* face;
+  int* side;
+} incidence;
+
+static incidence build_incidence(long n, long nf, const int32_t* cells) {
+  incidence I;
+  I.off = (long*)calloc((size_t)n + 1, sizeof(long));
+  I.face = (long*)malloc(sizeof(long) * (size_t)(2 * nf + 1));
+  I.side = (int*)malloc(sizeof(int) * (size_t)(2 * nf + 1));
+  for (long k = 0; k < nf; k++) {
+    I.off[cells[2 * k] + 1]++;
+    I.off[cells[2 * k + 1] + 1]++;
+  }
+  for (long i = 0; i < n; i++) I.off[i + 1] += I.off[i];
+  long* fill = (long*)malloc(sizeof(long) * (size_t)(n + 1));
+  memcpy(fill, I.off, sizeof(long) * (size_t)(n + 1));
+  for (long k = 0; k < nf; k++) {
+    for (int s = 0; s < 2; s++) {
+      const long c = cells[2 * k + s];
+      I.face[fill[c]] = k;
+      I.side[fill[c]] = s;
+      fill[c]++;
+    }
+  }
+  free(fill);
+  return I;
+}
+
+static void free_incidence(incidence* I) {
+  free(I->off);
+  free(I->face);
+  free(I->side);
+}
+
+/* For cell i seen through face k from `side`: its own generator r_i, the
+ * neighbour's generator r_j and the face centroid f, all in cell i's frame. */
+static void incidence_geometry(int dim, long k, int side, const double* gen, const int32_t* cells,
+                               const int8_t* shift, const double* cen, const double* box, double* ri, double* rj,
+                               double* f) {
+  double rL[3], rR[3];
+  face_positions(dim, k, gen, cells, shift, box, rL, rR);
+  for (int d = 0; d < dim; d++) {
+    if (side == 0) {
+      ri[d] = rL[d];
+      rj[d] = rR[d];
+      f[d] = cen[k * dim + d];
+    } else {
+      const double sh = shift[k * dim + d] * box[d];
+      ri[d] = rR[d] - sh; /* = generator of R in its own frame */
+      rj[d] = rL[d] - sh;
+      f[d] = cen[k * dim + d] - sh;
+    }
+  }
+}
+
+/* ---------------------------------------------------- A0: volumes, centroids
+ * Sec. 2.3: a cell's volume is the sum of the pyramids spanned by its faces
+ * and its generator; the pyramid over face k has height |r_R - r_L| / 2.
+ * The centre of mass is the volume-weighted mean of the pyramid centroids,
+ * which sit a fraction D/(D+1) of the way from the apex to the base centroid.
+ * Returns 0, or -1 if a cell has non-positive volume. */
+int ora_geometry(int dim, long n, const double* gen, long nf, const int32_t* cells, const int8_t* shift,
+                 const double* area, const double* cen, const double* box, double* V, double* s) {
+  double* mom = (double*)calloc((size_t)n * dim, sizeof(double));
+  for (long i = 0; i < n; i++) V[i] = 0.0;
+  for (long k = 0; k < nf; k++) {
+    const int L = cells[2 * k], R = cells[2 * k + 1];
+    double rL[3], rR[3];
+    face_positions(dim, k, gen, cells, shift, box, rL, rR);
+    double sep = 0.0;
+    for (int d = 0; d < dim; d++) sep += (rR[d] - rL[d]) * (rR[d] - rL[d]);
+    sep = sqrt(sep);
+    const double vpyr = area[k] * (0.5 * sep) / dim;
+    const double frac = (double)dim / (double)(dim + 1);
+    V[L] += vpyr;
+    V[R] += vpyr;
+    for (int d = 0; d < dim; d++) {
+      const double f = cen[k * dim + d];
+      /* left pyramid, in L's frame */
+      mom[(long)L * dim + d] += vpyr * (rL[d] + frac * (f - rL[d]));
+      /* right pyramid, apex at the image of R; shifted back into R's frame */
+      const double sh = shift[k * dim + d] * box[d];
+      mom[(long)R * dim + d] += vpyr * (rR[d] + frac * (f - rR[d]) - sh);
+    }
+  }
+  int bad = 0;
+  for (long i = 0; i < n; i++) {
+    if (!(V[i] > 0.0)) bad = 1;
+    for (int d = 0; d < dim; d++) s[i * dim + d] = mom[i * dim + d] / V[i];
+  }
+  free(mom);
+  return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------ A1: conserved -> primitive
+ * Sec. 3, step 2 and the equation of state P = (gamma-1) rho u:
+ * rho = m/V, v = p/m, P = (gamma-1) (E/V - rho |v|^2 / 2). */
+void ora_primitives(int dim, long n, const double* Q, const double* V, double gamma, double* W) {
+  const int nv = dim + 2;
+  for (long i = 0; i < n; i++) {
+    const double m = Q[i * nv];
+    const double rho = m / V[i];
+    double v2 = 0.0;
+    W[i * nv] = rho;
+    for (int d = 0; d < dim; d++) {
+      const double v = Q[i * nv + 1 + d] / m;
+      W[i * nv + 1 + d] = v;
+      v2 += v * v;
+    }
+    const double E = Q[i * nv + dim + 1];
+    W[i * nv + dim + 1] = (gamma - 1.0) * (E / V[i] - 0.5 * rho * v2);
+  }
+}
+
+/* ---------------------------------------------- A2 + A3: gradients, limiter
+ * Gradient, eq. (eqngrad2), Sec. 3.1:
+ *   <grad phi>_i = (1/V_i) sum_j A_ij ( [phi_j - phi_i] c_ij / r_ij
+ *                                       - (phi_i + phi_j)/2 * r_ij_vec / r_ij )
+ * with r_ij_vec = r_i - r_j and c_ij = f_ij - (r_i + r_j)/2.
+ * Limiter, Sec. 3.1 (Barth-Jespersen form): per primitive variable
+ * alpha_i = min(1, min_j psi_ij), psi_ij = (phi_max - phi_i)/dphi for dphi>0,
+ * (phi_min - phi_i)/dphi for dphi<0, 1 for dphi=0, dphi = grad . (f_ij - s_i);
+ * phi_max/phi_min over the neighbours and the cell itself (the paper's second
+ * "max" is read as "min").  grad: [n][dim+2][dim]. */
+void ora_gradients(int dim, long n, const double* W, const double* gen, const double* V, const double* s, long nf,
+                   const int32_t* cells, const int8_t* shift, const double* area, const double* cen,
+                   const double* box, int limit, double* grad) {
+  const int nv = dim + 2;
+  incidence I = build_incidence(n, nf, cells);
+  for (long i = 0; i < n; i++) {
+    double g[NV_MAX][3];
+    for (int v = 0; v < nv; v++)
+      for (int d = 0; d < 3; d++) g[v][d] = 0.0;
+    for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+      const long k = I.face[q];
+      const int side = I.side[q];
+      const long j = cells[2 * k + (1 - side)];
+      double ri[3], rj[3], f[3];
+      incidence_geometry(dim, k, side, gen, cells, shift, cen, box, ri, rj, f);
+      double rij[3], c[3], r = 0.0;
+      for (int d = 0; d < dim; d++) {
+        rij[d] = ri[d] - rj[d];
+        c[d] = f[d] - 0.5 * (ri[d] + rj[d]);
+        r += rij[d] * rij[d];
+      }
+      r = sqrt(r);
+      for (int v = 0; v < nv; v++) {
+        const double phi_i = W[i * nv + v], phi_j = W[j * nv + v];
+        for (int d = 0; d < dim; d++)
+          g[v][d] += area[k] * ((phi_j - phi_i) * c[d] / r - 0.5 * (phi_i + phi_j) * rij[d] / r);
+      }
+    }
+    for (int v = 0; v < nv; v++)
+      for (int d = 0; d < dim; d++) g[v][d] /= V[i];
+
+    if (limit) {
+      for (int v = 0; v < nv; v++) {
+        const double phi_i = W[i * nv + v];
+        double phi_max = phi_i, phi_min = phi_i;
+        for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+          const long k = I.face[q];
+          const long j = cells[2 * k + (1 - I.side[q])];
+          const double phi_j = W[j * nv + v];
+          if (phi_j > phi_max) phi_max = phi_j;
+          if (phi_j < phi_min) phi_min = phi_j;
+        }
+        double alpha = 1.0;
+        for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+          const long k = I.face[q];
+          double ri[3], rj[3], f[3];
+          incidence_geometry(dim, k, I.side[q], gen, cells, shift, cen, box, ri, rj, f);
+          double dphi = 0.0;
+          for (int d = 0; d < dim; d++) dphi += g[v][d] * (f[d] - s[i * dim + d]);
+          double psi;
+          if (dphi > 0.0)
+            psi = (phi_max - phi_i) / dphi;
+          else if (dphi < 0.0)
+            psi = (phi_min - phi_i) / dphi;
+          else
+            psi = 1.0;
+          if (psi < alpha) alpha = psi;
+        }
+        for (int d = 0; d < dim; d++) g[v][d] *= alpha;
+      }
+    }
+    for (int v = 0; v < nv; v++)
+      for (int d = 0; d < dim; d++) grad[(i * nv + v) * dim + d] = g[v][d];
+  }
+  free_incidence(&I);
+}
+
+/* ---------------------------------------------------------- A4: CFL step
+ * Eq. (EqnTiStep), Sec. 7.1: dt_i = C_CFL R_i / (c_i + |v_i - w_i|), with
+ * R_i = (3 V_i / 4 pi)^(1/3) in 3D, (V_i / pi)^(1/2) in 2D, c_i = sqrt(gamma
+ * P/rho); the global step is the minimum over cells.  wmesh may be NULL (0). */
+double ora_timestep(int dim, long n, const double* W, const double* V, const double* wmesh, double gamma,
+                    double cfl, double* dt_cell) {
+  const int nv = dim + 2;
+  double dtmin = INFINITY;
+  for (long i = 0; i < n; i++) {
+    const double rho = W[i * nv], P = W[i * nv + dim + 1];
+    const double R = (dim == 3) ? cbrt(3.0 * V[i] / (4.0 * M_PI)) : sqrt(V[i] / M_PI);
+    const double c = sqrt(gamma * P / rho);
+    double vr = 0.0;
+    for (int d = 0; d < dim; d++) {
+      const double dv = W[i * nv + 1 + d] - (wmesh ? wmesh[i * dim + d] : 0.0);
+      vr += dv * dv;
+    }
+    const double dt = cfl * R / (c + sqrt(vr));
+    if (dt_cell) dt_cell[i] = dt;
+    if (dt < dtmin) dtmin = dt;
+  }
+  return dtmin;
+}
+
+/* ------------------------------------------------ A7: exact Riemann solver
+ * Sec. 3.3 names an exact solver for the ideal gas with an extension for
+ * vacuum states.  Written here from the gas dynamics of the 1D Riemann
+ * problem: the star pressure p* is the root of
+ *   f(p) = f_L(p) + f_R(p) + (u_R - u_L),
+ *   f_K(p) = (p - p_K) sqrt(A_K / (p + B_K))              (shock, p > p_K)
+ *          = 2 c_K/(gamma-1) ((p/p_K)^((gamma-1)/(2gamma)) - 1)   (rarefaction)
+ *   A_K = 2/((gamma+1) rho_K), B_K = (gamma-1)/(gamma+1) p_K,
+ * found by Newton from the adaptive primitive-variable / two-rarefaction /
+ * two-shock guess, to the relative change 2|dp|/(p_new+p_old) < tol; then
+ * u* = (u_L+u_R)/2 + (f_R(p*) - f_L(p*))/2 and the self-similar solution is
+ * sampled at x/t = 0.  Vacuum: a vacuum side, or vacuum generated between two
+ * rarefactions when 2(c_L+c_R)/(gamma-1) <= u_R - u_L; the sampled state in
+ * vacuum is rho = P = 0.
+ *
+ * in: (rho, u, p) per side.  out: rho, u, p at x/t=0, p*, u*, side (0 left of
+ * the contact, 1 right; decides the upwind transverse velocity).
+ * Returns 0 ok, 1 vacuum involved, -1 Newton did not converge in maxit. */
+
+static double pfun(double p, double rhoK, double pK, double cK, double g, double* dfdp) {
+  if (p > pK) {
+    const double A = 2.0 / ((g + 1.0) * rhoK);
+    const double B = (g - 1.0) / (g + 1.0) * pK;
+    const double q = sqrt(A / (p + B));
+    *dfdp = q * (1.0 - 0.5 * (p - pK) / (p + B));
+    return (p - pK) * q;
+  }
+  const double pr = p / pK;
+  *dfdp = pow(pr, -(g + 1.0) / (2.0 * g)) / (rhoK * cK);
+  return 2.0 * cK / (g - 1.0) * (pow(pr, (g - 1.0) / (2.0 * g)) - 1.0);
+}
+
+/* state inside a rarefaction fan (left-facing if dir = -1, right-facing +1)
+ * at x/t = S, from the isentropic relations and the Riemann invariant */
+static void fan_state(double g, double rhoK, double uK, double pK, double cK, int dir, double S, double* rho,
+                      double* u, double* p) {
+  double c;
+  if (dir < 0) { /* left wave: u + 2c/(g-1) constant, S = u - c */
+    c = 2.0 / (g + 1.0) * cK + (g - 1.0) / (g + 1.0) * (uK - S);
+    *u = S + c;
+  } else { /* right wave: u - 2c/(g-1) constant, S = u + c */
+    c = 2.0 / (g + 1.0) * cK - (g - 1.0) / (g + 1.0) * (uK - S);
+    *u = S - c;
+  }
+  const double ratio = c / cK;
+  *rho = rhoK * pow(ratio, 2.0 / (g - 1.0));
+  *p = pK * pow(ratio, 2.0 * g / (g - 1.0));
+}
+
+/* one side adjoining vacuum (dir=-1: left state facing vacuum on its right) */
+static void sample_vacuum_side(double g, double rhoK, double uK, double pK, int dir, double S, double* out) {
+  const double cK = sqrt(g * pK / rhoK);
+  if (dir < 0) { /* left state, vacuum to the right: left-facing fan */
+    const double head = uK - cK, front = uK + 2.0 * cK / (g - 1.0);
+    if (S <= head) {
+      out[0] = rhoK; out[1] = uK; out[2] = pK;
+    } else if (S >= front) {
+      out[0] = 0.0; out[1] = front; out[2] = 0.0;
+    } else {
+      fan_state(g, rhoK, uK, pK, cK, -1, S, &out[0], &out[1], &out[2]);
+    }
+  } else { /* right state, vacuum to the left: right-facing fan */
+    const double head = uK + cK, front = uK - 2.0 * cK / (g - 1.0);
+    if (S >= head) {
+      out[0] = rhoK; out[1] = uK; out[2] = pK;
+    } else if (S <= front) {
+      out[0] = 0.0; out[1] = front; out[2] = 0.0;
+    } else {
+      fan_state(g, rhoK, uK, pK, cK, +1, S, &out[0], &out[1], &out[2]);
+    }
+  }
+}
+
+int ora_riemann(double g, const double* WL, const double* WR, double tol, int maxit, double* out, int* niter) {
+  const double rhoL = WL[0], uL = WL[1], pL = WL[2];
+  const double rhoR = WR[0], uR = WR[1], pR = WR[2];
+  const double S = 0.0;
+  *niter = 0;
+  /* vacuum on one or both sides */
+  if (!(rhoL > 0.0) && !(rhoR > 0.0)) {
+    out[0] = out[1] = out[2] = out[3] = out[4] = 0.0;
+    out[5] = 0.0;
+    return 1;
+  }
+  if (!(rhoL > 0.0)) {
+    sample_vacuum_side(g, rhoR, uR, pR, +1, S, out);
+    out[3] = 0.0;
+    out[4] = uR - 2.0 * sqrt(g * pR / rhoR) / (g - 1.0);
+    out[5] = 1.0;
+    return 1;
+  }
+  if (!(rhoR > 0.0)) {
+    sample_vacuum_side(g, rhoL, uL, pL, -1, S, out);
+    out[3] = 0.0;
+    out[4] = uL + 2.0 * sqrt(g * pL / rhoL) / (g - 1.0);
+    out[5] = 0.0;
+    return 1;
+  }
+  const double cL = sqrt(g * pL / rhoL), cR = sqrt(g * pR / rhoR);
+  /* vacuum generated between two rarefactions */
+  if (2.0 * (cL + cR) / (g - 1.0) <= uR - uL) {
+    const double frontL = uL + 2.0 * cL / (g - 1.0);
+    const double frontR = uR - 2.0 * cR / (g - 1.0);
+    if (S <= frontL) {
+      sample_vacuum_side(g, rhoL, uL, pL, -1, S, out);
+      out[5] = 0.0;
+    } else if (S >= frontR) {
+      sample_vacuum_side(g, rhoR, uR, pR, +1, S, out);
+      out[5] = 1.0;
+    } else {
+      out[0] = 0.0; out[1] = 0.5 * (frontL + frontR); out[2] = 0.0;
+      out[5] = 0.0;
+    }
+    out[3] = 0.0;
+    out[4] = 0.5 * (frontL + frontR);
+    return 1;
+  }
+  /* initial guess: adaptive choice among the linearised (primitive-variable),
+   * two-rarefaction and two-shock estimates, switch ratio 2 */
+  const double du = uR - uL;
+  double p0;
+  {
+    const double ppv0 = 0.5 * (pL + pR) - 0.125 * du * (rhoL + rhoR) * (cL + cR);
+    const double ppv = ppv0 > 0.0 ? ppv0 : 0.0;
+    const double pmin = pL < pR ? pL : pR, pmax = pL > pR ? pL : pR;
+    if (pmax / pmin <= 2.0 && ppv >= pmin && ppv <= pmax) {
+      p0 = ppv;
+    } else if (ppv < pmin) {
+      const double z = (g - 1.0) / (2.0 * g);
+      const double num = cL + cR - 0.5 * (g - 1.0) * du;
+      const double den = cL / pow(pL, z) + cR / pow(pR, z);
+      p0 = pow(num / den, 1.0 / z);
+    } else {
+      const double AL = 2.0 / ((g + 1.0) * rhoL), BL = (g - 1.0) / (g + 1.0) * pL;
+      const double AR = 2.0 / ((g + 1.0) * rhoR), BR = (g - 1.0) / (g + 1.0) * pR;
+      const double gL = sqrt(AL / (ppv + BL)), gR = sqrt(AR / (ppv + BR));
+      p0 = (gL * pL + gR * pR - du) / (gL + gR);
+    }
+    const double pfloor = 1e-10 * 0.5 * (pL + pR);
+    if (!(p0 > pfloor)) p0 = pfloor;
+  }
+  /* Newton iteration on f(p) = 0 */
+  double p = p0;
+  int it = 0, conv = 0;
+  while (it < maxit) {
+    double dL, dR;
+    const double f = pfun(p, rhoL, pL, cL, g, &dL) + pfun(p, rhoR, pR, cR, g, &dR) + du;
+    double pn = p - f / (dL + dR);
+    if (!(pn > 0.0)) pn = 1e-3 * p;
+    it++;
+    const double change = 2.0 * fabs(pn - p) / (pn + p);
+    p = pn;
+    if (change < tol) {
+      conv = 1;
+      break;
+    }
+  }
+  *niter = it;
+  double dL, dR;
+  const double fL = pfun(p, rhoL, pL, cL, g, &dL), fR = pfun(p, rhoR, pR, cR, g, &dR);
+  const double us = 0.5 * (uL + uR) + 0.5 * (fR - fL);
+  out[3] = p;
+  out[4] = us;
+  /* sample at x/t = S */
+  if (S <= us) { /* left of the contact */
+    out[5] = 0.0;
+    if (p > pL) { /* left shock */
+      const double SL = uL - cL * sqrt((g + 1.0) / (2.0 * g) * p / pL + (g - 1.0) / (2.0 * g));
+      if (S <= SL) {
+        out[0] = rhoL; out[1] = uL; out[2] = pL;
+      } else {
+        const double r = p / pL, g6 = (g - 1.0) / (g + 1.0);
+        out[0] = rhoL * (r + g6) / (g6 * r + 1.0); out[1] = us; out[2] = p;
+      }
+    } else { /* left rarefaction */
+      const double head = uL - cL;
+      const double cs = cL * pow(p / pL, (g - 1.0) / (2.0 * g));
+      const double tail = us - cs;
+      if (S <= head) {
+        out[0] = rhoL; out[1] = uL; out[2] = pL;
+      } else if (S > tail) {
+        out[0] = rhoL * pow(p / pL, 1.0 / g); out[1] = us; out[2] = p;
+      } else {
+        fan_state(g, rhoL, uL, pL, cL, -1, S, &out[0], &out[1], &out[2]);
+      }
+    }
+  } else { /* right of the contact */
+    out[5] = 1.0;
+    if (p > pR) { /* right shock */
+      const double SR = uR + cR * sqrt((g + 1.0) / (2.0 * g) * p / pR + (g - 1.0) / (2.0 * g));
+      if (S >= SR) {
+        out[0] = rhoR; out[1] = uR; out[2] = pR;
+      } else {
+        const double r = p / pR, g6 = (g - 1.0) / (g + 1.0);
+        out[0] = rhoR * (r + g6) / (g6 * r + 1.0); out[1] = us; out[2] = p;
+      }
+    } else { /* right rarefaction */
+      const double head = uR + cR;
+      const double cs = cR * pow(p / pR, (g - 1.0) / (2.0 * g));
+      const double tail = us + cs;
+      if (S >= head) {
+        out[0] = rhoR; out[1] = uR; out[2] = pR;
+      } else if (S < tail) {
+        out[0] = rhoR * pow(p / pR, 1.0 / g); out[1] = us; out[2] = p;
+      } else {
+        fan_state(g, rhoR, uR, pR, cR, +1, S, &out[0], &out[1], &out[2]);
+      }
+    }
+  }
+  return conv ? 0 : -1;
+}
+
+/* batch form for tests: W* arrays [m][3], out [m][6], niter [m]; returns
+ * the number of problems that did not converge */
+long ora_riemann_batch(double g, long m, const double* WL, const double* WR, double tol, int maxit, double* out,
+                       int32_t* niter) {
+  long bad = 0;
+  for (long q = 0; q < m; q++) {
+    int it = 0;
+    if (ora_riemann(g, WL + 3 * q, WR + 3 * q, tol, maxit, out + 6 * q, &it) < 0) bad++;
+    niter[q] = it;
+  }
+  return bad;
+}
+
+/* ------------------------------------------------------ A5: face velocity
+ * Sec. 3.3 (Fig. FigSketchVelFace): w = (w_L + w_R)/2 + w', with
+ * w' = [(w_L - w_R) . (f - (r_R + r_L)/2)] / |r_R - r_L| * (r_R - r_L)/|r_R - r_L|.
+ * wface: [nf][dim].  wmesh NULL means a static mesh. */
+void ora_face_velocities(int dim, long nf, const int32_t* cells, const int8_t* shift, const double* gen,
+                         const double* cen, const double* box, const double* wmesh, double* wface) {
+  for (long k = 0; k < nf; k++) {
+    const int L = cells[2 * k], R = cells[2 * k + 1];
+    double rL[3], rR[3];
+    face_positions(dim, k, gen, cells, shift, box, rL, rR);
+    double sep = 0.0;
+    for (int d = 0; d < dim; d++) sep += (rR[d] - rL[d]) * (rR[d] - rL[d]);
+    sep = sqrt(sep);
+    double proj = 0.0;
+    for (int d = 0; d < dim; d++) {
+      const double wL = wmesh ? wmesh[(long)L * dim + d] : 0.0;
+      const double wR = wmesh ? wmesh[(long)R * dim + d] : 0.0;
+      proj += (wL - wR) * (cen[k * dim + d] - 0.5 * (rR[d] + rL[d]));
+    }
+    for (int d = 0; d < dim; d++) {
+      const double wL = wmesh ? wmesh[(long)L * dim + d] : 0.0;
+      const double wR = wmesh ? wmesh[(long)R * dim + d] : 0.0;
+      wface[k * dim + d] = 0.5 * (wR + wL) + proj / sep * (rR[d] - rL[d]) / sep;
+    }
+  }
+}
+
+/* ------------------------------------------------- A6: MUSCL-Hancock flux
+ * Sec. 3.3, eqs. (eqnrefframe) to (eqfinalflux), for every face:
+ *  1. W'_K = W_K - (0, w, 0): the cell-centre state in the face frame;
+ *  2. W''_K = W'_K + dW/dr|_K (f - s_K) + dW'/dt|_K dt/2, with the time
+ *     derivative from dW/dt = -A(W) dW/dr evaluated at the cell-centre state
+ *     W'_K in the face frame (component form:
+ *       drho/dt = -(v'.grad rho + rho div v),
+ *       dv/dt   = -(v'.grad) v - grad P / rho,
+ *       dP/dt   = -(gamma P div v + v'.grad P));
+ *     if either side's rho'' or P'' is not positive, both sides fall back to
+ *     W' (first order) and the face is counted;
+ *  3. rotate: normal velocity u = v''.n, transverse vector v'' - u n kept;
+ *  4. Riemann problem along n, sampled at x/t = 0; transverse velocity taken
+ *     from the side of the contact that x/t = 0 lies on (the left side when
+ *     u* = 0);
+ *  5. back to the lab frame v_lab = u_F n + v_t + w and the flux of the
+ *     moving face, projected on n:
+ *       F_m = rho_F u_F,  F_p = rho_F v_lab u_F + P_F n,
+ *       F_E = (rho_F |v_lab|^2/2 + P_F/(gamma-1)) u_F + P_F v_lab . n.
+ * F: [nf][dim+2] per unit area (not multiplied by A).
+ * counters: [0] fallback faces, [1] vacuum faces, [2] Newton iterations,
+ * [3] Newton failures.  Returns 0, or -1 if any Newton solve failed. */
+int ora_fluxes(int dim, long n, const double* W, const double* grad, const double* gen, const double* s,
+               const double* wmesh, long nf, const int32_t* cells, const int8_t* shift, const double* area,
+               const double* cen, const double* box, double gamma, double dt, double tol, int maxit, double* F,
+               int64_t* counters) {
+  (void)n;
+  (void)area;
+  const int nv = dim + 2;
+  double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
+  ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
+  int rc = 0;
+  for (long k = 0; k < nf; k++) {
+    const int cellK[2] = {cells[2 * k], cells[2 * k + 1]};
+    double rL[3], rR[3];
+    face_positions(dim, k, gen, cells, shift, box, rL, rR);
+    double nrm[3], sep = 0.0;
+    for (int d = 0; d < dim; d++) sep += (rR[d] - rL[d]) * (rR[d] - rL[d]);
+    sep = sqrt(sep);
+    for (int d = 0; d < dim; d++) nrm[d] = (rR[d] - rL[d]) / sep;
+    const double* w = wface + k * dim;
+
+    double Wp[2][NV_MAX], Wpp[2][NV_MAX];
+    for (int side = 0; side < 2; side++) {
+      const long i = cellK[side];
+      const double* Wi = W + i * nv;
+      const double* gi = grad + i * nv * dim;
+      /* face centroid relative to the centre of mass, in cell i's frame */
+      double fs[3];
+      for (int d = 0; d < dim; d++) {
+        const double sh = (side == 1) ? shift[k * dim + d] * box[d] : 0.0;
+        fs[d] = (cen[k * dim + d] - sh) - s[i * dim + d];
+      }
+      /* 1. boost into the face frame */
+      Wp[side][0] = Wi[0];
+      for (int d = 0; d < dim; d++) Wp[side][1 + d] = Wi[1 + d] - w[d];
+      Wp[side][dim + 1] = Wi[dim + 1];
+      /* 2a. spatial extrapolation to the face centroid */
+      for (int v = 0; v < nv; v++) {
+        double dv = 0.0;
+        for (int d = 0; d < dim; d++) dv += gi[v * dim + d] * fs[d];
+        Wpp[side][v] = Wp[side][v] + dv;
+      }
+      /* 2b. half-step time prediction with A(W') at the cell centre */
+      const double rho = Wp[side][0], P = Wp[side][dim + 1];
+      const double* vp = &Wp[side][1];
+      double divv = 0.0, vgrad_rho = 0.0, vgrad_P = 0.0;
+      for (int d = 0; d < dim; d++) {
+        divv += gi[(1 + d) * dim + d];
+        vgrad_rho += vp[d] * gi[0 * dim + d];
+        vgrad_P += vp[d] * gi[(dim + 1) * dim + d];
+      }
+      const double drho_dt = -(vgrad_rho + rho * divv);
+      const double dP_dt = -(gamma * P * divv + vgrad_P);
+      Wpp[side][0] += 0.5 * dt * drho_dt;
+      Wpp[side][dim + 1] += 0.5 * dt * dP_dt;
+      for (int a = 0; a < dim; a++) {
+        double adv = 0.0;
+        for (int d = 0; d < dim; d++) adv += vp[d] * gi[(1 + a) * dim + d];
+        const double dva_dt = -adv - gi[(dim + 1) * dim + a] / rho;
+        Wpp[side][1 + a] += 0.5 * dt * dva_dt;
+      }
+    }
+    if (!(Wpp[0][0] > 0.0) || !(Wpp[0][dim + 1] > 0.0) || !(Wpp[1][0] > 0.0) || !(Wpp[1][dim + 1] > 0.0)) {
+      for (int side = 0; side < 2; side++)
+        for (int v = 0; v < nv; v++) Wpp[side][v] = Wp[side][v];
+      counters[0]++;
+    }
+    /* 3. rotate: normal component and transverse vector */
+    double un[2], vt[2][3];
+    for (int side = 0; side < 2; side++) {
+      double u = 0.0;
+      for (int d = 0; d < dim; d++) u += Wpp[side][1 + d] * nrm[d];
+      un[side] = u;
+      for (int d = 0; d < dim; d++) vt[side][d] = Wpp[side][1 + d] - u * nrm[d];
+    }
+    /* 4. Riemann problem */
+    const double WLr[3] = {Wpp[0][0], un[0], Wpp[0][dim + 1]};
+    const double WRr[3] = {Wpp[1][0], un[1], Wpp[1][dim + 1]};
+    double out[6];
+    int it = 0;
+    const int st = ora_riemann(gamma, WLr, WRr, tol, maxit, out, &it);
+    counters[2] += it;
+    if (st < 0) {
+      counters[3]++;
+      rc = -1;
+    }
+    if (st == 1) counters[1]++;
+    const double rhoF = out[0], uF = out[1], PF = out[2];
+    const int up = (out[5] > 0.5) ? 1 : 0;
+    /* 5. back to the lab frame and the flux of the moving face */
+    double vlab[3], v2 = 0.0, vn = 0.0;
+    for (int d = 0; d < dim; d++) {
+      vlab[d] = uF * nrm[d] + vt[up][d] + w[d];
+      v2 += vlab[d] * vlab[d];
+      vn += vlab[d] * nrm[d];
+    }
+    double* Fk = F + k * nv;
+    Fk[0] = rhoF * uF;
+    for (int d = 0; d < dim; d++) Fk[1 + d] = rhoF * vlab[d] * uF + PF * nrm[d];
+    Fk[dim + 1] = (0.5 * rhoF * v2 + PF / (gamma - 1.0)) * uF + PF * vn;
+  }
+  free(wface);
+  return rc;
+}
+
+/* ------------------------------------------------- A8: conservative update
+ * Eq. (eqnupdate): Q_i^{n+1} = Q_i^n - dt sum_j A_ij F_ij, where the flux
+ * F_ij leaves cell i through face (i,j); with the face normal pointing from
+ * L to R that is +F for the left cell and -F for the right cell. */
+void ora_update(int dim, long n, const double* Q, long nf, const int32_t* cells, const double* area,
+                const double* F, double dt, double* Qnew) {
+  const int nv = dim + 2;
+  incidence I = build_incidence(n, nf, cells);
+  for (long i = 0; i < n; i++) {
+    double sum[NV_MAX] = {0, 0, 0, 0, 0};
+    for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+      const long k = I.face[q];
+      const double sgn = (I.side[q] == 0) ? 1.0 : -1.0;
+      for (int v = 0; v < nv; v++) sum[v] += sgn * area[k] * F[k * nv + v];
+    }
+    for (int v = 0; v < nv; v++) Qnew[i * nv + v] = Q[i * nv + v] - dt * sum[v];
+  }
+  free_incidence(&I);
+}
+
+/* ------------------------------------------------ A9: conservation sums */
+void ora_totals(int dim, long n, const double* Q, double* tot) {
+  const int nv = dim + 2;
+  for (int v = 0; v < nv; v++) tot[v] = 0.0;
+  for (long i = 0; i < n; i++)
+    for (int v = 0; v < nv; v++) tot[v] += Q[i * nv + v];
+}
+
+/* ---------------------------------------------------- A10: generator drift
+ * Sec. 3, step 8: r_i <- r_i + w_i dt, wrapped back into the box. */
+void ora_drift(int dim, long n, double* gen, const double* wmesh, const double* box, double dt) {
+  for (long i = 0; i < n; i++)
+    for (int d = 0; d < dim; d++) {
+      double x = gen[i * dim + d] + wmesh[i * dim + d] * dt;
+      x = fmod(x, box[d]);
+      if (x < 0.0) x += box[d];
+      if (x >= box[d]) x -= box[d];
+      gen[i * dim + d] = x;
+    }
+}
+
+/* ------------------------------------------------------- one whole step
+ * Sec. 3, steps 2-7 on a given tessellation: primitives, gradients and
+ * limiter, mesh velocities (mode 0 static, 1 w = v, 2 the given wmesh),
+ * the time step (dt <= 0 means dt = CFL condition with coefficient cfl),
+ * fluxes and the conservative update.  V, s are taken from ora_geometry.
+ * Outputs Qnew; dt_used; counters as in ora_fluxes. */
+int ora_step(int dim, long n, const double* gen, long nf, const int32_t* cells, const int8_t* shift,
+             const double* area, const double* cen, const double* box, const double* V, const double* s,
+             const double* Q, double gamma, int mode, const double* wmesh_in, double dt, double cfl, int limit,
+             double tol, int maxit, double* Qnew, double* dt_used, int64_t* counters) {
+  const int nv = dim + 2;
+  double* W = (double*)malloc(sizeof(double) * (size_t)(n * nv));
+  double* grad = (double*)malloc(sizeof(double) * (size_t)(n * nv * dim));
+  double* wm = (double*)malloc(sizeof(double) * (size_t)(n * dim));
+  double* F = (double*)malloc(sizeof(double) * (size_t)(nf * nv + 1));
+  ora_primitives(dim, n, Q, V, gamma, W);
+  ora_gradients(dim, n, W, gen, V, s, nf, cells, shift, area, cen, box, limit, grad);
+  for (long i = 0; i < n; i++)
+    for (int d = 0; d < dim; d++)
+      wm[i * dim + d] = (mode == 0) ? 0.0 : (mode == 1) ? W[i * nv + 1 + d] : wmesh_in[i * dim + d];
+  if (!(dt > 0.0)) dt = ora_timestep(dim, n, W, V, wm, gamma, cfl, NULL);
+  *dt_used = dt;
+  for (int c = 0; c < 4; c++) counters[c] = 0;
+  const int rc = ora_fluxes(dim, n, W, grad, gen, s, wm, nf, cells, shift, area, cen, box, gamma, dt, tol, maxit,
+                            F, counters);
+  ora_update(dim, n, Q, nf, cells, area, F, dt, Qnew);
+  free(W);
+  free(grad);
+  free(wm);
+  free(F);
+  return rc;
+}

@@ -1,0 +1,24 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def turb16():
+    from harness import ics
+    return ics.turbulent_3d(16, seed=2)
+
+
+@pytest.fixture(scope="session")
+def sod_small():
+    from harness import ics
+    return ics.sod_2d(32, 16, seed=1)
