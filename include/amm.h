@@ -1,0 +1,182 @@
+/*
+ * amm.h -- C ABI of the GB300 moving-mesh hydro library (libamm.so).
+ *
+ * One second-order unsplit Godunov (MUSCL-Hancock) update of the ideal-gas
+ * Euler equations on a given Voronoi tessellation, after Springel (2010),
+ * "E pur si muove", Sec. 3: primitives, Voronoi gradients and slope limiter,
+ * face velocities, the per-face flux in the frame of the moving face with an
+ * exact Riemann solver, the conservative cell update, and the global Courant
+ * time step (Sec. 7.1).  The tessellation is an input.
+ *
+ * Conventions shared by every call
+ *  - Face k joins the left cell L = face_cells[2k] and the right cell
+ *    R = face_cells[2k+1].  The right cell's generator is taken in its periodic
+ *    image r_R + face_shift[k] * box (face_shift in box lengths, per axis), the
+ *    face normal points from L to R, and face_centroid[k] is given in the left
+ *    cell's frame.
+ *  - Cell states are conserved totals Q_i = (m, p_1..p_dim, E) (Sec. 3, the
+ *    integrals of rho, rho v and rho e over the cell), row-major [n][dim+2],
+ *    FP64.  Primitives are W_i = (rho, v_1..v_dim, P).
+ *  - Every pointer argument is a HOST pointer unless the name ends in _device.
+ *    The library copies what it needs; the caller keeps ownership of all
+ *    arrays it passes.
+ *  - Every call returns an amm_status (0 = AMM_OK, negative = error).  Nothing
+ *    aborts, traps or throws across the ABI.  amm_last_error() describes the
+ *    most recent error of a context.
+ *  - Work is queued on the context's CUDA stream and runs asynchronously;
+ *    calls that return data to the host (amm_get_*, amm_timestep, amm_sync)
+ *    synchronise that stream first.  Numeric problems found on the device
+ *    (a Newton solve that hit its cap, a cell whose pressure or mass became
+ *    non-positive) are reported as AMM_ERR_NUMERIC by the next synchronising
+ *    call, with counts in amm_stats.
+ *  - One context per stream; a context is not thread-safe.
+ */
+#ifndef AMM_H
+#define AMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMM_OK = 0,
+  AMM_ERR_INVALID_ARG = -1,        /* bad sizes, indices, pointers or options */
+  AMM_ERR_OPEN_CELL = -2,          /* a cell is not closed: |sum_faces A n| > 1e-9 sum A, or V <= 0 */
+  AMM_ERR_NONPOSITIVE_STATE = -3,  /* an input cell has m <= 0 or P <= 0 */
+  AMM_ERR_CUDA = -4,               /* a CUDA runtime call failed (no device, out of memory, ...) */
+  AMM_ERR_NUMERIC = -5,            /* device-side numeric failure; see amm_stats */
+  AMM_ERR_NOT_READY = -6,          /* a prerequisite is missing (e.g. no proposal weights loaded) */
+  AMM_ERR_TIMEOUT = -7             /* a bounded device-side wait ran out */
+} amm_status;
+
+typedef enum {
+  AMM_FP64 = 0,          /* every step in FP64 */
+  AMM_FP32 = 1,          /* FP32 bulk arithmetic; FP64 accumulation, Newton guard and sums */
+  AMM_FP32_LEARNED = 2   /* AMM_FP32 with the learned p* proposal as the Newton start */
+} amm_precision;
+
+typedef enum {
+  AMM_EULERIAN = 0,      /* w_i = 0: static mesh */
+  AMM_LAGRANGIAN = 1,    /* w_i = v_i, eq. (eqnvelmesh) */
+  AMM_EXPLICIT_W = 2     /* w_i given by amm_set_mesh_velocity */
+} amm_mesh_motion;
+
+typedef struct amm_options {
+  int precision;            /* amm_precision */
+  int mesh_motion;          /* amm_mesh_motion */
+  int limiter;              /* 1: slope limiter of Sec. 3.1 on; 0: unlimited gradients */
+  int max_iter;             /* Newton iteration cap (default 64); hitting it is AMM_ERR_NUMERIC */
+  double riemann_tol;       /* relative Newton tolerance 2|dp|/(p_new+p_old); <= 0 picks
+                               1e-12 for AMM_FP64 and 1e-6 for the FP32 forms */
+  void* stream;             /* cudaStream_t to run on; NULL: the context creates its own */
+  int64_t n_boxes;          /* independent periodic boxes in one context (ensemble), >= 1 */
+  const int64_t* box_cells; /* [n_boxes+1] cell offsets of each box; NULL when n_boxes == 1 */
+  const int64_t* box_faces; /* [n_boxes+1] face offsets of each box; NULL when n_boxes == 1 */
+} amm_options;
+
+typedef struct amm_stats {
+  int64_t steps;             /* updates applied since the last reset */
+  int64_t faces;             /* face fluxes computed */
+  int64_t newton_iters;      /* total Newton iterations */
+  int64_t newton_fail;       /* faces whose Newton solve hit max_iter */
+  int64_t fallback_faces;    /* faces whose extrapolated state was not positive (first order used) */
+  int64_t vacuum_faces;      /* faces whose Riemann problem generated vacuum */
+  int64_t guard_faces;       /* FP32 forms: faces whose Newton solve finished in FP64 */
+  int64_t nonpositive_cells; /* cells left with m <= 0 or P <= 0 by an update */
+  int32_t newton_max;        /* largest iteration count on one face */
+  uint32_t status;           /* bit 0 Newton cap, bit 1 non-positive cell, bit 2 wait timeout */
+  int64_t newton_hist[16];   /* faces by Newton iteration count 0..14, 15 and more */
+} amm_stats;
+
+typedef struct amm_ctx amm_ctx;
+
+/* Fills *opt with the defaults: FP64, Lagrangian, limiter on, max_iter 64,
+ * tolerance by precision, own stream, one box. */
+void amm_default_options(amm_options* opt);
+
+/* Creates a context for one tessellation (Sec. 3, step 1 done by the caller).
+ *   dim            2 or 3
+ *   n_cells        cells (= generators), all boxes together
+ *   generators     [n_cells][dim] positions, inside [0, box) of their box
+ *   n_faces        faces, all boxes together
+ *   face_cells     [n_faces][2] left, right cell (global indices, same box)
+ *   face_shift     [n_faces][dim] periodic image of the right cell, box lengths
+ *   face_area      [n_faces] area (length in 2D), >= 0
+ *   face_centroid  [n_faces][dim] centroid in the left cell's frame
+ *   box            [n_boxes][dim] periodic box lengths
+ *   cell_Q         [n_cells][dim+2] conserved totals
+ *   gamma          adiabatic index, > 1
+ *   opt            options; NULL for defaults
+ * Derives on the device the cell volumes and centres of mass from the
+ * pyramid sums of Sec. 2.3, the per-face geometry and the cell->face lists,
+ * and validates the input.  Errors: AMM_ERR_INVALID_ARG, AMM_ERR_OPEN_CELL,
+ * AMM_ERR_NONPOSITIVE_STATE, AMM_ERR_CUDA; *out is NULL on error. */
+int amm_create(amm_ctx** out, int dim, int64_t n_cells, const double* generators, int64_t n_faces,
+               const int32_t* face_cells, const int8_t* face_shift, const double* face_area,
+               const double* face_centroid, const double* box, const double* cell_Q, double gamma,
+               const amm_options* opt);
+
+/* Releases all device memory of the context.  NULL is accepted. */
+int amm_destroy(amm_ctx* ctx);
+
+/* Message of the last error on this context (never NULL). */
+const char* amm_last_error(const amm_ctx* ctx);
+
+/* Replaces the cell states; host [n_cells][dim+2] or device (same layout).
+ * Checks m > 0 and P > 0 (AMM_ERR_NONPOSITIVE_STATE).  Used for
+ * checkpoint/resume: a resumed run is bitwise identical to an uninterrupted one. */
+int amm_set_state(amm_ctx* ctx, const double* Q);
+int amm_set_state_device(amm_ctx* ctx, const double* Q_device);
+
+/* Mesh-generator velocities for AMM_EXPLICIT_W, host [n_cells][dim] (Sec. 3.2). */
+int amm_set_mesh_velocity(amm_ctx* ctx, const double* w);
+
+/* Sec. 3, step 3: primitives, Voronoi gradients (eq. eqngrad2) and the slope
+ * limiter for the current state; also the per-box Courant minimum used by
+ * amm_timestep.  Queued on the stream. */
+int amm_gradients(amm_ctx* ctx);
+
+/* Sec. 7.1, eq. (EqnTiStep): dt_out[b] = cfl * min_i R_i / (c_i + |v_i - w_i|)
+ * over the cells of box b; host array of n_boxes.  Runs amm_gradients first if
+ * the gradients are stale.  Synchronises. */
+int amm_timestep(amm_ctx* ctx, double cfl, double* dt_out);
+
+/* Sec. 3, steps 6-7: face velocities, fluxes, conservative update with time
+ * step dt (every box), then the primitives of the new state and the
+ * conservation sums.  Runs amm_gradients first if the gradients are stale. */
+int amm_step(amm_ctx* ctx, double dt);
+/* Same with one time step per box, host [n_boxes]. */
+int amm_step_boxes(amm_ctx* ctx, const double* dt);
+
+/* nsteps complete steps (gradients, Courant step with coefficient cfl per box,
+ * fluxes, update), the time step staying on the device; replayed from a
+ * captured CUDA graph when use_graph != 0.  Does not synchronise. */
+int amm_advance(amm_ctx* ctx, double cfl, int64_t nsteps, int use_graph);
+
+/* A10 (Sec. 3, step 8): moves the stored generators by w_i * dt (wrapped into
+ * the box) for the caller's next tessellation. */
+int amm_drift(amm_ctx* ctx, double dt);
+
+/* Waits for queued work; returns AMM_ERR_NUMERIC if the device flagged a
+ * numeric failure since the last reset, AMM_ERR_TIMEOUT for a timed-out wait. */
+int amm_sync(amm_ctx* ctx);
+
+/* Getters (synchronise).  Host arrays sized as documented. */
+int amm_get_state(amm_ctx* ctx, double* Q);                 /* [n_cells][dim+2] */
+int amm_get_state_device(amm_ctx* ctx, double* Q_device);   /* [n_cells][dim+2], device */
+int amm_get_primitives(amm_ctx* ctx, double* W);            /* [n_cells][dim+2] */
+int amm_get_gradients(amm_ctx* ctx, double* grad);          /* [n_cells][dim+2][dim], limited */
+int amm_get_face_flux(amm_ctx* ctx, double* AF);            /* [n_faces][dim+2], area times flux of the last step */
+int amm_get_geometry(amm_ctx* ctx, double* V, double* s);   /* [n_cells], [n_cells][dim] (s absolute) */
+int amm_get_totals(amm_ctx* ctx, double* tot);              /* [n_boxes][dim+2], FP64 sums after the last step */
+int amm_get_dt(amm_ctx* ctx, double* dt);                   /* [n_boxes], time step of the last step */
+int amm_get_generators(amm_ctx* ctx, double* gen);          /* [n_cells][dim] */
+int amm_get_stats(amm_ctx* ctx, amm_stats* stats);
+int amm_reset_stats(amm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMM_H */

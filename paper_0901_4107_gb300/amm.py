@@ -1,0 +1,306 @@
+"""Thin ctypes binding of libamm (include/amm.h).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  The functions carry the C names; arrays are numpy (host) or,
+for the *_device calls, integer device addresses (e.g. torch.Tensor.data_ptr()).
+Errors raise AmmError with the library's status code and message.  If the
+shared library has not been built this module raises on first use -- there
+is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+AMM_OK = 0
+AMM_ERR_INVALID_ARG = -1
+AMM_ERR_OPEN_CELL = -2
+AMM_ERR_NONPOSITIVE_STATE = -3
+AMM_ERR_CUDA = -4
+AMM_ERR_NUMERIC = -5
+AMM_ERR_NOT_READY = -6
+AMM_ERR_TIMEOUT = -7
+
+AMM_FP64, AMM_FP32, AMM_FP32_LEARNED = 0, 1, 2
+AMM_EULERIAN, AMM_LAGRANGIAN, AMM_EXPLICIT_W = 0, 1, 2
+
+PRECISIONS = {"fp64": AMM_FP64, "fp32": AMM_FP32, "fp32_learned": AMM_FP32_LEARNED}
+MOTIONS = {"eulerian": AMM_EULERIAN, "lagrangian": AMM_LAGRANGIAN, "explicit": AMM_EXPLICIT_W}
+
+
+class AmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libamm status %d: %s" % (code, msg))
+        self.code = code
+
+
+class amm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mesh_motion", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("riemann_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("n_boxes", ctypes.c_int64), ("box_cells", ctypes.POINTER(ctypes.c_int64)),
+                ("box_faces", ctypes.POINTER(ctypes.c_int64))]
+
+
+class amm_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("faces", ctypes.c_int64), ("newton_iters", ctypes.c_int64),
+                ("newton_fail", ctypes.c_int64), ("fallback_faces", ctypes.c_int64),
+                ("vacuum_faces", ctypes.c_int64), ("guard_faces", ctypes.c_int64),
+                ("nonpositive_cells", ctypes.c_int64), ("newton_max", ctypes.c_int32), ("status", ctypes.c_uint32),
+                ("newton_hist", ctypes.c_int64 * 16)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+_SIGS = {
+    "amm_default_options": (None, [_P]),
+    "amm_last_error": (ctypes.c_char_p, [_P]),
+    "amm_create": (_I, [ctypes.POINTER(_P), _I, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _D, _P]),
+    "amm_destroy": (_I, [_P]),
+    "amm_set_state": (_I, [_P, _P]),
+    "amm_set_state_device": (_I, [_P, _P]),
+    "amm_set_mesh_velocity": (_I, [_P, _P]),
+    "amm_gradients": (_I, [_P]),
+    "amm_timestep": (_I, [_P, _D, _P]),
+    "amm_step": (_I, [_P, _D]),
+    "amm_step_boxes": (_I, [_P, _P]),
+    "amm_advance": (_I, [_P, _D, _I64, _I]),
+    "amm_drift": (_I, [_P, _D]),
+    "amm_sync": (_I, [_P]),
+    "amm_get_state": (_I, [_P, _P]),
+    "amm_get_state_device": (_I, [_P, _P]),
+    "amm_get_primitives": (_I, [_P, _P]),
+    "amm_get_gradients": (_I, [_P, _P]),
+    "amm_get_face_flux": (_I, [_P, _P]),
+    "amm_get_geometry": (_I, [_P, _P, _P]),
+    "amm_get_totals": (_I, [_P, _P]),
+    "amm_get_dt": (_I, [_P, _P]),
+    "amm_get_generators": (_I, [_P, _P]),
+    "amm_get_stats": (_I, [_P, _P]),
+    "amm_reset_stats": (_I, [_P]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads libamm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libamm.so is not built (%s); run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class Context:
+    """Owns an amm_ctx*; remembers dim, sizes and boxes for the getters."""
+
+    def __init__(self, handle, dim, n, nf, nboxes):
+        self.handle = handle
+        self.dim, self.n, self.nf, self.nboxes = dim, n, nf, nboxes
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().amm_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _check(ctx, rc):
+    if rc != AMM_OK:
+        h = ctx.handle if isinstance(ctx, Context) else ctx
+        msg = lib().amm_last_error(h).decode() if h else ""
+        raise AmmError(rc, msg)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True, max_iter=64, riemann_tol=0.0,
+                        stream=None):
+    o = amm_options()
+    lib().amm_default_options(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.mesh_motion = MOTIONS[mesh_motion] if isinstance(mesh_motion, str) else int(mesh_motion)
+    o.limiter = int(bool(limiter))
+    o.max_iter = int(max_iter)
+    o.riemann_tol = float(riemann_tol)
+    o.stream = stream
+    return o
+
+
+def amm_create(dim, generators, face_cells, face_shift, face_area, face_centroid, box, cell_Q, gamma, opt=None,
+               box_cells=None, box_faces=None):
+    """Creates a context; `box` is [dim] or [n_boxes, dim]; with several boxes
+    pass the cell and face offsets ([n_boxes+1] each)."""
+    gen = _arr(generators, np.float64)
+    cells = _arr(face_cells, np.int32)
+    shift = _arr(face_shift, np.int8)
+    area = _arr(face_area, np.float64)
+    cen = _arr(face_centroid, np.float64)
+    boxa = _arr(box, np.float64).reshape(-1, dim)
+    Q = _arr(cell_Q, np.float64)
+    n, nf = gen.shape[0], area.shape[0]
+    if opt is None:
+        opt = amm_default_options()
+    keep = []
+    if boxa.shape[0] > 1:
+        bc = _arr(box_cells, np.int64)
+        bf = _arr(box_faces, np.int64)
+        keep += [bc, bf]
+        opt.n_boxes = boxa.shape[0]
+        opt.box_cells = bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        opt.box_faces = bf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    else:
+        opt.n_boxes = 1
+    h = ctypes.c_void_p()
+    rc = lib().amm_create(ctypes.byref(h), dim, n, gen.ctypes.data, nf, cells.ctypes.data, shift.ctypes.data,
+                          area.ctypes.data, cen.ctypes.data, boxa.ctypes.data, Q.ctypes.data, float(gamma),
+                          ctypes.byref(opt))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_create failed (details on stderr)")
+    return Context(h, dim, n, nf, boxa.shape[0])
+
+
+def amm_destroy(ctx):
+    if ctx.handle:
+        lib().amm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def amm_set_state(ctx, Q):
+    Q = _arr(Q, np.float64)
+    assert Q.shape == (ctx.n, ctx.dim + 2)
+    _check(ctx, lib().amm_set_state(ctx.handle, Q.ctypes.data))
+
+
+def amm_set_state_device(ctx, q_ptr):
+    _check(ctx, lib().amm_set_state_device(ctx.handle, ctypes.c_void_p(int(q_ptr))))
+
+
+def amm_set_mesh_velocity(ctx, w):
+    w = _arr(w, np.float64)
+    assert w.shape == (ctx.n, ctx.dim)
+    _check(ctx, lib().amm_set_mesh_velocity(ctx.handle, w.ctypes.data))
+
+
+def amm_gradients(ctx):
+    _check(ctx, lib().amm_gradients(ctx.handle))
+
+
+def amm_timestep(ctx, cfl):
+    out = np.empty(ctx.nboxes)
+    _check(ctx, lib().amm_timestep(ctx.handle, float(cfl), out.ctypes.data))
+    return out
+
+
+def amm_step(ctx, dt):
+    _check(ctx, lib().amm_step(ctx.handle, float(dt)))
+
+
+def amm_step_boxes(ctx, dt):
+    dt = _arr(dt, np.float64)
+    assert dt.shape == (ctx.nboxes,)
+    _check(ctx, lib().amm_step_boxes(ctx.handle, dt.ctypes.data))
+
+
+def amm_advance(ctx, cfl, nsteps=1, use_graph=True):
+    _check(ctx, lib().amm_advance(ctx.handle, float(cfl), int(nsteps), int(bool(use_graph))))
+
+
+def amm_drift(ctx, dt):
+    _check(ctx, lib().amm_drift(ctx.handle, float(dt)))
+
+
+def amm_sync(ctx):
+    _check(ctx, lib().amm_sync(ctx.handle))
+
+
+def amm_get_state(ctx, out=None):
+    Q = np.empty((ctx.n, ctx.dim + 2)) if out is None else out
+    _check(ctx, lib().amm_get_state(ctx.handle, Q.ctypes.data))
+    return Q
+
+
+def amm_get_state_device(ctx, q_ptr):
+    _check(ctx, lib().amm_get_state_device(ctx.handle, ctypes.c_void_p(int(q_ptr))))
+
+
+def amm_get_primitives(ctx):
+    W = np.empty((ctx.n, ctx.dim + 2))
+    _check(ctx, lib().amm_get_primitives(ctx.handle, W.ctypes.data))
+    return W
+
+
+def amm_get_gradients(ctx):
+    g = np.empty((ctx.n, ctx.dim + 2, ctx.dim))
+    _check(ctx, lib().amm_get_gradients(ctx.handle, g.ctypes.data))
+    return g
+
+
+def amm_get_face_flux(ctx):
+    F = np.empty((ctx.nf, ctx.dim + 2))
+    _check(ctx, lib().amm_get_face_flux(ctx.handle, F.ctypes.data))
+    return F
+
+
+def amm_get_geometry(ctx):
+    V = np.empty(ctx.n)
+    s = np.empty((ctx.n, ctx.dim))
+    _check(ctx, lib().amm_get_geometry(ctx.handle, V.ctypes.data, s.ctypes.data))
+    return V, s
+
+
+def amm_get_totals(ctx):
+    t = np.empty((ctx.nboxes, ctx.dim + 2))
+    _check(ctx, lib().amm_get_totals(ctx.handle, t.ctypes.data))
+    return t
+
+
+def amm_get_dt(ctx):
+    d = np.empty(ctx.nboxes)
+    _check(ctx, lib().amm_get_dt(ctx.handle, d.ctypes.data))
+    return d
+
+
+def amm_get_generators(ctx):
+    g = np.empty((ctx.n, ctx.dim))
+    _check(ctx, lib().amm_get_generators(ctx.handle, g.ctypes.data))
+    return g
+
+
+def amm_get_stats(ctx):
+    s = amm_stats()
+    _check(ctx, lib().amm_get_stats(ctx.handle, ctypes.byref(s)))
+    d = {f: getattr(s, f) for f, _ in amm_stats._fields_ if f != "newton_hist"}
+    d["newton_hist"] = list(s.newton_hist)
+    return d
+
+
+def amm_reset_stats(ctx):
+    _check(ctx, lib().amm_reset_stats(ctx.handle))
+
+
+def create_from_mesh(mesh, Q, gamma, precision="fp64", mesh_motion="lagrangian", **kw):
+    """Convenience: a context from any object with dim, points, cells, shift,
+    area, centroid and box attributes (e.g. a host tessellation)."""
+    opt = amm_default_options(precision, mesh_motion, **kw)
+    return amm_create(mesh.dim, mesh.points, mesh.cells, mesh.shift, mesh.area, mesh.centroid, mesh.box, Q, gamma,
+                      opt)

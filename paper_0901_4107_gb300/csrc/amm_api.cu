@@ -1,0 +1,655 @@
+// C ABI of libamm (declared in include/amm.h): context creation and
+// validation, the per-step call sequence, CUDA-graph capture of a whole step,
+// and the getters.  Host code only; kernels live in geometry.cu and
+// hydro_f{32,64}.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amm_internal.cuh"
+
+using amm::R4;
+using amm::Tile;
+
+namespace {
+
+int fail(amm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(amm_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, AMM_ERR_CUDA, m);
+}
+
+#define CU(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+void free_ctx(amm_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
+                  c->ftiles, c->box_first_ctile, c->fgeo, c->cgeo64, c->W,   c->P,       c->grad,
+                  c->wmesh, c->flux,    c->fluxE,   c->cour_bits, c->dt_box, c->dt_used, c->partial,
+                  c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->cgeo && c->cgeo != (void*)c->cgeo64) cudaFree(c->cgeo);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  delete c;
+}
+
+template <typename F64, typename F32>
+cudaError_t dispatch(amm_ctx* c, F64 f64, F32 f32) {
+  return c->is_fp64() ? f64() : f32();
+}
+
+cudaError_t ensure_scratch(amm_ctx* c, size_t doubles) {
+  if (c->scratch_size >= doubles) return cudaSuccess;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_size = 0;
+  cudaError_t e = cudaMalloc((void**)&c->scratch, sizeof(double) * doubles);
+  if (e == cudaSuccess) c->scratch_size = doubles;
+  return e;
+}
+
+cudaError_t run_gradients(amm_ctx* c) {
+  return dispatch(c, [&] { return amm::launch_gradients<double>(c); }, [&] { return amm::launch_gradients<float>(c); });
+}
+
+// the step after the gradients: flux, update, totals; cfl > 0 takes the
+// time step from the Courant minimum on the device, cfl == 0 from dt_box
+cudaError_t run_step_tail(amm_ctx* c, double cfl) {
+  cudaError_t e = dispatch(c, [&] { return amm::launch_flux<double>(c, cfl); },
+                           [&] { return amm::launch_flux<float>(c, cfl); });
+  if (e != cudaSuccess) return e;
+  e = dispatch(c, [&] { return amm::launch_update<double>(c, cfl); }, [&] { return amm::launch_update<float>(c, cfl); });
+  if (e != cudaSuccess) return e;
+  return dispatch(c, [&] { return amm::launch_finish<double>(c, cfl); },
+                  [&] { return amm::launch_finish<float>(c, cfl); });
+}
+
+int check_status(amm_ctx* c) {
+  amm::DeviceStats s;
+  cudaError_t e = cudaMemcpy(&s, c->stats, sizeof(s), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+  if (s.status & amm::ST_TIMEOUT) return fail(c, AMM_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (s.status & (amm::ST_NEWTON_CAP | amm::ST_NONPOS)) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "numeric failure: %llu Newton solves hit the cap, %llu cells non-positive",
+             (unsigned long long)s.newton_fail, (unsigned long long)s.nonpos);
+    return fail(c, AMM_ERR_NUMERIC, buf);
+  }
+  return AMM_OK;
+}
+
+bool finite_all(const double* a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void amm_default_options(amm_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = AMM_FP64;
+  o->mesh_motion = AMM_LAGRANGIAN;
+  o->limiter = 1;
+  o->max_iter = 64;
+  o->riemann_tol = 0.0;
+  o->stream = nullptr;
+  o->n_boxes = 1;
+  o->box_cells = nullptr;
+  o->box_faces = nullptr;
+}
+
+const char* amm_last_error(const amm_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf, const int32_t* cells,
+               const int8_t* shift, const double* area, const double* cen, const double* box, const double* Q,
+               double gamma, const amm_options* opt_in) {
+  amm_ctx* c = nullptr;
+  if (!out) return AMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  amm_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else
+    amm_default_options(&opt);
+  if (dim != 2 && dim != 3) return AMM_ERR_INVALID_ARG;
+  if (n < 2 || n > (int64_t)1 << 30 || nf < 1 || nf > ((int64_t)1 << 30) - 1) return AMM_ERR_INVALID_ARG;
+  if (!gen || !cells || !shift || !area || !cen || !box || !Q) return AMM_ERR_INVALID_ARG;
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return AMM_ERR_INVALID_ARG;
+  if (opt.precision < AMM_FP64 || opt.precision > AMM_FP32_LEARNED) return AMM_ERR_INVALID_ARG;
+  if (opt.mesh_motion < AMM_EULERIAN || opt.mesh_motion > AMM_EXPLICIT_W) return AMM_ERR_INVALID_ARG;
+  if (opt.max_iter < 1 || opt.max_iter > 10000) return AMM_ERR_INVALID_ARG;
+  if (opt.n_boxes < 1 || opt.n_boxes > (1 << 20)) return AMM_ERR_INVALID_ARG;
+  if (!(opt.riemann_tol > 0.0)) opt.riemann_tol = (opt.precision == AMM_FP64) ? 1e-12 : 1e-6;
+  const int nb = (int)opt.n_boxes;
+  std::vector<int64_t> bc(nb + 1), bf(nb + 1);
+  if (nb == 1) {
+    bc[0] = 0; bc[1] = n; bf[0] = 0; bf[1] = nf;
+  } else {
+    if (!opt.box_cells || !opt.box_faces) return AMM_ERR_INVALID_ARG;
+    for (int b = 0; b <= nb; b++) {
+      bc[b] = opt.box_cells[b];
+      bf[b] = opt.box_faces[b];
+    }
+    if (bc[0] != 0 || bc[nb] != n || bf[0] != 0 || bf[nb] != nf) return AMM_ERR_INVALID_ARG;
+    for (int b = 0; b < nb; b++)
+      if (bc[b + 1] <= bc[b] + 1 || bf[b + 1] <= bf[b]) return AMM_ERR_INVALID_ARG;
+  }
+  const int nv = dim + 2;
+  // host validation of the mesh and the state
+  if (!finite_all(gen, (size_t)n * dim) || !finite_all(area, (size_t)nf) || !finite_all(cen, (size_t)nf * dim) ||
+      !finite_all(Q, (size_t)n * nv) || !finite_all(box, (size_t)nb * dim))
+    return AMM_ERR_INVALID_ARG;
+  for (int b = 0; b < nb; b++) {
+    for (int d = 0; d < dim; d++)
+      if (!(box[b * dim + d] > 0.0)) return AMM_ERR_INVALID_ARG;
+    for (int64_t i = bc[b]; i < bc[b + 1]; i++)
+      for (int d = 0; d < dim; d++) {
+        const double x = gen[i * dim + d];
+        if (!(x >= 0.0 && x < box[b * dim + d])) return AMM_ERR_INVALID_ARG;
+      }
+    for (int64_t k = bf[b]; k < bf[b + 1]; k++) {
+      const int64_t L = cells[2 * k], R = cells[2 * k + 1];
+      if (L < bc[b] || L >= bc[b + 1] || R < bc[b] || R >= bc[b + 1]) return AMM_ERR_INVALID_ARG;
+      if (!(area[k] >= 0.0)) return AMM_ERR_INVALID_ARG;
+      bool zero = true;
+      for (int d = 0; d < dim; d++) zero &= shift[k * dim + d] == 0;
+      if (L == R && zero) return AMM_ERR_INVALID_ARG;
+    }
+  }
+  for (int64_t i = 0; i < n; i++)
+    if (!(Q[i * nv] > 0.0)) return AMM_ERR_NONPOSITIVE_STATE;
+
+  c = new amm_ctx();
+  c->dim = dim;
+  c->n = n;
+  c->nf = nf;
+  c->nboxes = nb;
+  c->gamma = gamma;
+  c->opt = opt;
+  c->box_cells = bc;
+  c->box_faces = bf;
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) {
+    int rc = cuda_fail(c, e0, "cudaGetDevice");
+    fprintf(stderr, "amm_create: %s\n", c->err.c_str());
+    free_ctx(c);
+    return rc;
+  }
+  auto bail = [&](int rc) {
+    // keep the message on stderr: the context is gone
+    if (rc != AMM_OK) fprintf(stderr, "amm_create: %s\n", c->err.c_str());
+    free_ctx(c);
+    return rc;
+  };
+#define CUB(call)                                    \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, #call)); \
+  } while (0)
+  if (opt.stream) {
+    c->stream = (cudaStream_t)opt.stream;
+  } else {
+    CUB(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  CUB(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+  c->opt.stream = c->stream;
+
+  // cell -> (face, side) lists in face order (counting sort)
+  std::vector<int> off(n + 1, 0);
+  for (int64_t k = 0; k < nf; k++) {
+    off[cells[2 * k] + 1]++;
+    off[cells[2 * k + 1] + 1]++;
+  }
+  for (int64_t i = 0; i < n; i++) off[i + 1] += off[i];
+  std::vector<int2> csr(2 * nf);
+  {
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int64_t k = 0; k < nf; k++) {
+      const int L = cells[2 * k], R = cells[2 * k + 1];
+      csr[fill[L]++] = make_int2((int)(k << 1), R);
+      csr[fill[R]++] = make_int2((int)((k << 1) | 1), L);
+    }
+  }
+  for (int64_t i = 0; i < n; i++)
+    if (off[i + 1] == off[i]) return bail(fail(c, AMM_ERR_OPEN_CELL, "a cell has no faces"));
+  // tiles
+  std::vector<Tile> ct, ft;
+  std::vector<int> bfc(nb + 1, 0);
+  for (int b = 0; b < nb; b++) {
+    bfc[b] = (int)ct.size();
+    for (int64_t s = bc[b]; s < bc[b + 1]; s += amm::CELL_TILE)
+      ct.push_back(Tile{b, (int)s, (int)std::min<int64_t>(s + amm::CELL_TILE, bc[b + 1]), 0});
+    for (int64_t s = bf[b]; s < bf[b + 1]; s += amm::FACE_TILE)
+      ft.push_back(Tile{b, (int)s, (int)std::min<int64_t>(s + amm::FACE_TILE, bf[b + 1]), 0});
+  }
+  bfc[nb] = (int)ct.size();
+  c->n_ctiles = (int)ct.size();
+  c->n_ftiles = (int)ft.size();
+  c->box_first_ctile_h = bfc;
+  // padded 3-vectors
+  std::vector<double> gen3((size_t)n * 3, 0.0), cen3((size_t)nf * 3, 0.0), box3((size_t)nb * 3, 1.0);
+  std::vector<int8_t> sh3((size_t)nf * 3, 0);
+  for (int64_t i = 0; i < n; i++)
+    for (int d = 0; d < dim; d++) gen3[i * 3 + d] = gen[i * dim + d];
+  for (int64_t k = 0; k < nf; k++)
+    for (int d = 0; d < dim; d++) {
+      cen3[k * 3 + d] = cen[k * dim + d];
+      sh3[k * 3 + d] = shift[k * dim + d];
+    }
+  for (int b = 0; b < nb; b++)
+    for (int d = 0; d < dim; d++) box3[b * 3 + d] = box[b * dim + d];
+  c->box_h = box3;
+
+  const size_t rs = c->real_size();
+  CUB(dalloc(&c->gen, (size_t)n * 3));
+  CUB(dalloc(&c->box, (size_t)nb * 3));
+  CUB(dalloc(&c->Q, (size_t)n * 5));
+  CUB(dalloc(&c->lr, (size_t)nf));
+  CUB(dalloc(&c->csr_off, (size_t)n + 1));
+  CUB(dalloc(&c->csr, (size_t)2 * nf));
+  CUB(dalloc(&c->ctiles, ct.size()));
+  CUB(dalloc(&c->ftiles, ft.size()));
+  CUB(dalloc(&c->box_first_ctile, (size_t)nb + 1));
+  CUB(cudaMalloc(&c->fgeo, rs * 4 * 2 * (size_t)nf));
+  CUB(dalloc(&c->cgeo64, (size_t)n));
+  if (c->is_fp64())
+    c->cgeo = c->cgeo64;
+  else
+    CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
+  CUB(cudaMalloc(&c->W, rs * 4 * (size_t)n));
+  CUB(cudaMalloc(&c->P, rs * (size_t)n));
+  CUB(cudaMalloc(&c->grad, rs * 16 * (size_t)n));
+  if (opt.mesh_motion == AMM_EXPLICIT_W) {
+    CUB(cudaMalloc(&c->wmesh, rs * 4 * (size_t)n));
+    CUB(cudaMemsetAsync(c->wmesh, 0, rs * 4 * (size_t)n, c->stream));
+  }
+  CUB(cudaMalloc(&c->flux, rs * 4 * (size_t)nf));
+  CUB(cudaMalloc(&c->fluxE, rs * (size_t)nf));
+  CUB(dalloc(&c->cour_bits, (size_t)nb));
+  CUB(dalloc(&c->dt_box, (size_t)nb));
+  CUB(dalloc(&c->dt_used, (size_t)nb));
+  CUB(dalloc(&c->partial, (size_t)5 * ct.size()));
+  CUB(dalloc(&c->totals, (size_t)5 * nb));
+  CUB(dalloc(&c->stats, 1));
+  CUB(dalloc(&c->closure, (size_t)n));
+  CUB(dalloc(&c->counter, 4));
+  CUB(cudaMemsetAsync(c->stats, 0, sizeof(amm::DeviceStats), c->stream));
+  CUB(cudaMemsetAsync(c->dt_box, 0, sizeof(double) * nb, c->stream));
+  CUB(cudaMemsetAsync(c->dt_used, 0, sizeof(double) * nb, c->stream));
+  CUB(cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * nb, c->stream));
+  CUB(cudaMemsetAsync(c->flux, 0, rs * 4 * (size_t)nf, c->stream));
+  CUB(cudaMemsetAsync(c->fluxE, 0, rs * (size_t)nf, c->stream));
+  CUB(cudaMemcpyAsync(c->gen, gen3.data(), sizeof(double) * gen3.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->box, box3.data(), sizeof(double) * box3.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->lr, cells, sizeof(int2) * (size_t)nf, cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->csr_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->csr, csr.data(), sizeof(int2) * csr.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->ctiles, ct.data(), sizeof(Tile) * ct.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->ftiles, ft.data(), sizeof(Tile) * ft.size(), cudaMemcpyHostToDevice, c->stream));
+  CUB(cudaMemcpyAsync(c->box_first_ctile, bfc.data(), sizeof(int) * bfc.size(), cudaMemcpyHostToDevice, c->stream));
+  // face inputs through scratch: area [nf], centroid [nf][3], shift [nf][3]
+  {
+    double* d_area = nullptr;
+    double* d_cen = nullptr;
+    int8_t* d_sh = nullptr;
+    CUB(dalloc(&d_area, (size_t)nf));
+    CUB(dalloc(&d_cen, (size_t)nf * 3));
+    CUB(dalloc(&d_sh, (size_t)nf * 3));
+    CUB(cudaMemcpyAsync(d_area, area, sizeof(double) * nf, cudaMemcpyHostToDevice, c->stream));
+    CUB(cudaMemcpyAsync(d_cen, cen3.data(), sizeof(double) * cen3.size(), cudaMemcpyHostToDevice, c->stream));
+    CUB(cudaMemcpyAsync(d_sh, sh3.data(), sh3.size(), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t eg = amm::launch_face_geometry(c, d_area, d_cen, d_sh);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d_area);
+    cudaFree(d_cen);
+    cudaFree(d_sh);
+    if (eg != cudaSuccess) return bail(cuda_fail(c, eg, "face/cell geometry"));
+  }
+  // closure and volume checks
+  {
+    std::vector<float> clo(n);
+    std::vector<R4<double>> cg(n);
+    CUB(cudaMemcpy(clo.data(), c->closure, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    CUB(cudaMemcpy(cg.data(), c->cgeo64, sizeof(R4<double>) * n, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; i++) {
+      if (!(cg[i].x > 0.0)) return bail(fail(c, AMM_ERR_OPEN_CELL, "cell " + std::to_string(i) + " has volume <= 0"));
+      if (!(clo[i] <= 1e-9f))
+        return bail(fail(c, AMM_ERR_OPEN_CELL, "cell " + std::to_string(i) + " is not closed (relative closure " +
+                                                   std::to_string(clo[i]) + ")"));
+    }
+  }
+  *out = c;
+  const int rc = amm_set_state(c, Q);
+  if (rc != AMM_OK) {
+    *out = nullptr;
+    return bail(rc);
+  }
+#undef CUB
+  return AMM_OK;
+}
+
+int amm_destroy(amm_ctx* c) {
+  if (!c) return AMM_OK;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  return AMM_OK;
+}
+
+static int set_state_common(amm_ctx* c, const double* Qdev_aos) {
+  CU(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), c->stream));
+  CU(dispatch(c, [&] { return amm::launch_set_state<double>(c, Qdev_aos, c->counter); },
+              [&] { return amm::launch_set_state<float>(c, Qdev_aos, c->counter); }));
+  unsigned long long bad = 0;
+  CU(cudaMemcpyAsync(&bad, c->counter, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->grads_fresh = false;
+  c->totals_fresh = false;
+  if (bad) return fail(c, AMM_ERR_NONPOSITIVE_STATE, std::to_string(bad) + " cells with m <= 0 or P <= 0");
+  return AMM_OK;
+}
+
+int amm_set_state(amm_ctx* c, const double* Q) {
+  if (!c || !Q) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  const size_t cnt = (size_t)c->n * (c->dim + 2);
+  CU(ensure_scratch(c, cnt));
+  CU(cudaMemcpyAsync(c->scratch, Q, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream));
+  return set_state_common(c, c->scratch);
+}
+
+int amm_set_state_device(amm_ctx* c, const double* Qd) {
+  if (!c || !Qd) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  return set_state_common(c, Qd);
+}
+
+int amm_set_mesh_velocity(amm_ctx* c, const double* w) {
+  if (!c || !w) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (c->opt.mesh_motion != AMM_EXPLICIT_W) return fail(c, AMM_ERR_INVALID_ARG, "mesh motion is not explicit");
+  const size_t cnt = (size_t)c->n * c->dim;
+  if (!finite_all(w, cnt)) return fail(c, AMM_ERR_INVALID_ARG, "non-finite mesh velocity");
+  CU(ensure_scratch(c, std::max(cnt, (size_t)c->n * (c->dim + 2))));
+  CU(cudaMemcpyAsync(c->scratch, w, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream));
+  CU(dispatch(c, [&] { return amm::launch_set_wmesh<double>(c, c->scratch); },
+              [&] { return amm::launch_set_wmesh<float>(c, c->scratch); }));
+  CU(cudaStreamSynchronize(c->stream));
+  c->grads_fresh = false;
+  return AMM_OK;
+}
+
+int amm_gradients(amm_ctx* c) {
+  if (!c) return AMM_ERR_INVALID_ARG;
+  CU(run_gradients(c));
+  c->grads_fresh = true;
+  return AMM_OK;
+}
+
+int amm_timestep(amm_ctx* c, double cfl, double* dt_out) {
+  if (!c || !dt_out || !(cfl > 0.0)) return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
+  if (!c->grads_fresh) {
+    CU(run_gradients(c));
+    c->grads_fresh = true;
+  }
+  std::vector<unsigned long long> bits(c->nboxes);
+  CU(cudaMemcpyAsync(bits.data(), c->cour_bits, sizeof(unsigned long long) * c->nboxes, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < c->nboxes; b++) {
+    double t;
+    std::memcpy(&t, &bits[b], sizeof t);
+    dt_out[b] = cfl * t;
+  }
+  return AMM_OK;
+}
+
+static int step_with_dt_box(amm_ctx* c) {
+  if (!c->grads_fresh) CU(run_gradients(c));
+  CU(run_step_tail(c, 0.0));
+  c->grads_fresh = false;
+  c->totals_fresh = true;
+  c->have_step = true;
+  return AMM_OK;
+}
+
+int amm_step(amm_ctx* c, double dt) {
+  if (!c || !(dt >= 0.0) || !std::isfinite(dt)) return fail(c, AMM_ERR_INVALID_ARG, "bad time step");
+  std::vector<double> d(c->nboxes, dt);
+  CU(cudaMemcpyAsync(c->dt_box, d.data(), sizeof(double) * c->nboxes, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+  return step_with_dt_box(c);
+}
+
+int amm_step_boxes(amm_ctx* c, const double* dt) {
+  if (!c || !dt) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  for (int b = 0; b < c->nboxes; b++)
+    if (!(dt[b] >= 0.0) || !std::isfinite(dt[b])) return fail(c, AMM_ERR_INVALID_ARG, "bad time step");
+  CU(cudaMemcpyAsync(c->dt_box, dt, sizeof(double) * c->nboxes, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return step_with_dt_box(c);
+}
+
+int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
+  if (!c || !(cfl > 0.0) || nsteps < 0) return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
+  if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
+    return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
+  if (nsteps == 0) return AMM_OK;
+  if (!use_graph) {
+    for (int64_t s = 0; s < nsteps; s++) {
+      CU(run_gradients(c));
+      CU(run_step_tail(c, cfl));
+    }
+  } else {
+    if (!c->graph || c->graph_cfl != cfl) {
+      if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+      }
+      // capture one whole step on the auxiliary stream
+      CU(cudaStreamSynchronize(c->stream));
+      cudaStream_t keep = c->stream;
+      c->stream = c->aux_stream;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = run_gradients(c);
+        if (e1 == cudaSuccess) e1 = run_step_tail(c, cfl);
+        e = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = e1;
+      }
+      c->stream = keep;
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "step graph capture");
+      }
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+      c->graph_cfl = cfl;
+    }
+    for (int64_t s = 0; s < nsteps; s++) CU(cudaGraphLaunch(c->graph, c->stream));
+  }
+  c->grads_fresh = false;
+  c->totals_fresh = true;
+  c->have_step = true;
+  return AMM_OK;
+}
+
+int amm_drift(amm_ctx* c, double dt) {
+  if (!c || !std::isfinite(dt)) return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
+  CU(amm::launch_drift(c, dt));
+  return AMM_OK;
+}
+
+int amm_sync(amm_ctx* c) {
+  if (!c) return AMM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+int amm_get_state(amm_ctx* c, double* Q) {
+  if (!c || !Q) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  const size_t cnt = (size_t)c->n * (c->dim + 2);
+  CU(ensure_scratch(c, cnt));
+  CU(dispatch(c, [&] { return amm::launch_get_state<double>(c, c->scratch); },
+              [&] { return amm::launch_get_state<float>(c, c->scratch); }));
+  CU(cudaMemcpyAsync(Q, c->scratch, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+int amm_get_state_device(amm_ctx* c, double* Qd) {
+  if (!c || !Qd) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  CU(dispatch(c, [&] { return amm::launch_get_state<double>(c, Qd); },
+              [&] { return amm::launch_get_state<float>(c, Qd); }));
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+int amm_get_primitives(amm_ctx* c, double* W) {
+  if (!c || !W) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  const size_t cnt = (size_t)c->n * (c->dim + 2);
+  CU(ensure_scratch(c, cnt));
+  CU(dispatch(c, [&] { return amm::launch_get_primitives<double>(c, c->scratch); },
+              [&] { return amm::launch_get_primitives<float>(c, c->scratch); }));
+  CU(cudaMemcpyAsync(W, c->scratch, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_get_gradients(amm_ctx* c, double* g) {
+  if (!c || !g) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->grads_fresh) {
+    CU(run_gradients(c));
+    c->grads_fresh = true;
+  }
+  const size_t cnt = (size_t)c->n * (c->dim + 2) * c->dim;
+  CU(ensure_scratch(c, cnt));
+  CU(dispatch(c, [&] { return amm::launch_get_gradients<double>(c, c->scratch); },
+              [&] { return amm::launch_get_gradients<float>(c, c->scratch); }));
+  CU(cudaMemcpyAsync(g, c->scratch, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_get_face_flux(amm_ctx* c, double* F) {
+  if (!c || !F) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  const size_t cnt = (size_t)c->nf * (c->dim + 2);
+  CU(ensure_scratch(c, cnt));
+  CU(dispatch(c, [&] { return amm::launch_get_flux<double>(c, c->scratch); },
+              [&] { return amm::launch_get_flux<float>(c, c->scratch); }));
+  CU(cudaMemcpyAsync(F, c->scratch, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_get_geometry(amm_ctx* c, double* V, double* s) {
+  if (!c || !V || !s) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  std::vector<R4<double>> cg(c->n);
+  std::vector<double> g3((size_t)c->n * 3);
+  CU(cudaMemcpyAsync(cg.data(), c->cgeo64, sizeof(R4<double>) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(g3.data(), c->gen, sizeof(double) * g3.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < c->n; i++) {
+    V[i] = cg[i].x;
+    const double ds[3] = {cg[i].y, cg[i].z, cg[i].w};
+    for (int d = 0; d < c->dim; d++) s[i * c->dim + d] = g3[i * 3 + d] + ds[d];
+  }
+  return AMM_OK;
+}
+
+int amm_get_totals(amm_ctx* c, double* tot) {
+  if (!c || !tot) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->totals_fresh) {
+    CU(dispatch(c, [&] { return amm::launch_finish<double>(c, -1.0); },
+                [&] { return amm::launch_finish<float>(c, -1.0); }));
+    c->totals_fresh = true;
+  }
+  std::vector<double> t((size_t)5 * c->nboxes);
+  CU(cudaMemcpyAsync(t.data(), c->totals, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const int nv = c->dim + 2;
+  for (int b = 0; b < c->nboxes; b++) {
+    tot[b * nv] = t[5 * b];
+    tot[b * nv + 1] = t[5 * b + 1];
+    tot[b * nv + 2] = t[5 * b + 2];
+    if (c->dim == 3) tot[b * nv + 3] = t[5 * b + 3];
+    tot[b * nv + c->dim + 1] = t[5 * b + 4];
+  }
+  return AMM_OK;
+}
+
+int amm_get_dt(amm_ctx* c, double* dt) {
+  if (!c || !dt) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  CU(cudaMemcpyAsync(dt, c->dt_used, sizeof(double) * c->nboxes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_get_generators(amm_ctx* c, double* gen) {
+  if (!c || !gen) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  std::vector<double> g3((size_t)c->n * 3);
+  CU(cudaMemcpyAsync(g3.data(), c->gen, sizeof(double) * g3.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < c->n; i++)
+    for (int d = 0; d < c->dim; d++) gen[i * c->dim + d] = g3[i * 3 + d];
+  return AMM_OK;
+}
+
+int amm_get_stats(amm_ctx* c, amm_stats* s) {
+  if (!c || !s) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  amm::DeviceStats d;
+  CU(cudaMemcpyAsync(&d, c->stats, sizeof(d), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  std::memset(s, 0, sizeof(*s));
+  s->steps = (int64_t)d.steps;
+  s->faces = (int64_t)d.faces;
+  s->newton_iters = (int64_t)d.newton_iters;
+  s->newton_fail = (int64_t)d.newton_fail;
+  s->fallback_faces = (int64_t)d.fallback;
+  s->vacuum_faces = (int64_t)d.vacuum;
+  s->guard_faces = (int64_t)d.guard;
+  s->nonpositive_cells = (int64_t)d.nonpos;
+  s->newton_max = (int32_t)d.newton_max;
+  s->status = d.status;
+  for (int b = 0; b < 16; b++) s->newton_hist[b] = (int64_t)d.hist[b];
+  return AMM_OK;
+}
+
+int amm_reset_stats(amm_ctx* c) {
+  if (!c) return AMM_ERR_INVALID_ARG;
+  CU(cudaMemsetAsync(c->stats, 0, sizeof(amm::DeviceStats), c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// Internal definitions shared by the library's translation units: the
+// context, the device data layout and the kernel launchers.
+//
+// Device layout (structure of arrays; "real" is double for the FP64 form and
+// float for the FP32 forms; vectors are always 3-component, z = 0 in 2D):
+//   per cell   Q      double, 5 planes of n: m, px, py, pz, E
+//              W      R4<real> {rho, vx, vy, vz}       P  real
+//              grad   4 x R4<real>: {d rho (xyz), dP/dx}, {d vx, dP/dy},
+//                                   {d vy, dP/dz}, {d vz, 0}
+//              cgeo   R4<real> {V, s - r}   cgeo64: R4<double> copy
+//              wmesh  R4<real> {wx, wy, wz, 0} (explicit mesh velocity only)
+//   per face   lr     int2 {L, R}
+//              fgeo   2 x R4<real>: {n (unit, L->R), |r_R - r_L|}, {c = f - m, A}
+//              flux   R4<real> {A F_m, A F_px, A F_py, A F_pz}, fluxE real A F_E
+//   cell->face csr_off int [n+1], csr int2 {face << 1 | side, neighbour}
+//              (side 0: the cell is the face's left cell), in face order.
+//   tiles      contiguous cell / face ranges, each inside one box; one CTA
+//              processes one tile, so per-box reductions never straddle boxes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "amm.h"
+
+namespace amm {
+
+template <typename real>
+struct alignas(4 * sizeof(real)) R4 {
+  real x, y, z, w;
+};
+
+constexpr int CELL_TILE = 256;   // cells per CTA
+constexpr int FACE_TILE = 256;   // faces per CTA
+
+struct Tile {
+  int box;
+  int begin;
+  int end;
+  int pad;
+};
+
+enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u };
+
+struct DeviceStats {
+  unsigned long long steps, faces, newton_iters, newton_fail, fallback, vacuum, guard, nonpos;
+  unsigned int newton_max, status;
+  unsigned long long hist[16];
+};
+
+struct Gas {
+  double gamma;
+};
+
+// Kernel-side view of a context for one precision.
+template <typename real>
+struct HydroView {
+  int dim, mode, limit, maxit, nboxes;
+  int n, nf;
+  double gamma, tol;
+  // dt source: dt_box[b] if cfl <= 0, else cfl * courant_min[b]
+  double cfl;
+  const double* dt_box;
+  double* dt_used;
+  unsigned long long* cour_bits;
+  double* Q;                  // 5 planes of n
+  R4<real>* W;
+  real* P;
+  R4<real>* grad;
+  const R4<real>* wmesh;
+  const R4<real>* cgeo;
+  const R4<double>* cgeo64;
+  const int2* lr;
+  const R4<real>* fgeo;
+  R4<real>* flux;
+  real* fluxE;
+  const int* csr_off;
+  const int2* csr;
+  const Tile* ctiles;
+  const Tile* ftiles;
+  double* partial;            // [n_ctiles][5]
+  double* totals;             // [nboxes][5]
+  const int* box_first_ctile; // [nboxes+1]
+  DeviceStats* stats;
+  // learned proposal (FP32 learned form only)
+  const void* mlp;
+};
+
+}  // namespace amm
+
+struct amm_ctx {
+  int dim = 0;
+  int64_t n = 0, nf = 0;
+  int nboxes = 1;
+  double gamma = 1.4;
+  amm_options opt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // graph capture
+  bool own_stream = false;
+  std::string err;
+  std::vector<int64_t> box_cells, box_faces;
+  std::vector<double> box_h;       // [nboxes][3]
+  int n_ctiles = 0, n_ftiles = 0;
+  std::vector<int> box_first_ctile_h;
+  // device memory
+  double* gen = nullptr;           // [n][3]
+  double* box = nullptr;           // [nboxes][3]
+  double* Q = nullptr;             // [5][n]
+  int2* lr = nullptr;
+  int* csr_off = nullptr;
+  int2* csr = nullptr;
+  amm::Tile* ctiles = nullptr;
+  amm::Tile* ftiles = nullptr;
+  int* box_first_ctile = nullptr;
+  int* cell_box = nullptr;         // [n] (drift only)
+  void* fgeo = nullptr;            // [nf][2] R4<real>
+  void* cgeo = nullptr;            // [n] R4<real>
+  amm::R4<double>* cgeo64 = nullptr;
+  void* W = nullptr;
+  void* P = nullptr;
+  void* grad = nullptr;
+  void* wmesh = nullptr;
+  void* flux = nullptr;
+  void* fluxE = nullptr;
+  unsigned long long* cour_bits = nullptr;
+  double* dt_box = nullptr;
+  double* dt_used = nullptr;
+  double* partial = nullptr;
+  double* totals = nullptr;
+  amm::DeviceStats* stats = nullptr;
+  float* closure = nullptr;        // [n] relative closure error (creation only)
+  void* mlp = nullptr;             // device copy of the proposal weights
+  bool mlp_loaded = false;
+  double* scratch = nullptr;       // layout conversions for getters/setters
+  size_t scratch_size = 0;         // in doubles
+  unsigned long long* counter = nullptr;
+  bool grads_fresh = false;
+  bool totals_fresh = false;
+  bool have_step = false;
+  // captured step graph
+  cudaGraphExec_t graph = nullptr;
+  double graph_cfl = -1.0;
+  bool is_fp64() const { return opt.precision == AMM_FP64; }
+  size_t real_size() const { return is_fp64() ? 8 : 4; }
+};
+
+namespace amm {
+
+// geometry.cu
+cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* cen, const int8_t* shift_d3);
+cudaError_t launch_cell_geometry(amm_ctx* c);
+cudaError_t launch_drift(amm_ctx* c, double dt);
+
+// hydro_f64.cu / hydro_f32.cu
+template <typename real>
+HydroView<real> make_view(amm_ctx* c, double cfl);
+template <typename real>
+cudaError_t launch_primitives(amm_ctx* c);
+template <typename real>
+cudaError_t launch_gradients(amm_ctx* c);
+template <typename real>
+cudaError_t launch_flux(amm_ctx* c, double cfl);
+template <typename real>
+cudaError_t launch_update(amm_ctx* c, double cfl);
+template <typename real>
+cudaError_t launch_finish(amm_ctx* c, double cfl);
+template <typename real>
+cudaError_t launch_set_state(amm_ctx* c, const double* Q_aos_device, unsigned long long* bad_count);
+template <typename real>
+cudaError_t launch_get_state(amm_ctx* c, double* Q_aos_device);
+template <typename real>
+cudaError_t launch_get_primitives(amm_ctx* c, double* W_aos_device);
+template <typename real>
+cudaError_t launch_get_gradients(amm_ctx* c, double* g_device);
+template <typename real>
+cudaError_t launch_get_flux(amm_ctx* c, double* F_device);
+template <typename real>
+cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
+
+}  // namespace amm

@@ -1,0 +1,299 @@
+// Exact Riemann solver for the ideal gas, device side (Sec. 3.3: exact
+// solver with a treatment of vacuum; the mathematics is that of the 1D Euler
+// Riemann problem).
+//
+// The star pressure p* is the root of
+//   f(p) = f_L(p) + f_R(p) + (u_R - u_L),
+//   f_K(p) = (p - p_K) sqrt(A_K / (p + B_K))                      p > p_K (shock)
+//          = 2 c_K / (gamma-1) ((p/p_K)^z - 1),  z=(gamma-1)/(2gamma)  p <= p_K (rarefaction)
+//   A_K = 2 / ((gamma+1) rho_K), B_K = (gamma-1)/(gamma+1) p_K,
+// found by Newton's method to the relative change 2|dp|/(p_new+p_old) < tol
+// from a starting value, then sampled at x/t = 0.  The rarefaction derivative
+// uses (p/p_K)^(z-1) = (p/p_K)^z / (p/p_K) so one power serves f and f'.
+// Vacuum generated between two rarefactions (2(c_L+c_R)/(gamma-1) <= u_R-u_L)
+// is handled in closed form; the extrapolated states reaching this solver are
+// always positive (non-positive ones fall back to first order before).
+//
+// FP32 form: the iteration runs in float.  Near vacuum and in strong
+// rarefactions float cannot resolve the relative tolerance (f is a
+// difference of terms ~2c/(gamma-1) that cancel), so once an iterate falls
+// below GUARD * min(p_L, p_R), or the float loop has not converged after
+// FLOAT_ITERS iterations, the solve continues in FP64 (pressure functions,
+// step and convergence test), and the face is counted.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace amm {
+
+template <typename real>
+struct GasC {
+  real g, gm1, gp1;
+  real z;            // (g-1)/(2g)
+  real inv_z;        // 1/z
+  real two_gm1;      // 2/(g-1)
+  real gm1_gp1;      // (g-1)/(g+1)
+  real two_gp1;      // 2/(g+1)
+  real shock_a;      // (g+1)/(2g)
+  real shock_b;      // (g-1)/(2g) = z
+  real inv_g;        // 1/g
+  real fan_rho;      // 2/(g-1)
+  real fan_p;        // 2g/(g-1)
+  real inv_gm1;      // 1/(g-1)
+  __host__ __device__ explicit GasC(double gamma) {
+    g = (real)gamma;
+    gm1 = (real)(gamma - 1.0);
+    gp1 = (real)(gamma + 1.0);
+    z = (real)((gamma - 1.0) / (2.0 * gamma));
+    inv_z = (real)(2.0 * gamma / (gamma - 1.0));
+    two_gm1 = (real)(2.0 / (gamma - 1.0));
+    gm1_gp1 = (real)((gamma - 1.0) / (gamma + 1.0));
+    two_gp1 = (real)(2.0 / (gamma + 1.0));
+    shock_a = (real)((gamma + 1.0) / (2.0 * gamma));
+    shock_b = (real)((gamma - 1.0) / (2.0 * gamma));
+    inv_g = (real)(1.0 / gamma);
+    fan_rho = (real)(2.0 / (gamma - 1.0));
+    fan_p = (real)(2.0 * gamma / (gamma - 1.0));
+    inv_gm1 = (real)(1.0 / (gamma - 1.0));
+  }
+};
+
+__device__ __forceinline__ double xpow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float xpow(float a, float b) { return __powf(a, b); }
+__device__ __forceinline__ double xsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float xsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double xrsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ float xrsqrt(float a) { return rsqrtf(a); }
+
+// f_K(p) and f_K'(p)
+template <typename real>
+__device__ __forceinline__ void wave_curve(real p, real rhoK, real pK, real cK, const GasC<real>& G, real& f,
+                                           real& df) {
+  if (p > pK) {
+    const real A = G.two_gp1 / rhoK;
+    const real B = G.gm1_gp1 * pK;
+    const real q = xsqrt(A / (p + B));
+    f = (p - pK) * q;
+    df = q * ((real)1 - (real)0.5 * (p - pK) / (p + B));
+  } else {
+    const real pr = p / pK;
+    const real prz = xpow(pr, G.z);
+    f = G.two_gm1 * cK * (prz - (real)1);
+    df = prz / (pr * rhoK * cK);
+  }
+}
+
+// Standard starting value: the linearised (primitive-variable) estimate when
+// the pressure ratio is small and it lies between p_L and p_R, else the
+// two-rarefaction estimate when it lies below both, else the two-shock
+// estimate evaluated at the linearised pressure; floored positive.
+template <typename real>
+__device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real cL, real rhoR, real uR, real pR,
+                                               real cR, const GasC<real>& G) {
+  const real du = uR - uL;
+  real ppv = (real)0.5 * (pL + pR) - (real)0.125 * du * (rhoL + rhoR) * (cL + cR);
+  ppv = ppv > (real)0 ? ppv : (real)0;
+  const real pmin = pL < pR ? pL : pR, pmax = pL > pR ? pL : pR;
+  real p0;
+  if (pmax / pmin <= (real)2 && ppv >= pmin && ppv <= pmax) {
+    p0 = ppv;
+  } else if (ppv < pmin) {
+    const real num = cL + cR - (real)0.5 * G.gm1 * du;
+    const real den = cL / xpow(pL, G.z) + cR / xpow(pR, G.z);
+    p0 = xpow(num / den, G.inv_z);
+  } else {
+    const real gL = xsqrt((G.two_gp1 / rhoL) / (ppv + G.gm1_gp1 * pL));
+    const real gR = xsqrt((G.two_gp1 / rhoR) / (ppv + G.gm1_gp1 * pR));
+    p0 = (gL * pL + gR * pR - du) / (gL + gR);
+  }
+  const real pfloor = (real)1e-10 * (real)0.5 * (pL + pR);
+  return (p0 > pfloor) ? p0 : pfloor;
+}
+
+struct RiemannInfo {
+  int iters;
+  int guard;      // finished in FP64
+  int vacuum;
+  int fail;       // hit the iteration cap
+};
+
+// Newton iteration for p*; returns p* in `real`, with the FP64 guard in the
+// FP32 form.  iterations counted in info.
+template <typename real>
+__device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL, real cL, real rhoR, real uR,
+                                             real pR, real cR, const GasC<real>& G, double tol, int maxit,
+                                             RiemannInfo& info) {
+  const real du = uR - uL;
+  int it = 0;
+  bool conv = false;
+  if constexpr (sizeof(real) == 8) {
+    while (it < maxit) {
+      real fL, dL, fR, dR;
+      wave_curve(p, rhoL, pL, cL, G, fL, dL);
+      wave_curve(p, rhoR, pR, cR, G, fR, dR);
+      real pn = p - (fL + fR + du) / (dL + dR);
+      if (!(pn > (real)0)) pn = (real)1e-3 * p;
+      it++;
+      const real ch = (real)2 * fabs(pn - p) / (pn + p);
+      p = pn;
+      if (ch < (real)tol) {
+        conv = true;
+        break;
+      }
+    }
+  } else {
+    constexpr int FLOAT_ITERS = 12;
+    const float guard_p = 1e-3f * (pL < pR ? (float)pL : (float)pR);
+    bool to64 = false;
+    while (it < maxit) {
+      if (it >= FLOAT_ITERS || (float)p < guard_p) {
+        to64 = true;
+        break;
+      }
+      real fL, dL, fR, dR;
+      wave_curve(p, rhoL, pL, cL, G, fL, dL);
+      wave_curve(p, rhoR, pR, cR, G, fR, dR);
+      real pn = p - (fL + fR + du) / (dL + dR);
+      if (!(pn > (real)0)) pn = (real)1e-3 * p;
+      it++;
+      const real ch = (real)2 * fabsf((float)(pn - p)) / (pn + p);
+      p = pn;
+      if (ch < (real)tol) {
+        conv = true;
+        break;
+      }
+    }
+    if (to64) {
+      info.guard = 1;
+      const GasC<double> G64((double)G.g);
+      double pd = (double)p;
+      const double rL = rhoL, uLd = uL, pLd = pL, rR = rhoR, uRd = uR, pRd = pR;
+      const double cLd = sqrt(G64.g * pLd / rL), cRd = sqrt(G64.g * pRd / rR);
+      const double dud = uRd - uLd;
+      while (it < maxit) {
+        double fL, dL, fR, dR;
+        wave_curve(pd, rL, pLd, cLd, G64, fL, dL);
+        wave_curve(pd, rR, pRd, cRd, G64, fR, dR);
+        double pn = pd - (fL + fR + dud) / (dL + dR);
+        if (!(pn > 0.0)) pn = 1e-3 * pd;
+        it++;
+        const double ch = 2.0 * fabs(pn - pd) / (pn + pd);
+        pd = pn;
+        if (ch < tol) {
+          conv = true;
+          break;
+        }
+      }
+      p = (real)pd;
+    }
+  }
+  info.iters = it;
+  info.fail = conv ? 0 : 1;
+  return p;
+}
+
+// Sampled state at x/t = 0 of the Riemann problem (rho, u, p per side).
+// Returns side of the contact (0: left, 1: right) for the transverse
+// velocity; rho = P = 0 inside generated vacuum.
+template <typename real>
+__device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real rhoR, real uR, real pR,
+                                              const GasC<real>& G, double tol, int maxit, bool have_guess,
+                                              real guess, real& rhoF, real& uF, real& pF, RiemannInfo& info) {
+  info.iters = 0;
+  info.guard = 0;
+  info.vacuum = 0;
+  info.fail = 0;
+  const real cL = xsqrt(G.g * pL / rhoL), cR = xsqrt(G.g * pR / rhoR);
+  if (G.two_gm1 * (cL + cR) <= uR - uL) {
+    // two rarefactions with vacuum between them
+    info.vacuum = 1;
+    const real frontL = uL + G.two_gm1 * cL;
+    const real frontR = uR - G.two_gm1 * cR;
+    if ((real)0 <= frontL) {
+      if ((real)0 <= uL - cL) {
+        rhoF = rhoL; uF = uL; pF = pL;
+      } else {
+        const real c = G.two_gp1 * cL + G.gm1_gp1 * uL;
+        const real r = c / cL;
+        uF = c;
+        rhoF = rhoL * xpow(r, G.fan_rho);
+        pF = pL * xpow(r, G.fan_p);
+      }
+      return 0;
+    }
+    if ((real)0 >= frontR) {
+      if ((real)0 >= uR + cR) {
+        rhoF = rhoR; uF = uR; pF = pR;
+      } else {
+        const real c = G.two_gp1 * cR - G.gm1_gp1 * uR;
+        const real r = c / cR;
+        uF = -c;
+        rhoF = rhoR * xpow(r, G.fan_rho);
+        pF = pR * xpow(r, G.fan_p);
+      }
+      return 1;
+    }
+    rhoF = (real)0; uF = (real)0.5 * (frontL + frontR); pF = (real)0;
+    return 0;
+  }
+  real p0 = have_guess ? guess : standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G);
+  const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, maxit, info);
+  real fL, dL, fR, dR;
+  wave_curve(ps, rhoL, pL, cL, G, fL, dL);
+  wave_curve(ps, rhoR, pR, cR, G, fR, dR);
+  const real us = (real)0.5 * (uL + uR) + (real)0.5 * (fR - fL);
+  if ((real)0 <= us) {
+    const real r = ps / pL;
+    if (ps > pL) {
+      const real SL = uL - cL * xsqrt(G.shock_a * r + G.shock_b);
+      if ((real)0 <= SL) {
+        rhoF = rhoL; uF = uL; pF = pL;
+      } else {
+        rhoF = rhoL * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1); uF = us; pF = ps;
+      }
+    } else {
+      if ((real)0 <= uL - cL) {
+        rhoF = rhoL; uF = uL; pF = pL;
+      } else {
+        const real tail = us - cL * xpow(r, G.z);
+        if ((real)0 > tail) {
+          rhoF = rhoL * xpow(r, G.inv_g); uF = us; pF = ps;
+        } else {
+          const real c = G.two_gp1 * cL + G.gm1_gp1 * uL;
+          const real q = c / cL;
+          uF = c;
+          rhoF = rhoL * xpow(q, G.fan_rho);
+          pF = pL * xpow(q, G.fan_p);
+        }
+      }
+    }
+    return 0;
+  }
+  const real r = ps / pR;
+  if (ps > pR) {
+    const real SR = uR + cR * xsqrt(G.shock_a * r + G.shock_b);
+    if ((real)0 >= SR) {
+      rhoF = rhoR; uF = uR; pF = pR;
+    } else {
+      rhoF = rhoR * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1); uF = us; pF = ps;
+    }
+  } else {
+    if ((real)0 >= uR + cR) {
+      rhoF = rhoR; uF = uR; pF = pR;
+    } else {
+      const real tail = us + cR * xpow(r, G.z);
+      if ((real)0 < tail) {
+        rhoF = rhoR * xpow(r, G.inv_g); uF = us; pF = ps;
+      } else {
+        const real c = G.two_gp1 * cR - G.gm1_gp1 * uR;
+        const real q = c / cR;
+        uF = -c;
+        rhoF = rhoR * xpow(q, G.fan_rho);
+        pF = pR * xpow(q, G.fan_p);
+      }
+    }
+  }
+  return 1;
+}
+
+}  // namespace amm
