@@ -176,6 +176,16 @@ int amm_get_generators(amm_ctx* ctx, double* gen);          /* [n_cells][dim] */
 int amm_get_stats(amm_ctx* ctx, amm_stats* stats);
 int amm_reset_stats(amm_ctx* ctx);
 
+/* Per-kernel timing for roofline measurements.  With profiling on, every
+ * step records CUDA events on the context's stream between its kernels (also
+ * inside a captured step graph, as external event nodes);
+ * amm_get_kernel_times waits for the last step and returns the durations in
+ * ms of its four kernel groups: [0] gradients+limiter+Courant, [1] face
+ * fluxes, [2] cell update, [3] totals.  AMM_ERR_NOT_READY when profiling is
+ * off.  Switching profiling re-captures the step graph. */
+int amm_profile(amm_ctx* ctx, int enable);
+int amm_get_kernel_times(amm_ctx* ctx, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libamm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# The FP32 forms take the fast single-precision paths (approximate division
+# and square root, denormals flushed); FP64 code is unaffected by these flags.
+PER_FILE = {"hydro_f32.cu": ["--use_fast_math"]}
 
 
 def nvcc():
@@ -54,7 +57,8 @@ def build(force=False, verbose=False, extra=()):
     for src in _sources():
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmds.append([exe, "-c", src, "-o", obj] + ARCH + FLAGS + list(extra))
+        cmds.append([exe, "-c", src, "-o", obj] + ARCH + FLAGS + PER_FILE.get(os.path.basename(src), []) +
+                    list(extra))
 
     def run(cmd):
         if verbose:

@@ -83,6 +83,8 @@ _SIGS = {
     "amm_get_generators": (_I, [_P, _P]),
     "amm_get_stats": (_I, [_P, _P]),
     "amm_reset_stats": (_I, [_P]),
+    "amm_profile": (_I, [_P, _I]),
+    "amm_get_kernel_times": (_I, [_P, _P]),
 }
 
 
@@ -296,6 +298,19 @@ def amm_get_stats(ctx):
 
 def amm_reset_stats(ctx):
     _check(ctx, lib().amm_reset_stats(ctx.handle))
+
+
+def amm_profile(ctx, enable=True):
+    _check(ctx, lib().amm_profile(ctx.handle, int(bool(enable))))
+
+
+KERNEL_GROUPS = ("gradients", "flux", "update", "finish")
+
+
+def amm_get_kernel_times(ctx):
+    ms = (ctypes.c_float * 4)()
+    _check(ctx, lib().amm_get_kernel_times(ctx.handle, ms))
+    return dict(zip(KERNEL_GROUPS, list(ms)))
 
 
 def create_from_mesh(mesh, Q, gamma, precision="fp64", mesh_motion="lagrangian", **kw):

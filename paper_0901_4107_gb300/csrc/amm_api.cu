@@ -44,13 +44,16 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_ctx(amm_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaEvent_t ev : c->prof_ev)
+    if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
                   c->ftiles, c->box_first_ctile, c->fgeo, c->cgeo64, c->W,   c->P,       c->grad,
                   c->wmesh, c->flux,    c->fluxE,   c->cour_bits, c->dt_box, c->dt_used, c->partial,
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (c->cgeo && c->cgeo != (void*)c->cgeo64) cudaFree(c->cgeo);
+  if (c->cgeo) cudaFree(c->cgeo);
+  if (c->crad) cudaFree(c->crad);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   delete c;
@@ -71,8 +74,21 @@ cudaError_t ensure_scratch(amm_ctx* c, size_t doubles) {
   return e;
 }
 
+cudaError_t mark(amm_ctx* c, int k) {
+  if (!c->profiling) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(c->prof_ev[k], c->stream, cudaEventRecordExternal)
+                                             : cudaEventRecord(c->prof_ev[k], c->stream);
+}
+
 cudaError_t run_gradients(amm_ctx* c) {
-  return dispatch(c, [&] { return amm::launch_gradients<double>(c); }, [&] { return amm::launch_gradients<float>(c); });
+  cudaError_t e = mark(c, 0);
+  if (e != cudaSuccess) return e;
+  e = dispatch(c, [&] { return amm::launch_gradients<double>(c); }, [&] { return amm::launch_gradients<float>(c); });
+  if (e != cudaSuccess) return e;
+  return mark(c, 1);
 }
 
 // the step after the gradients: flux, update, totals; cfl > 0 takes the
@@ -81,10 +97,13 @@ cudaError_t run_step_tail(amm_ctx* c, double cfl) {
   cudaError_t e = dispatch(c, [&] { return amm::launch_flux<double>(c, cfl); },
                            [&] { return amm::launch_flux<float>(c, cfl); });
   if (e != cudaSuccess) return e;
+  if ((e = mark(c, 2)) != cudaSuccess) return e;
   e = dispatch(c, [&] { return amm::launch_update<double>(c, cfl); }, [&] { return amm::launch_update<float>(c, cfl); });
   if (e != cudaSuccess) return e;
-  return dispatch(c, [&] { return amm::launch_finish<double>(c, cfl); },
-                  [&] { return amm::launch_finish<float>(c, cfl); });
+  if ((e = mark(c, 3)) != cudaSuccess) return e;
+  e = dispatch(c, [&] { return amm::launch_finish<double>(c, cfl); }, [&] { return amm::launch_finish<float>(c, cfl); });
+  if (e != cudaSuccess) return e;
+  return mark(c, 4);
 }
 
 int check_status(amm_ctx* c) {
@@ -284,10 +303,8 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   CUB(dalloc(&c->box_first_ctile, (size_t)nb + 1));
   CUB(cudaMalloc(&c->fgeo, rs * 4 * 2 * (size_t)nf));
   CUB(dalloc(&c->cgeo64, (size_t)n));
-  if (c->is_fp64())
-    c->cgeo = c->cgeo64;
-  else
-    CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
+  CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
+  CUB(cudaMalloc(&c->crad, rs * (size_t)n));
   CUB(cudaMalloc(&c->W, rs * 4 * (size_t)n));
   CUB(cudaMalloc(&c->P, rs * (size_t)n));
   CUB(cudaMalloc(&c->grad, rs * 16 * (size_t)n));
@@ -469,7 +486,7 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
       CU(run_step_tail(c, cfl));
     }
   } else {
-    if (!c->graph || c->graph_cfl != cfl) {
+    if (!c->graph || c->graph_cfl != cfl || c->graph_profiled != c->profiling) {
       if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -495,6 +512,7 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
       c->graph_cfl = cfl;
+      c->graph_profiled = c->profiling;
     }
     for (int64_t s = 0; s < nsteps; s++) CU(cudaGraphLaunch(c->graph, c->stream));
   }
@@ -642,6 +660,22 @@ int amm_get_stats(amm_ctx* c, amm_stats* s) {
   s->newton_max = (int32_t)d.newton_max;
   s->status = d.status;
   for (int b = 0; b < 16; b++) s->newton_hist[b] = (int64_t)d.hist[b];
+  return AMM_OK;
+}
+
+int amm_profile(amm_ctx* c, int enable) {
+  if (!c) return AMM_ERR_INVALID_ARG;
+  if (enable && !c->prof_ev[0])
+    for (cudaEvent_t& ev : c->prof_ev) CU(cudaEventCreate(&ev));
+  c->profiling = enable != 0;
+  return AMM_OK;
+}
+
+int amm_get_kernel_times(amm_ctx* c, float* ms) {
+  if (!c || !ms) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->profiling) return fail(c, AMM_ERR_NOT_READY, "profiling is off");
+  CU(cudaEventSynchronize(c->prof_ev[4]));
+  for (int k = 0; k < 4; k++) CU(cudaEventElapsedTime(&ms[k], c->prof_ev[k], c->prof_ev[k + 1]));
   return AMM_OK;
 }
 

@@ -7,7 +7,7 @@
 //              W      R4<real> {rho, vx, vy, vz}       P  real
 //              grad   4 x R4<real>: {d rho (xyz), dP/dx}, {d vx, dP/dy},
 //                                   {d vy, dP/dz}, {d vz, 0}
-//              cgeo   R4<real> {V, s - r}   cgeo64: R4<double> copy
+//              cgeo   R4<real> {1/V, s - r}   crad real R_i   cgeo64 R4<double> {V, s - r}
 //              wmesh  R4<real> {wx, wy, wz, 0} (explicit mesh velocity only)
 //   per face   lr     int2 {L, R}
 //              fgeo   2 x R4<real>: {n (unit, L->R), |r_R - r_L|}, {c = f - m, A}
@@ -51,8 +51,38 @@ struct DeviceStats {
   unsigned long long hist[16];
 };
 
-struct Gas {
-  double gamma;
+// Ideal-gas constants in the bulk arithmetic type, derived once on the host.
+template <typename real>
+struct GasC {
+  real g, gm1, gp1;
+  real z;            // (g-1)/(2g)
+  real inv_z;        // 1/z
+  real two_gm1;      // 2/(g-1)
+  real gm1_gp1;      // (g-1)/(g+1)
+  real two_gp1;      // 2/(g+1)
+  real shock_a;      // (g+1)/(2g)
+  real shock_b;      // (g-1)/(2g) = z
+  real inv_g;        // 1/g
+  real fan_rho;      // 2/(g-1)
+  real fan_p;        // 2g/(g-1)
+  real inv_gm1;      // 1/(g-1)
+  GasC() = default;
+  __host__ __device__ explicit GasC(double gamma) {
+    g = (real)gamma;
+    gm1 = (real)(gamma - 1.0);
+    gp1 = (real)(gamma + 1.0);
+    z = (real)((gamma - 1.0) / (2.0 * gamma));
+    inv_z = (real)(2.0 * gamma / (gamma - 1.0));
+    two_gm1 = (real)(2.0 / (gamma - 1.0));
+    gm1_gp1 = (real)((gamma - 1.0) / (gamma + 1.0));
+    two_gp1 = (real)(2.0 / (gamma + 1.0));
+    shock_a = (real)((gamma + 1.0) / (2.0 * gamma));
+    shock_b = (real)((gamma - 1.0) / (2.0 * gamma));
+    inv_g = (real)(1.0 / gamma);
+    fan_rho = (real)(2.0 / (gamma - 1.0));
+    fan_p = (real)(2.0 * gamma / (gamma - 1.0));
+    inv_gm1 = (real)(1.0 / (gamma - 1.0));
+  }
 };
 
 // Kernel-side view of a context for one precision.
@@ -61,6 +91,7 @@ struct HydroView {
   int dim, mode, limit, maxit, nboxes;
   int n, nf;
   double gamma, tol;
+  GasC<real> gas;
   // dt source: dt_box[b] if cfl <= 0, else cfl * courant_min[b]
   double cfl;
   const double* dt_box;
@@ -71,8 +102,9 @@ struct HydroView {
   real* P;
   R4<real>* grad;
   const R4<real>* wmesh;
-  const R4<real>* cgeo;
-  const R4<double>* cgeo64;
+  const R4<real>* cgeo;        // {1/V, s - r}
+  const real* crad;            // effective radius R_i of eq. (EqnTiStep)
+  const R4<double>* cgeo64;    // {V, s - r} in FP64
   const int2* lr;
   const R4<real>* fgeo;
   R4<real>* flux;
@@ -117,7 +149,8 @@ struct amm_ctx {
   int* box_first_ctile = nullptr;
   int* cell_box = nullptr;         // [n] (drift only)
   void* fgeo = nullptr;            // [nf][2] R4<real>
-  void* cgeo = nullptr;            // [n] R4<real>
+  void* cgeo = nullptr;            // [n] R4<real> {1/V, s - r}
+  void* crad = nullptr;            // [n] real, effective radius
   amm::R4<double>* cgeo64 = nullptr;
   void* W = nullptr;
   void* P = nullptr;
@@ -143,6 +176,10 @@ struct amm_ctx {
   // captured step graph
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0;
+  bool graph_profiled = false;
+  // per-kernel timing: events recorded between the kernels of a step
+  bool profiling = false;
+  cudaEvent_t prof_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool is_fp64() const { return opt.precision == AMM_FP64; }
   size_t real_size() const { return is_fp64() ? 8 : 4; }
 };

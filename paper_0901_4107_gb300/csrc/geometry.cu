@@ -87,6 +87,22 @@ __global__ void k_cast4(const R4<double>* in, R4<real>* out, size_t count) {
   out[i] = b;
 }
 
+// per-cell constants of the bulk type: 1/V, s - r and the effective radius
+// R = (3V/4pi)^(1/3) in 3D, (V/pi)^(1/2) in 2D (eq. EqnTiStep)
+template <typename real>
+__global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad, int n, int dim) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R4<double> a = cg64[i];
+  R4<real> b;
+  b.x = (real)(1.0 / a.x);
+  b.y = (real)a.y;
+  b.z = (real)a.z;
+  b.w = (real)a.w;
+  cg[i] = b;
+  crad[i] = (real)((dim == 3) ? cbrt(3.0 * a.x / (4.0 * M_PI)) : sqrt(a.x / M_PI));
+}
+
 // A10: r_i <- r_i + w_i dt, wrapped into the box; w from the mesh mode
 __global__ void k_drift(const Tile* ctiles, int mode, int precision, double* gen, const double* box,
                         const double* Q, int n, const void* wmesh, double dt) {
@@ -133,9 +149,14 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t nfg = 2 * (size_t)c->nf;
-  if (!c->is_fp64()) {  // the FP64 form reads cgeo64 directly
+  const unsigned nbc = (unsigned)((c->n + 255) / 256);
+  if (c->is_fp64()) {
+    k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad, (int)c->n,
+                                                       c->dim);
+  } else {
     k_cast4<float><<<(unsigned)((nfg + 255) / 256), 256, 0, c->stream>>>(fg64, (R4<float>*)c->fgeo, nfg);
-    k_cast4<float><<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, c->n);
+    k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad, (int)c->n,
+                                                      c->dim);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

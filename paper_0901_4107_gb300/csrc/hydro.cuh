@@ -31,20 +31,32 @@ __device__ __forceinline__ double box_dt(const HydroView<real>& v, int b) {
 }
 
 // ------------------------------------------------------------------ A1
+// Returns P.  The FP32 form keeps only the thermal-energy difference
+// E - |p|^2/(2m) in FP64 (it cancels when the flow is supersonic); the FP64
+// form is FP64 throughout.
 template <typename real>
-__device__ __forceinline__ void prims_from_Q(const HydroView<real>& v, int i, double m, double px, double py,
+__device__ __forceinline__ real prims_from_Q(const HydroView<real>& v, int i, double m, double px, double py,
                                              double pz, double E) {
-  const double V = v.cgeo64[i].x;
-  const double rho = m / V;
-  const double vx = px / m, vy = py / m, vz = pz / m;
-  const double P = (v.gamma - 1.0) * (E / V - 0.5 * rho * (vx * vx + vy * vy + vz * vz));
   R4<real> w;
-  w.x = (real)rho;
-  w.y = (real)vx;
-  w.z = (real)vy;
-  w.w = (real)vz;
+  real P;
+  if constexpr (sizeof(real) == 8) {
+    const double iV = v.cgeo[i].x;
+    const double im = 1.0 / m;
+    const double rho = m * iV;
+    const double vx = px * im, vy = py * im, vz = pz * im;
+    P = (v.gamma - 1.0) * (E * iV - 0.5 * rho * (vx * vx + vy * vy + vz * vz));
+    w.x = rho; w.y = vx; w.z = vy; w.w = vz;
+  } else {
+    const float iV = v.cgeo[i].x;
+    const float mf = (float)m;
+    const float im = 1.0f / mf;
+    const double kin = (px * px + py * py + pz * pz) * (double)(0.5f * im);
+    P = v.gas.gm1 * ((float)(E - kin) * iV);
+    w.x = mf * iV; w.y = (float)px * im; w.z = (float)py * im; w.w = (float)pz * im;
+  }
   v.W[i] = w;
-  v.P[i] = (real)P;
+  v.P[i] = P;
+  return P;
 }
 
 template <typename real>
@@ -53,20 +65,16 @@ __global__ void k_primitives(HydroView<real> v, unsigned long long* bad) {
   if (i >= v.n) return;
   const double m = v.Q[i], px = v.Q[v.n + i], py = v.Q[2 * (size_t)v.n + i], pz = v.Q[3 * (size_t)v.n + i];
   const double E = v.Q[4 * (size_t)v.n + i];
-  prims_from_Q(v, i, m, px, py, pz, E);
-  if (bad) {
-    const double V = v.cgeo64[i].x;
-    const double P = (v.gamma - 1.0) * (E / V - 0.5 * (px * px + py * py + pz * pz) / (m * V));
-    if (!(m > 0.0) || !(P > 0.0)) atomicAdd(bad, 1ull);
-  }
+  const real P = prims_from_Q(v, i, m, px, py, pz, E);
+  if (bad && (!(m > 0.0) || !(P > (real)0))) atomicAdd(bad, 1ull);
 }
 
 // ------------------------------------------------------------ A2+A3+A4
 template <typename real>
-__global__ void __launch_bounds__(CELL_TILE) k_gradients(HydroView<real> v) {
+__global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradients(HydroView<real> v) {
   const Tile t = v.ctiles[blockIdx.x];
   const int i = t.begin + (int)threadIdx.x;
-  double tc = 1.0e300;
+  real tc = (real)3.0e38;
   if (i < t.end) {
     const R4<real> Wi = v.W[i];
     const real phi_i[5] = {Wi.x, Wi.y, Wi.z, Wi.w, v.P[i]};
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(CELL_TILE) k_gradients(HydroView<real> v) {
         mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
       }
     }
-    const real invV = (real)1 / cg.x;
+    const real invV = cg.x;
 #pragma unroll
     for (int a = 0; a < 5; a++) {
       g[a][0] *= invV;
@@ -157,22 +165,25 @@ __global__ void __launch_bounds__(CELL_TILE) k_gradients(HydroView<real> v) {
       wx = wm.x; wy = wm.y; wz = wm.z;
     }
     const real dx = Wi.y - wx, dy = Wi.z - wy, dz = Wi.w - wz;
-    const real cs = xsqrt((real)v.gamma * phi_i[4] / Wi.x);
-    const real R = (v.dim == 3) ? cbrt((real)0.238732414637843 * cg.x) : xsqrt((real)0.318309886183791 * cg.x);
-    tc = (double)(R / (cs + xsqrt(dx * dx + dy * dy + dz * dz)));
+    const real cs = xsqrt(v.gas.g * phi_i[4] / Wi.x);
+    tc = v.crad[i] / (cs + xsqrt(dx * dx + dy * dy + dz * dz));
   }
   // block minimum, then one integer atomic per CTA (positive doubles order
   // like their bit patterns; min is order independent, so this is exact)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tc = fmin(tc, __shfl_xor_sync(0xffffffffu, tc, o));
-  __shared__ double wmin[CELL_TILE / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const real u = __shfl_xor_sync(0xffffffffu, tc, o);
+    tc = u < tc ? u : tc;
+  }
+  __shared__ real wmin[CELL_TILE / 32];
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = tc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = wmin[0];
-    for (int w = 1; w < CELL_TILE / 32; w++) m = fmin(m, wmin[w]);
-    if (m > 0.0 && m < 1.0e300)
-      atomicMin(v.cour_bits + t.box, (unsigned long long)__double_as_longlong(m));
+    real m = wmin[0];
+    for (int w = 1; w < CELL_TILE / 32; w++) m = wmin[w] < m ? wmin[w] : m;
+    const double md = (double)m;
+    if (md > 0.0 && md < 1.0e300)
+      atomicMin(v.cour_bits + t.box, (unsigned long long)__double_as_longlong(md));
   }
 }
 
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(FACE_TILE) k_flux(HydroView<real> v) {
   const int k0 = t.begin + (int)threadIdx.x;
   const bool valid = k0 < t.end;
   const int k = valid ? k0 : t.begin;
-  const GasC<real> G(v.gamma);
+  const GasC<real>& G = v.gas;
   const real hdt = (real)(0.5 * box_dt(v, t.box));
   const int2 lr = v.lr[k];
   const R4<real> G0 = v.fgeo[2 * (size_t)k];
@@ -354,10 +365,8 @@ __global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
       q[a] = v.Q[a * n + i] - dt * acc[a];
       v.Q[a * n + i] = q[a];
     }
-    prims_from_Q(v, i, q[0], q[1], q[2], q[3], q[4]);
-    const double V = v.cgeo64[i].x;
-    const double P = (v.gamma - 1.0) * (q[4] / V - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (q[0] * V));
-    nonpos = (!(q[0] > 0.0) || !(P > 0.0)) ? 1u : 0u;
+    const real P = prims_from_Q(v, i, q[0], q[1], q[2], q[3], q[4]);
+    nonpos = (!(q[0] > 0.0) || !(P > (real)0)) ? 1u : 0u;
   }
   // per-tile FP64 sums in a fixed tree order (bit reproducible)
   __shared__ double red[5][CELL_TILE];
@@ -442,10 +451,8 @@ __global__ void k_set_state(HydroView<real> v, const double* Qa, int dim, unsign
   v.Q[2 * n + i] = py;
   v.Q[3 * n + i] = pz;
   v.Q[4 * n + i] = E;
-  prims_from_Q(v, i, m, px, py, pz, E);
-  const double V = v.cgeo64[i].x;
-  const double P = (v.gamma - 1.0) * (E / V - 0.5 * (px * px + py * py + pz * pz) / (m * V));
-  if (!(m > 0.0) || !(P > 0.0)) atomicAdd(bad, 1ull);
+  const real P = prims_from_Q(v, i, m, px, py, pz, E);
+  if (!(m > 0.0) || !(P > (real)0)) atomicAdd(bad, 1ull);
 }
 
 template <typename real>
@@ -533,6 +540,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.nf = (int)c->nf;
   v.gamma = c->gamma;
   v.tol = c->opt.riemann_tol;
+  v.gas = GasC<real>(c->gamma);
   v.cfl = cfl;
   v.dt_box = c->dt_box;
   v.dt_used = c->dt_used;
@@ -544,6 +552,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.wmesh = (const R4<real>*)c->wmesh;
   v.cgeo = (const R4<real>*)c->cgeo;
   v.cgeo64 = c->cgeo64;
+  v.crad = (const real*)c->crad;
   v.lr = c->lr;
   v.fgeo = (const R4<real>*)c->fgeo;
   v.flux = (R4<real>*)c->flux;

@@ -24,39 +24,10 @@
 
 #include <cuda_runtime.h>
 
+#include "amm_internal.cuh"
+
 namespace amm {
 
-template <typename real>
-struct GasC {
-  real g, gm1, gp1;
-  real z;            // (g-1)/(2g)
-  real inv_z;        // 1/z
-  real two_gm1;      // 2/(g-1)
-  real gm1_gp1;      // (g-1)/(g+1)
-  real two_gp1;      // 2/(g+1)
-  real shock_a;      // (g+1)/(2g)
-  real shock_b;      // (g-1)/(2g) = z
-  real inv_g;        // 1/g
-  real fan_rho;      // 2/(g-1)
-  real fan_p;        // 2g/(g-1)
-  real inv_gm1;      // 1/(g-1)
-  __host__ __device__ explicit GasC(double gamma) {
-    g = (real)gamma;
-    gm1 = (real)(gamma - 1.0);
-    gp1 = (real)(gamma + 1.0);
-    z = (real)((gamma - 1.0) / (2.0 * gamma));
-    inv_z = (real)(2.0 * gamma / (gamma - 1.0));
-    two_gm1 = (real)(2.0 / (gamma - 1.0));
-    gm1_gp1 = (real)((gamma - 1.0) / (gamma + 1.0));
-    two_gp1 = (real)(2.0 / (gamma + 1.0));
-    shock_a = (real)((gamma + 1.0) / (2.0 * gamma));
-    shock_b = (real)((gamma - 1.0) / (2.0 * gamma));
-    inv_g = (real)(1.0 / gamma);
-    fan_rho = (real)(2.0 / (gamma - 1.0));
-    fan_p = (real)(2.0 * gamma / (gamma - 1.0));
-    inv_gm1 = (real)(1.0 / (gamma - 1.0));
-  }
-};
 
 __device__ __forceinline__ double xpow(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float xpow(float a, float b) { return __powf(a, b); }
