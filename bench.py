@@ -296,6 +296,7 @@ def main():
                                     stream=stream.cuda_stream)
 
     ctx32 = make("fp32")
+    tuning = amm.amm_autotune(ctx32, CFL, reps=5)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.05)
@@ -335,7 +336,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": n, "faces": nf, "form": "fp32 (FP64 accumulation and sums)",
                    "l2": "flushed between timed steps (256 MiB write); state reset to the same input",
-                   "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "tuning": tuning},
         "cells_per_s": n * world / (step_ms * 1e-3),
         "roofline": roof,
         "kernels": kern,
@@ -347,6 +349,7 @@ def main():
         forms = {"fp32": {"value": value, "ms_per_step": step_ms, "wall_s": wall32}}
         # FP64 form on the same workload
         ctx64 = make("fp64")
+        amm.amm_autotune(ctx64, CFL, reps=2)
         k64 = max(3, min(args.steps, 200))
         ms64, ker64, wall64 = timed_form(amm, torch, ctx64, Q0d, k64, min(args.warmup, 5), stream, flush)
         forms["fp64"] = {"value": nf / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),

@@ -74,6 +74,10 @@ typedef struct amm_options {
   int64_t n_boxes;          /* independent periodic boxes in one context (ensemble), >= 1 */
   const int64_t* box_cells; /* [n_boxes+1] cell offsets of each box; NULL when n_boxes == 1 */
   const int64_t* box_faces; /* [n_boxes+1] face offsets of each box; NULL when n_boxes == 1 */
+  int fp64_accumulate;      /* FP32 forms only.  0 (default): each cell sums its face fluxes exactly,
+                               as int64 multiples of a per-box, per-component power of two, so the
+                               update conserves exactly and is order independent; 1: sums in FP64
+                               floating point (about 20x slower on GB300's FP64 pipe) */
 } amm_options;
 
 typedef struct amm_stats {
@@ -185,6 +189,26 @@ int amm_reset_stats(amm_ctx* ctx);
  * off.  Switching profiling re-captures the step graph. */
 int amm_profile(amm_ctx* ctx, int enable);
 int amm_get_kernel_times(amm_ctx* ctx, float* ms);
+
+/* Launch shapes.  grad_lanes / update_lanes: consecutive threads that share
+ * one cell in the gradient and update kernels (1, 2, 4 or 8); flux_block:
+ * faces (threads) per CTA of the flux kernel (128 or 256).  Results do not
+ * depend on them except for the FP64 rounding order of sums. */
+typedef struct amm_tuning {
+  int grad_lanes;
+  int update_lanes;
+  int flux_block;
+  float step_ms;   /* amm_autotune: sum of the chosen kernels' median times */
+} amm_tuning;
+
+int amm_set_tuning(amm_ctx* ctx, const amm_tuning* t);
+int amm_get_tuning(amm_ctx* ctx, amm_tuning* t);
+
+/* Times every launch shape on this context's own mesh and state (reps steps
+ * each from the same state, restored afterwards; device events on the
+ * context's stream), keeps the fastest per kernel and returns it in *out
+ * (may be NULL).  Synchronises; allocates one state-sized temporary. */
+int amm_autotune(amm_ctx* ctx, double cfl, int reps, amm_tuning* out);
 
 #ifdef __cplusplus
 }

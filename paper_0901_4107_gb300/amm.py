@@ -40,7 +40,7 @@ class amm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mesh_motion", ctypes.c_int), ("limiter", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("riemann_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("n_boxes", ctypes.c_int64), ("box_cells", ctypes.POINTER(ctypes.c_int64)),
-                ("box_faces", ctypes.POINTER(ctypes.c_int64))]
+                ("box_faces", ctypes.POINTER(ctypes.c_int64)), ("fp64_accumulate", ctypes.c_int)]
 
 
 class amm_stats(ctypes.Structure):
@@ -84,6 +84,9 @@ _SIGS = {
     "amm_get_stats": (_I, [_P, _P]),
     "amm_reset_stats": (_I, [_P]),
     "amm_profile": (_I, [_P, _I]),
+    "amm_set_tuning": (_I, [_P, _P]),
+    "amm_get_tuning": (_I, [_P, _P]),
+    "amm_autotune": (_I, [_P, _D, _I, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
 }
 
@@ -136,7 +139,7 @@ def _arr(a, dtype):
 
 
 def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True, max_iter=64, riemann_tol=0.0,
-                        stream=None):
+                        stream=None, fp64_accumulate=False):
     o = amm_options()
     lib().amm_default_options(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -145,6 +148,7 @@ def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True
     o.max_iter = int(max_iter)
     o.riemann_tol = float(riemann_tol)
     o.stream = stream
+    o.fp64_accumulate = int(bool(fp64_accumulate))
     return o
 
 
@@ -311,6 +315,32 @@ def amm_get_kernel_times(ctx):
     ms = (ctypes.c_float * 4)()
     _check(ctx, lib().amm_get_kernel_times(ctx.handle, ms))
     return dict(zip(KERNEL_GROUPS, list(ms)))
+
+
+class amm_tuning(ctypes.Structure):
+    _fields_ = [("grad_lanes", ctypes.c_int), ("update_lanes", ctypes.c_int), ("flux_block", ctypes.c_int),
+                ("step_ms", ctypes.c_float)]
+
+
+def _tuning_dict(t):
+    return {f: getattr(t, f) for f, _ in amm_tuning._fields_}
+
+
+def amm_set_tuning(ctx, grad_lanes=4, update_lanes=4, flux_block=256):
+    t = amm_tuning(int(grad_lanes), int(update_lanes), int(flux_block), 0.0)
+    _check(ctx, lib().amm_set_tuning(ctx.handle, ctypes.byref(t)))
+
+
+def amm_get_tuning(ctx):
+    t = amm_tuning()
+    _check(ctx, lib().amm_get_tuning(ctx.handle, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def amm_autotune(ctx, cfl=0.3, reps=5):
+    t = amm_tuning()
+    _check(ctx, lib().amm_autotune(ctx.handle, float(cfl), int(reps), ctypes.byref(t)))
+    return _tuning_dict(t)
 
 
 def create_from_mesh(mesh, Q, gamma, precision="fp64", mesh_motion="lagrangian", **kw):

@@ -14,6 +14,8 @@
 //              flux   R4<real> {A F_m, A F_px, A F_py, A F_pz}, fluxE real A F_E
 //   cell->face csr_off int [n+1], csr int2 {face << 1 | side, neighbour}
 //              (side 0: the cell is the face's left cell), in face order.
+//   numbering  cells are renumbered along a Morton curve per box and faces
+//              sorted by their new left cell; cell_perm / face_perm map back
 //   tiles      contiguous cell / face ranges, each inside one box; one CTA
 //              processes one tile, so per-box reductions never straddle boxes.
 #pragma once
@@ -91,7 +93,12 @@ struct HydroView {
   int dim, mode, limit, maxit, nboxes;
   int n, nf;
   double gamma, tol;
+  real tol_r;                  // tol in the bulk type
   GasC<real> gas;
+  int fixed_acc;               // FP32 forms: exact int64 fixed-point flux sums
+  int headroom;                // bits reserved for the incidence count in the fixed-point sums
+  int update_lanes;            // lanes per cell of the update kernel (partial sums per block)
+  unsigned* fmax_bits;         // [nboxes][5] max |A F| per component (float bits) of the step
   // dt source: dt_box[b] if cfl <= 0, else cfl * courant_min[b]
   double cfl;
   const double* dt_box;
@@ -113,6 +120,8 @@ struct HydroView {
   const int2* csr;
   const Tile* ctiles;
   const Tile* ftiles;
+  const int* cell_perm;        // internal -> caller numbering
+  const int* face_perm;
   double* partial;            // [n_ctiles][5]
   double* totals;             // [nboxes][5]
   const int* box_first_ctile; // [nboxes+1]
@@ -147,7 +156,9 @@ struct amm_ctx {
   amm::Tile* ctiles = nullptr;
   amm::Tile* ftiles = nullptr;
   int* box_first_ctile = nullptr;
-  int* cell_box = nullptr;         // [n] (drift only)
+  int* cell_perm = nullptr;        // [n] internal cell -> caller's cell
+  int* face_perm = nullptr;        // [nf] internal face -> caller's face
+  std::vector<int> perm_h;         // host copy of cell_perm
   void* fgeo = nullptr;            // [nf][2] R4<real>
   void* cgeo = nullptr;            // [n] R4<real> {1/V, s - r}
   void* crad = nullptr;            // [n] real, effective radius
@@ -159,6 +170,12 @@ struct amm_ctx {
   void* flux = nullptr;
   void* fluxE = nullptr;
   unsigned long long* cour_bits = nullptr;
+  unsigned* fmax_bits = nullptr;   // [nboxes][5]
+  int headroom = 7;
+  int grad_lanes = 4;              // lanes per cell in the gradient kernel
+  int update_lanes = 4;            // lanes per cell in the update kernel
+  int flux_block = 256;            // threads (faces) per CTA of the flux kernel
+  float tuned_ms = 0.f;
   double* dt_box = nullptr;
   double* dt_used = nullptr;
   double* partial = nullptr;

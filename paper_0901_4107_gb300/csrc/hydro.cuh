@@ -70,93 +70,134 @@ __global__ void k_primitives(HydroView<real> v, unsigned long long* bad) {
 }
 
 // ------------------------------------------------------------ A2+A3+A4
-template <typename real>
+// G consecutive lanes share a cell: lane l takes the cell's incidences l,
+// l+G, ...; partial sums, extrema and limiter minima are combined with
+// butterfly shuffles inside the lane group, so every lane ends with the
+// cell's values and lanes split the gradient store.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+template <int G, typename T>
+__device__ __forceinline__ T group_max(T x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+template <int G, typename T>
+__device__ __forceinline__ T group_min(T x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y < x ? y : x;
+  }
+  return x;
+}
+
+template <typename real, int G>
 __global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradients(HydroView<real> v) {
-  const Tile t = v.ctiles[blockIdx.x];
-  const int i = t.begin + (int)threadIdx.x;
-  real tc = (real)3.0e38;
-  if (i < t.end) {
-    const R4<real> Wi = v.W[i];
-    const real phi_i[5] = {Wi.x, Wi.y, Wi.z, Wi.w, v.P[i]};
-    const R4<real> cg = v.cgeo[i];
-    real g[5][3];
-    real mx[5], mn[5];
+  constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
+  constexpr int UNR = 1;                               // incidences in flight per lane
+  const Tile t = v.ctiles[blockIdx.x / G];
+  const int lane = (int)threadIdx.x % G;
+  const int i = t.begin + (int)(blockIdx.x % G) * CELLS + (int)threadIdx.x / G;
+  const bool valid = i < t.end;
+  const int ii = valid ? i : t.begin;
+  const R4<real> Wi = v.W[ii];
+  const real phi_i[5] = {Wi.x, Wi.y, Wi.z, Wi.w, v.P[ii]};
+  const R4<real> cg = v.cgeo[ii];
+  const int q0 = valid ? v.csr_off[ii] : 0;
+  const int q1 = valid ? v.csr_off[ii + 1] : 0;
+  real g[5][3];
+  real mx[5], mn[5];
+#pragma unroll
+  for (int a = 0; a < 5; a++) {
+    g[a][0] = g[a][1] = g[a][2] = (real)0;
+    mx[a] = mn[a] = phi_i[a];
+  }
+#pragma unroll UNR
+  for (int q = q0 + lane; q < q1; q += G) {
+    const int2 e = v.csr[q];
+    const int k = e.x >> 1;
+    const real sg = (e.x & 1) ? (real)-1 : (real)1;
+    const R4<real> G0 = v.fgeo[2 * (size_t)k];
+    const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
+    const R4<real> Wj = v.W[e.y];
+    const real phi_j[5] = {Wj.x, Wj.y, Wj.z, Wj.w, v.P[e.y]};
+    // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out)
+    const real a_r = G1.w / G0.w;
+    const real a_h = (real)0.5 * G1.w * sg;
 #pragma unroll
     for (int a = 0; a < 5; a++) {
-      g[a][0] = g[a][1] = g[a][2] = (real)0;
-      mx[a] = mn[a] = phi_i[a];
+      const real d = (phi_j[a] - phi_i[a]) * a_r;
+      const real s = (phi_i[a] + phi_j[a]) * a_h;
+      g[a][0] += d * G1.x + s * G0.x;
+      g[a][1] += d * G1.y + s * G0.y;
+      g[a][2] += d * G1.z + s * G0.z;
+      mx[a] = phi_j[a] > mx[a] ? phi_j[a] : mx[a];
+      mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
     }
-    const int q0 = v.csr_off[i], q1 = v.csr_off[i + 1];
-    for (int q = q0; q < q1; q++) {
+  }
+  const real invV = cg.x;
+#pragma unroll
+  for (int a = 0; a < 5; a++) {
+    g[a][0] = group_sum<G>(g[a][0]) * invV;
+    g[a][1] = group_sum<G>(g[a][1]) * invV;
+    g[a][2] = group_sum<G>(g[a][2]) * invV;
+    mx[a] = group_max<G>(mx[a]);
+    mn[a] = group_min<G>(mn[a]);
+  }
+  if (v.limit) {
+    real alpha[5] = {(real)1, (real)1, (real)1, (real)1, (real)1};
+  #pragma unroll UNR
+  for (int q = q0 + lane; q < q1; q += G) {
       const int2 e = v.csr[q];
       const int k = e.x >> 1;
-      const real sg = (e.x & 1) ? (real)-1 : (real)1;
+      const real hs = (e.x & 1) ? (real)-0.5 : (real)0.5;
       const R4<real> G0 = v.fgeo[2 * (size_t)k];
       const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
-      const R4<real> Wj = v.W[e.y];
-      const real phi_j[5] = {Wj.x, Wj.y, Wj.z, Wj.w, v.P[e.y]};
-      // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out)
-      const real a_r = G1.w / G0.w;
-      const real a_h = (real)0.5 * G1.w * sg;
+      // f - s_i = (f - r_i) - (s_i - r_i), f - r_i = |r_ij|/2 n_out + c
+      const real fx = hs * G0.w * G0.x + G1.x - cg.y;
+      const real fy = hs * G0.w * G0.y + G1.y - cg.z;
+      const real fz = hs * G0.w * G0.z + G1.z - cg.w;
 #pragma unroll
       for (int a = 0; a < 5; a++) {
-        const real d = (phi_j[a] - phi_i[a]) * a_r;
-        const real s = (phi_i[a] + phi_j[a]) * a_h;
-        g[a][0] += d * G1.x + s * G0.x;
-        g[a][1] += d * G1.y + s * G0.y;
-        g[a][2] += d * G1.z + s * G0.z;
-        mx[a] = phi_j[a] > mx[a] ? phi_j[a] : mx[a];
-        mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
+        const real dphi = g[a][0] * fx + g[a][1] * fy + g[a][2] * fz;
+        real psi = (real)1;
+        if (dphi > (real)0)
+          psi = (mx[a] - phi_i[a]) / dphi;
+        else if (dphi < (real)0)
+          psi = (mn[a] - phi_i[a]) / dphi;
+        alpha[a] = psi < alpha[a] ? psi : alpha[a];
       }
     }
-    const real invV = cg.x;
 #pragma unroll
     for (int a = 0; a < 5; a++) {
-      g[a][0] *= invV;
-      g[a][1] *= invV;
-      g[a][2] *= invV;
+      const real al = group_min<G>(alpha[a]);
+      g[a][0] *= al;
+      g[a][1] *= al;
+      g[a][2] *= al;
     }
-    if (v.limit) {
-      real alpha[5] = {(real)1, (real)1, (real)1, (real)1, (real)1};
-      for (int q = q0; q < q1; q++) {
-        const int2 e = v.csr[q];
-        const int k = e.x >> 1;
-        const real hs = (e.x & 1) ? (real)-0.5 : (real)0.5;
-        const R4<real> G0 = v.fgeo[2 * (size_t)k];
-        const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
-        // f - s_i = (f - r_i) - (s_i - r_i), f - r_i = |r_ij|/2 n_out + c
-        const real fx = hs * G0.w * G0.x + G1.x - cg.y;
-        const real fy = hs * G0.w * G0.y + G1.y - cg.z;
-        const real fz = hs * G0.w * G0.z + G1.z - cg.w;
-#pragma unroll
-        for (int a = 0; a < 5; a++) {
-          const real dphi = g[a][0] * fx + g[a][1] * fy + g[a][2] * fz;
-          real psi = (real)1;
-          if (dphi > (real)0)
-            psi = (mx[a] - phi_i[a]) / dphi;
-          else if (dphi < (real)0)
-            psi = (mn[a] - phi_i[a]) / dphi;
-          alpha[a] = psi < alpha[a] ? psi : alpha[a];
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < 5; a++) {
-        g[a][0] *= alpha[a];
-        g[a][1] *= alpha[a];
-        g[a][2] *= alpha[a];
-      }
-    }
+  }
+  if (valid) {
+    R4<real> o[4];
+    o[0].x = g[0][0]; o[0].y = g[0][1]; o[0].z = g[0][2]; o[0].w = g[4][0];
+    o[1].x = g[1][0]; o[1].y = g[1][1]; o[1].z = g[1][2]; o[1].w = g[4][1];
+    o[2].x = g[2][0]; o[2].y = g[2][1]; o[2].z = g[2][2]; o[2].w = g[4][2];
+    o[3].x = g[3][0]; o[3].y = g[3][1]; o[3].z = g[3][2]; o[3].w = (real)0;
     R4<real>* go = v.grad + 4 * (size_t)i;
-    R4<real> o;
-    o.x = g[0][0]; o.y = g[0][1]; o.z = g[0][2]; o.w = g[4][0];
-    go[0] = o;
-    o.x = g[1][0]; o.y = g[1][1]; o.z = g[1][2]; o.w = g[4][1];
-    go[1] = o;
-    o.x = g[2][0]; o.y = g[2][1]; o.z = g[2][2]; o.w = g[4][2];
-    go[2] = o;
-    o.x = g[3][0]; o.y = g[3][1]; o.z = g[3][2]; o.w = (real)0;
-    go[3] = o;
-    // Courant time R_i / (c_i + |v_i - w_i|)
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+      if (r % G == lane) go[r] = o[r];
+  }
+  // Courant time R_i / (c_i + |v_i - w_i|), one lane per cell
+  real tc = (real)3.0e38;
+  if (valid && lane == 0) {
     real wx = 0, wy = 0, wz = 0;
     if (v.mode == AMM_LAGRANGIAN) {
       wx = Wi.y; wy = Wi.z; wz = Wi.w;
@@ -170,11 +211,7 @@ __global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradie
   }
   // block minimum, then one integer atomic per CTA (positive doubles order
   // like their bit patterns; min is order independent, so this is exact)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const real u = __shfl_xor_sync(0xffffffffu, tc, o);
-    tc = u < tc ? u : tc;
-  }
+  tc = group_min<32>(tc);
   __shared__ real wmin[CELL_TILE / 32];
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = tc;
   __syncthreads();
@@ -220,14 +257,19 @@ __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real
            hdt * ((real)v.gamma * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
 }
 
-template <typename real, bool LEARNED>
-__global__ void __launch_bounds__(FACE_TILE) k_flux(HydroView<real> v) {
-  const Tile t = v.ftiles[blockIdx.x];
-  const int k0 = t.begin + (int)threadIdx.x;
+// B threads (faces) per CTA; a tile of FACE_TILE faces spans FACE_TILE/B CTAs
+template <typename real, bool LEARNED, int B>
+__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
+  constexpr int SUB = FACE_TILE / B;
+  const Tile t = v.ftiles[blockIdx.x / SUB];
+  const int k0 = t.begin + (int)(blockIdx.x % SUB) * B + (int)threadIdx.x;
   const bool valid = k0 < t.end;
   const int k = valid ? k0 : t.begin;
   const GasC<real>& G = v.gas;
-  const real hdt = (real)(0.5 * box_dt(v, t.box));
+  __shared__ real s_hdt;
+  if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
+  __syncthreads();
+  const real hdt = s_hdt;
   const int2 lr = v.lr[k];
   const R4<real> G0 = v.fgeo[2 * (size_t)k];
   const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
@@ -290,63 +332,171 @@ __global__ void __launch_bounds__(FACE_TILE) k_flux(HydroView<real> v) {
   const real v2 = vlab[0] * vlab[0] + vlab[1] * vlab[1] + vlab[2] * vlab[2];
   const real vn = vlab[0] * n[0] + vlab[1] * n[1] + vlab[2] * n[2];
   const real mflux = rhoF * uF;
+  R4<real> fout;
+  fout.x = A * mflux;
+  fout.y = A * (mflux * vlab[0] + pF * n[0]);
+  fout.z = A * (mflux * vlab[1] + pF * n[1]);
+  fout.w = A * (mflux * vlab[2] + pF * n[2]);
+  const real fE = A * (((real)0.5 * rhoF * v2 + pF * G.inv_gm1) * uF + pF * vn);
   if (valid) {
-    R4<real> f;
-    f.x = A * mflux;
-    f.y = A * (mflux * vlab[0] + pF * n[0]);
-    f.z = A * (mflux * vlab[1] + pF * n[1]);
-    f.w = A * (mflux * vlab[2] + pF * n[2]);
-    v.flux[k] = f;
-    v.fluxE[k] = A * (((real)0.5 * rhoF * v2 + pF * G.inv_gm1) * uF + pF * vn);
+    v.flux[k] = fout;
+    v.fluxE[k] = fE;
   }
-  // statistics: block histogram in shared memory, then a few global atomics
-  __shared__ unsigned int sh[16 + 6];
-  if (threadIdx.x < 22) sh[threadIdx.x] = 0;
-  __syncthreads();
-  if (valid) {
-    atomicAdd(&sh[st.iters < 15 ? st.iters : 15], 1u);
-    atomicAdd(&sh[16], (unsigned)st.iters);
-    if (st.guard) atomicAdd(&sh[17], 1u);
-    if (st.vacuum) atomicAdd(&sh[18], 1u);
-    if (st.fail) atomicAdd(&sh[19], 1u);
-    if (st.fallback) atomicAdd(&sh[20], 1u);
-    atomicMax(&sh[21], (unsigned)st.iters);
-  }
-  __syncthreads();
-  DeviceStats* S = v.stats;
-  if (threadIdx.x < 16) {
-    if (sh[threadIdx.x]) atomicAdd(&S->hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
-  } else if (threadIdx.x == 16) {
-    atomicAdd(&S->newton_iters, (unsigned long long)sh[16]);
-    atomicAdd(&S->faces, (unsigned long long)(t.end - t.begin));
-  } else if (threadIdx.x == 17) {
-    if (sh[17]) atomicAdd(&S->guard, (unsigned long long)sh[17]);
-  } else if (threadIdx.x == 18) {
-    if (sh[18]) atomicAdd(&S->vacuum, (unsigned long long)sh[18]);
-  } else if (threadIdx.x == 19) {
-    if (sh[19]) {
-      atomicAdd(&S->newton_fail, (unsigned long long)sh[19]);
-      atomicOr(&S->status, (unsigned)ST_NEWTON_CAP);
+  if (sizeof(real) == 4 && v.fixed_acc) {
+    // largest |A F| per component for the exact fixed-point sums (float bits
+    // of non-negative values order like the values)
+    unsigned m[5] = {0u, 0u, 0u, 0u, 0u};
+    if (valid) {
+      m[0] = __float_as_uint(fabsf((float)fout.x));
+      m[1] = __float_as_uint(fabsf((float)fout.y));
+      m[2] = __float_as_uint(fabsf((float)fout.z));
+      m[3] = __float_as_uint(fabsf((float)fout.w));
+      m[4] = __float_as_uint(fabsf((float)fE));
     }
-  } else if (threadIdx.x == 20) {
-    if (sh[20]) atomicAdd(&S->fallback, (unsigned long long)sh[20]);
-  } else if (threadIdx.x == 21) {
-    atomicMax(&S->newton_max, sh[21]);
+    __shared__ unsigned wm[B / 32][5];
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+      const unsigned r = __reduce_max_sync(0xffffffffu, m[a]);
+      if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5][a] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      unsigned r = 0u;
+      for (int w = 0; w < B / 32; w++) r = wm[w][threadIdx.x] > r ? wm[w][threadIdx.x] : r;
+      atomicMax(v.fmax_bits + 5 * t.box + threadIdx.x, r);
+    }
+  }
+  // statistics: warp reductions (no contended shared-memory atomics), one
+  // slot per warp in shared memory, then a few global atomics per CTA
+  const unsigned full = 0xffffffffu;
+  const unsigned it = valid ? (unsigned)st.iters : 0u;
+  unsigned mine[22];
+#pragma unroll
+  for (int b = 0; b < 15; b++) mine[b] = __popc(__ballot_sync(full, valid && it == (unsigned)b));
+  mine[15] = __popc(__ballot_sync(full, valid && it >= 15u));
+  mine[16] = __reduce_add_sync(full, it);
+  mine[17] = __popc(__ballot_sync(full, valid && st.guard));
+  mine[18] = __popc(__ballot_sync(full, valid && st.vacuum));
+  mine[19] = __popc(__ballot_sync(full, valid && st.fail));
+  mine[20] = __popc(__ballot_sync(full, valid && st.fallback));
+  mine[21] = __reduce_max_sync(full, it);
+  __shared__ unsigned sh[B / 32][22];
+  const int wid = (int)threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int s = 0; s < 22; s++) sh[wid][s] = mine[s];
+  }
+  __syncthreads();
+  if (threadIdx.x < 22) {
+    unsigned tot = 0;
+    for (int w = 0; w < B / 32; w++)
+      tot = (threadIdx.x == 21) ? (sh[w][21] > tot ? sh[w][21] : tot) : tot + sh[w][threadIdx.x];
+    DeviceStats* S = v.stats;
+    const int s = (int)threadIdx.x;
+    if (s < 16) {
+      if (tot) atomicAdd(&S->hist[s], (unsigned long long)tot);
+    } else if (s == 16) {
+      atomicAdd(&S->newton_iters, (unsigned long long)tot);
+      const int nf_here = min(B, t.end - (t.begin + (int)(blockIdx.x % SUB) * B));
+      if (nf_here > 0) atomicAdd(&S->faces, (unsigned long long)nf_here);
+    } else if (s == 17) {
+      if (tot) atomicAdd(&S->guard, (unsigned long long)tot);
+    } else if (s == 18) {
+      if (tot) atomicAdd(&S->vacuum, (unsigned long long)tot);
+    } else if (s == 19) {
+      if (tot) {
+        atomicAdd(&S->newton_fail, (unsigned long long)tot);
+        atomicOr(&S->status, (unsigned)ST_NEWTON_CAP);
+      }
+    } else if (s == 20) {
+      if (tot) atomicAdd(&S->fallback, (unsigned long long)tot);
+    } else {
+      if (tot) atomicMax(&S->newton_max, tot);
+    }
   }
 }
 
 // ------------------------------------------------------------ A8+A1+A9
-template <typename real>
+// Fixed-point image of an FP32 value: x * 2^s as an int64, with
+// s = 188 - headroom - eb and eb the biased exponent of the largest magnitude
+// of the component, so every |x| 2^s < 2^(62 - headroom) and a sum over at
+// most 2^headroom terms cannot overflow.  Built from the float's bits on the
+// integer pipe (a float-to-int64 conversion instruction would run on GB300's
+// narrow FP64 pipe); values below the resolution 2^-s are truncated toward
+// zero, the same way for both cells of a face.  Inf/NaN sets `bad`.
+__device__ __forceinline__ long long to_fixed(float x, int eb, int headroom, bool& bad) {
+  const unsigned u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xffu);
+  if (e == 0) return 0;               // zero (denormals are flushed in the FP32 form)
+  if (e == 255) {
+    bad = true;
+    return 0;
+  }
+  const long long M = (long long)((u & 0x7fffffu) | 0x800000u);
+  const int sh = e - eb + 38 - headroom;
+  long long X;
+  if (sh >= 0)
+    X = M << sh;
+  else
+    X = (sh > -40) ? (M >> (-sh)) : 0ll;
+  return (u >> 31) ? -X : X;
+}
+
+// 2^(eb - 188 + headroom) in FP64 (exact)
+__device__ __forceinline__ double fixed_scale(int eb, int headroom) {
+  return __longlong_as_double((long long)(1023 + eb - 188 + headroom) << 52);
+}
+
+// G consecutive lanes share a cell (as in the gradient kernel); lane l sums
+// the cell's incidences l, l+G, ...; the lane partial sums are combined with
+// shuffles and lane 0 applies the update.
+template <typename real, int G>
 __global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
-  const Tile t = v.ctiles[blockIdx.x];
-  const int i = t.begin + (int)threadIdx.x;
+  constexpr int CELLS = CELL_TILE / G;
+  const Tile t = v.ctiles[blockIdx.x / G];
+  const int lane = (int)threadIdx.x % G;
+  const int i = t.begin + (int)(blockIdx.x % G) * CELLS + (int)threadIdx.x / G;
+  const bool valid = i < t.end;
+  const int q0 = valid ? v.csr_off[i] : 0;
+  const int q1 = valid ? v.csr_off[i + 1] : 0;
+  const size_t n = (size_t)v.n;
   double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  unsigned nonpos = 0;
-  if (i < t.end) {
-    const double dt = box_dt(v, t.box);
+  double d[5];
+  bool bad = false;
+  if (sizeof(real) == 4 && v.fixed_acc) {
+    // Exact sums: every face flux is converted once to an int64 multiple of
+    // 2^-s (s per box and component, from the step's largest |A F|) and the
+    // integers are added; both cells of a face add the identical integer
+    // with opposite signs, so the update conserves exactly and does not
+    // depend on the summation order.  One rounding per cell remains, when
+    // the integer total is scaled back to FP64.
+    int eb[5];
+#pragma unroll
+    for (int a = 0; a < 5; a++) eb[a] = (int)((v.fmax_bits[5 * t.box + a] >> 23) & 0xffu);
+    long long acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int e = q0 + lane; e < q1; e += G) {
+      const int2 r = v.csr[e];
+      const int k = r.x >> 1;
+      const R4<real> f = v.flux[k];
+      const float fv[5] = {(float)f.x, (float)f.y, (float)f.z, (float)f.w, (float)v.fluxE[k]};
+#pragma unroll
+      for (int a = 0; a < 5; a++) {
+        const long long x = to_fixed(fv[a], eb[a], v.headroom, bad);
+        acc[a] += (r.x & 1) ? -x : x;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; a++) acc[a] = group_sum<G>(acc[a]);
+    bad = group_max<G>((int)bad) != 0;
+    if (lane == 0) {
+#pragma unroll
+      for (int a = 0; a < 5; a++) d[a] = __ll2double_rn(acc[a]) * fixed_scale(eb[a], v.headroom);
+    }
+  } else {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const int q0 = v.csr_off[i], q1 = v.csr_off[i + 1];
-    for (int e = q0; e < q1; e++) {
+#pragma unroll 4
+    for (int e = q0 + lane; e < q1; e += G) {
       const int2 r = v.csr[e];
       const int k = r.x >> 1;
       const R4<real> f = v.flux[k];
@@ -359,31 +509,38 @@ __global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
         acc[4] += fe;
       }
     }
-    const size_t n = (size_t)v.n;
+#pragma unroll
+    for (int a = 0; a < 5; a++) d[a] = group_sum<G>(acc[a]);
+  }
+  unsigned nonpos = 0;
+  if (valid && lane == 0) {
+    const double dt = box_dt(v, t.box);
 #pragma unroll
     for (int a = 0; a < 5; a++) {
-      q[a] = v.Q[a * n + i] - dt * acc[a];
+      q[a] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v.Q[a * n + i] - dt * d[a];
       v.Q[a * n + i] = q[a];
     }
     const real P = prims_from_Q(v, i, q[0], q[1], q[2], q[3], q[4]);
     nonpos = (!(q[0] > 0.0) || !(P > (real)0)) ? 1u : 0u;
   }
-  // per-tile FP64 sums in a fixed tree order (bit reproducible)
-  __shared__ double red[5][CELL_TILE];
+  // per-block FP64 sums in a fixed order (bit reproducible): the cells' lane
+  // 0 values are combined across the warp, then across the warps
+  __shared__ double red[CELL_TILE / 32][5];
 #pragma unroll
-  for (int a = 0; a < 5; a++) red[a][threadIdx.x] = q[a];
-  __syncthreads();
-  for (int s = CELL_TILE / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
+  for (int a = 0; a < 5; a++) {
+    double s = q[a];
 #pragma unroll
-      for (int a = 0; a < 5; a++) red[a][threadIdx.x] += red[a][threadIdx.x + s];
-    }
-    __syncthreads();
+    for (int o = 16; o >= G; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][a] = s;
   }
-  if (threadIdx.x < 5) v.partial[5 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
-  const unsigned bad = __syncthreads_count(nonpos);
-  if (threadIdx.x == 0 && bad) {
-    atomicAdd(&v.stats->nonpos, (unsigned long long)bad);
+  const unsigned nbad = __syncthreads_count(nonpos);
+  if (threadIdx.x < 5) {
+    double s = red[0][threadIdx.x];
+    for (int w = 1; w < CELL_TILE / 32; w++) s += red[w][threadIdx.x];
+    v.partial[5 * (size_t)blockIdx.x + threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0 && nbad) {
+    atomicAdd(&v.stats->nonpos, (unsigned long long)nbad);
     atomicOr(&v.stats->status, (unsigned)ST_NONPOS);
   }
 }
@@ -405,23 +562,28 @@ __global__ void __launch_bounds__(CELL_TILE) k_partial_sums(HydroView<real> v) {
     }
     __syncthreads();
   }
-  if (threadIdx.x < 5) v.partial[5 * (size_t)blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 5) {
+    const size_t base = 5 * (size_t)blockIdx.x * v.update_lanes;
+    v.partial[base + threadIdx.x] = red[threadIdx.x][0];
+    for (int g = 1; g < v.update_lanes; g++) v.partial[base + 5 * g + threadIdx.x] = 0.0;
+  }
 }
 
-// one CTA per box: ordered sum of the box's tile partials; time step record
+// one CTA per box: ordered sum of the box's block partials; time step record
+constexpr int FINISH_THREADS = 512;
 template <typename real>
 __global__ void k_finish(HydroView<real> v, int count_step) {
   const int b = blockIdx.x;
-  const int t0 = v.box_first_ctile[b], t1 = v.box_first_ctile[b + 1];
-  __shared__ double red[5][128];
+  const int t0 = v.box_first_ctile[b] * v.update_lanes, t1 = v.box_first_ctile[b + 1] * v.update_lanes;
+  __shared__ double red[5][FINISH_THREADS];
   double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int tt = t0 + (int)threadIdx.x; tt < t1; tt += 128)
+  for (int tt = t0 + (int)threadIdx.x; tt < t1; tt += FINISH_THREADS)
 #pragma unroll
     for (int a = 0; a < 5; a++) s[a] += v.partial[5 * (size_t)tt + a];
 #pragma unroll
   for (int a = 0; a < 5; a++) red[a][threadIdx.x] = s[a];
   __syncthreads();
-  for (int st = 64; st > 0; st >>= 1) {
+  for (int st = FINISH_THREADS / 2; st > 0; st >>= 1) {
     if ((int)threadIdx.x < st) {
 #pragma unroll
       for (int a = 0; a < 5; a++) red[a][threadIdx.x] += red[a][threadIdx.x + st];
@@ -441,7 +603,7 @@ __global__ void k_set_state(HydroView<real> v, const double* Qa, int dim, unsign
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   const int nv = dim + 2;
-  const double* q = Qa + (size_t)i * nv;
+  const double* q = Qa + (size_t)v.cell_perm[i] * nv;
   const double m = q[0];
   const double px = q[1], py = q[2], pz = (dim == 3) ? q[3] : 0.0;
   const double E = q[dim + 1];
@@ -461,7 +623,7 @@ __global__ void k_get_state(HydroView<real> v, double* Qa, int dim) {
   if (i >= v.n) return;
   const int nv = dim + 2;
   const size_t n = (size_t)v.n;
-  double* q = Qa + (size_t)i * nv;
+  double* q = Qa + (size_t)v.cell_perm[i] * nv;
   q[0] = v.Q[i];
   q[1] = v.Q[n + i];
   q[2] = v.Q[2 * n + i];
@@ -475,7 +637,7 @@ __global__ void k_get_prims(HydroView<real> v, double* Wa, int dim) {
   if (i >= v.n) return;
   const int nv = dim + 2;
   const R4<real> w = v.W[i];
-  double* o = Wa + (size_t)i * nv;
+  double* o = Wa + (size_t)v.cell_perm[i] * nv;
   o[0] = w.x;
   o[1] = w.y;
   o[2] = w.z;
@@ -493,7 +655,7 @@ __global__ void k_get_grads(HydroView<real> v, double* ga, int dim) {
                            {g3.x, g3.y, g3.z}, {g0.w, g1.w, g2.w}};
   // variables in output order rho, v_1..v_dim, P
   const int var_of[5] = {0, 1, 2, 3, 4};
-  double* o = ga + (size_t)i * (dim + 2) * dim;
+  double* o = ga + (size_t)v.cell_perm[i] * (dim + 2) * dim;
   int out = 0;
   for (int a = 0; a < 5; a++) {
     if (dim == 2 && a == 3) continue;
@@ -507,7 +669,7 @@ __global__ void k_get_flux(HydroView<real> v, double* Fa, int dim) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= v.nf) return;
   const R4<real> f = v.flux[k];
-  double* o = Fa + (size_t)k * (dim + 2);
+  double* o = Fa + (size_t)v.face_perm[k] * (dim + 2);
   o[0] = f.x;
   o[1] = f.y;
   o[2] = f.z;
@@ -520,9 +682,10 @@ __global__ void k_set_wmesh(HydroView<real> v, const double* wa, int dim) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   R4<real> w;
-  w.x = (real)wa[(size_t)i * dim];
-  w.y = (real)wa[(size_t)i * dim + 1];
-  w.z = (dim == 3) ? (real)wa[(size_t)i * dim + 2] : (real)0;
+  const size_t o = (size_t)v.cell_perm[i] * dim;
+  w.x = (real)wa[o];
+  w.y = (real)wa[o + 1];
+  w.z = (dim == 3) ? (real)wa[o + 2] : (real)0;
   w.w = (real)0;
   const_cast<R4<real>*>(v.wmesh)[i] = w;
 }
@@ -540,6 +703,11 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.nf = (int)c->nf;
   v.gamma = c->gamma;
   v.tol = c->opt.riemann_tol;
+  v.tol_r = (real)c->opt.riemann_tol;
+  v.fixed_acc = (c->opt.precision != AMM_FP64 && !c->opt.fp64_accumulate) ? 1 : 0;
+  v.headroom = c->headroom;
+  v.update_lanes = (c->update_lanes == 1 || c->update_lanes == 2 || c->update_lanes == 8) ? c->update_lanes : 4;
+  v.fmax_bits = c->fmax_bits;
   v.gas = GasC<real>(c->gamma);
   v.cfl = cfl;
   v.dt_box = c->dt_box;
@@ -551,8 +719,9 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.grad = (R4<real>*)c->grad;
   v.wmesh = (const R4<real>*)c->wmesh;
   v.cgeo = (const R4<real>*)c->cgeo;
-  v.cgeo64 = c->cgeo64;
   v.crad = (const real*)c->crad;
+  v.cgeo64 = c->cgeo64;
+
   v.lr = c->lr;
   v.fgeo = (const R4<real>*)c->fgeo;
   v.flux = (R4<real>*)c->flux;
@@ -561,6 +730,8 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.csr = c->csr;
   v.ctiles = c->ctiles;
   v.ftiles = c->ftiles;
+  v.cell_perm = c->cell_perm;
+  v.face_perm = c->face_perm;
   v.partial = c->partial;
   v.totals = c->totals;
   v.box_first_ctile = c->box_first_ctile;
@@ -583,21 +754,35 @@ cudaError_t launch_gradients(amm_ctx* c) {
   auto v = make_view<real>(c, 0.0);
   cudaError_t e = cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
-  k_gradients<real><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v);
+  e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * 5 * c->nboxes, c->stream);
+  if (e != cudaSuccess) return e;
+  switch (c->grad_lanes) {
+    case 1: k_gradients<real, 1><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+    case 2: k_gradients<real, 2><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+    case 8: k_gradients<real, 8><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+    default: k_gradients<real, 4><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+  }
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_flux(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
+  const bool b128 = c->flux_block == 128;
   if (c->opt.precision == AMM_FP32_LEARNED) {
     if constexpr (sizeof(real) == 4) {
-      k_flux<real, true><<<c->n_ftiles, FACE_TILE, 0, c->stream>>>(v);
+      if (b128)
+        k_flux<real, true, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+      else
+        k_flux<real, true, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
-    k_flux<real, false><<<c->n_ftiles, FACE_TILE, 0, c->stream>>>(v);
+    if (b128)
+      k_flux<real, false, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+    else
+      k_flux<real, false, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
   }
   return cudaGetLastError();
 }
@@ -605,7 +790,12 @@ cudaError_t launch_flux(amm_ctx* c, double cfl) {
 template <typename real>
 cudaError_t launch_update(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
-  k_update<real><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v);
+  switch (c->update_lanes) {
+    case 1: k_update<real, 1><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+    case 2: k_update<real, 2><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+    case 8: k_update<real, 8><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+    default: k_update<real, 4><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+  }
   return cudaGetLastError();
 }
 
@@ -614,9 +804,9 @@ cudaError_t launch_finish(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
   if (cfl < 0.0) {  // totals of the current state, no step
     k_partial_sums<real><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v);
-    k_finish<real><<<c->nboxes, 128, 0, c->stream>>>(v, 0);
+    k_finish<real><<<c->nboxes, FINISH_THREADS, 0, c->stream>>>(v, 0);
   } else {
-    k_finish<real><<<c->nboxes, 128, 0, c->stream>>>(v, 1);
+    k_finish<real><<<c->nboxes, FINISH_THREADS, 0, c->stream>>>(v, 1);
   }
   return cudaGetLastError();
 }

@@ -88,12 +88,21 @@ struct RiemannInfo {
   int fail;       // hit the iteration cap
 };
 
+// State of the last Newton step: f_L, f_R and their derivatives at the
+// previous iterate p_prev; u* at the final p follows to first order,
+// u* = (u_L+u_R)/2 + (f_R - f_L + (f_R' - f_L')(p - p_prev))/2, with an error
+// of order (p - p_prev)^2, far below the tolerance.
+template <typename real>
+struct NewtonTail {
+  real fL, dL, fR, dR, dp;
+};
+
 // Newton iteration for p*; returns p* in `real`, with the FP64 guard in the
 // FP32 form.  iterations counted in info.
 template <typename real>
 __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL, real cL, real rhoR, real uR,
                                              real pR, real cR, const GasC<real>& G, double tol, int maxit,
-                                             RiemannInfo& info) {
+                                             RiemannInfo& info, NewtonTail<real>& tail) {
   const real du = uR - uL;
   int it = 0;
   bool conv = false;
@@ -106,6 +115,7 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
       if (!(pn > (real)0)) pn = (real)1e-3 * p;
       it++;
       const real ch = (real)2 * fabs(pn - p) / (pn + p);
+      tail.fL = fL; tail.dL = dL; tail.fR = fR; tail.dR = dR; tail.dp = pn - p;
       p = pn;
       if (ch < (real)tol) {
         conv = true;
@@ -114,6 +124,7 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
     }
   } else {
     constexpr int FLOAT_ITERS = 12;
+    const float tol_f = (float)tol;
     const float guard_p = 1e-3f * (pL < pR ? (float)pL : (float)pR);
     bool to64 = false;
     while (it < maxit) {
@@ -128,8 +139,9 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
       if (!(pn > (real)0)) pn = (real)1e-3 * p;
       it++;
       const real ch = (real)2 * fabsf((float)(pn - p)) / (pn + p);
+      tail.fL = fL; tail.dL = dL; tail.fR = fR; tail.dR = dR; tail.dp = pn - p;
       p = pn;
-      if (ch < (real)tol) {
+      if (ch < tol_f) {
         conv = true;
         break;
       }
@@ -149,6 +161,7 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
         if (!(pn > 0.0)) pn = 1e-3 * pd;
         it++;
         const double ch = 2.0 * fabs(pn - pd) / (pn + pd);
+        tail.fL = (real)fL; tail.dL = (real)dL; tail.fR = (real)fR; tail.dR = (real)dR; tail.dp = (real)(pn - pd);
         pd = pn;
         if (ch < tol) {
           conv = true;
@@ -208,11 +221,9 @@ __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real 
     return 0;
   }
   real p0 = have_guess ? guess : standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G);
-  const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, maxit, info);
-  real fL, dL, fR, dR;
-  wave_curve(ps, rhoL, pL, cL, G, fL, dL);
-  wave_curve(ps, rhoR, pR, cR, G, fR, dR);
-  const real us = (real)0.5 * (uL + uR) + (real)0.5 * (fR - fL);
+  NewtonTail<real> nt;
+  const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, maxit, info, nt);
+  const real us = (real)0.5 * (uL + uR) + (real)0.5 * ((nt.fR - nt.fL) + (nt.dR - nt.dL) * nt.dp);
   if ((real)0 <= us) {
     const real r = ps / pL;
     if (ps > pL) {

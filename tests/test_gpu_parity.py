@@ -316,3 +316,53 @@ def test_full_size_config2(amm):
         out = amm.amm_get_state(ctx)
         emax, e999 = errs(out, ref, fl)
         assert emax < TOL[prec], (prec, emax, e999)
+
+
+def test_fixed_point_accumulation_matches_fp64_accumulation(amm):
+    """The FP32 form's exact int64 flux sums and the FP64 floating-point sums
+    of the same FP32 fluxes differ only by FP64 rounding of the sums."""
+    P = ics.lognormal_3d(16, seed=11)
+    Q = P.conserved()
+    W = O.primitives(O.Mesh(P.tess), Q, P.tess.volume, P.gamma)
+    fl = floor_of(Q, 3, P.gamma, W)
+    out = []
+    for acc64 in (False, True):
+        ctx = amm.create_from_mesh(P.tess, Q, P.gamma, precision="fp32", fp64_accumulate=acc64)
+        amm.amm_step(ctx, 2e-3)
+        out.append(amm.amm_get_state(ctx))
+    emax, _ = errs(out[0], out[1], fl)
+    assert emax < 1e-13, emax
+
+
+@pytest.mark.parametrize("tuning", [(1, 1, 128), (2, 8, 256), (8, 2, 128), (4, 4, 256)])
+def test_launch_shapes_keep_parity(amm, tuning):
+    """Every launch shape the autotuner may pick gives oracle parity."""
+    P = ics.turbulent_3d(16, seed=2)
+    M = O.Mesh(P.tess)
+    Q = P.conserved()
+    ref, dt, _, _ = O.step(M, Q, P.gamma, "lagrangian", cfl=0.3)
+    W = O.primitives(M, Q, P.tess.volume, P.gamma)
+    fl = floor_of(Q, 3, P.gamma, W)
+    for prec in ("fp64", "fp32"):
+        ctx = amm.create_from_mesh(P.tess, Q, P.gamma, precision=prec)
+        amm.amm_set_tuning(ctx, *tuning)
+        amm.amm_step(ctx, dt)
+        emax, _ = errs(amm.amm_get_state(ctx), ref, fl)
+        assert emax < TOL[prec], (prec, tuning, emax)
+
+
+def test_autotune_restores_state_and_keeps_parity(amm):
+    P = ics.turbulent_3d(16, seed=3)
+    M = O.Mesh(P.tess)
+    Q = P.conserved()
+    ref, dt, _, _ = O.step(M, Q, P.gamma, "lagrangian", cfl=0.3)
+    W = O.primitives(M, Q, P.tess.volume, P.gamma)
+    fl = floor_of(Q, 3, P.gamma, W)
+    ctx = amm.create_from_mesh(P.tess, Q, P.gamma, precision="fp32")
+    t = amm.amm_autotune(ctx, 0.3, reps=2)
+    assert t["grad_lanes"] in (1, 2, 4, 8) and t["flux_block"] in (128, 256) and t["step_ms"] > 0
+    assert np.array_equal(amm.amm_get_state(ctx), Q)
+    assert amm.amm_get_stats(ctx)["steps"] == 0
+    amm.amm_step(ctx, dt)
+    emax, _ = errs(amm.amm_get_state(ctx), ref, fl)
+    assert emax < TOL["fp32"]
