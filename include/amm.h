@@ -210,6 +210,32 @@ int amm_get_tuning(amm_ctx* ctx, amm_tuning* t);
  * (may be NULL).  Synchronises; allocates one state-sized temporary. */
 int amm_autotune(amm_ctx* ctx, double cfl, int reps, amm_tuning* out);
 
+/* Allocation-free Courant time step.  The paper has no counterpart to this
+ * entry point: it exists for callers that cannot allocate device memory --
+ * code whose device memory is owned by another allocator (for example a
+ * framework's caching pool that has reserved most of HBM) or that must not
+ * call cudaMalloc/cudaFree on a latency-critical path, since those calls can
+ * synchronise the device.  It computes the same quantity as amm_timestep for
+ * one box, dt = cfl * min_i R_i / (c_i + |v_i - w_i|), from caller-owned
+ * device arrays, without a context:
+ *   W_device      [n_cells][dim+2] primitives (rho, v, P), FP64, device
+ *   V_device      [n_cells] cell volumes, FP64, device
+ *   wmesh_device  [n_cells][dim] mesh velocities, or NULL for a static mesh
+ *   dt_device     one FP64 on the device, receives dt
+ *   stream        cudaStream_t (NULL: the legacy default stream)
+ * The call is asynchronous on `stream`.  Its only working memory is a static
+ * device array of AMM_NOALLOC_MAX_BLOCKS doubles (128 KiB) that every GPU
+ * loading the library holds until exit; hence at most AMM_NOALLOC_MAX_CELLS
+ * cells (AMM_ERR_INVALID_ARG beyond).  The first call on each device looks up
+ * the array's device address (with that device current) and should come
+ * before any stream capture.  All calls share the array, so calls whose
+ * kernels overlap on the GPU race; order them on one stream.
+ * Errors: AMM_ERR_INVALID_ARG, AMM_ERR_CUDA. */
+#define AMM_NOALLOC_MAX_BLOCKS 16384
+#define AMM_NOALLOC_MAX_CELLS ((int64_t)AMM_NOALLOC_MAX_BLOCKS * 4096)
+int amm_timestep_noalloc(int dim, int64_t n_cells, const double* W_device, const double* V_device,
+                         const double* wmesh_device, double gamma, double cfl, double* dt_device, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ _SIGS = {
     "amm_set_tuning": (_I, [_P, _P]),
     "amm_get_tuning": (_I, [_P, _P]),
     "amm_autotune": (_I, [_P, _D, _I, _P]),
+    "amm_timestep_noalloc": (_I, [_I, _I64, _P, _P, _P, _D, _D, _P, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
 }
 
@@ -341,6 +342,16 @@ def amm_autotune(ctx, cfl=0.3, reps=5):
     t = amm_tuning()
     _check(ctx, lib().amm_autotune(ctx.handle, float(cfl), int(reps), ctypes.byref(t)))
     return _tuning_dict(t)
+
+
+def amm_timestep_noalloc(dim, n_cells, W_ptr, V_ptr, wmesh_ptr, gamma, cfl, dt_ptr, stream=None):
+    """Allocation-free Courant step on caller-owned device buffers (integer
+    device addresses); asynchronous on `stream`.  Raises AmmError on failure."""
+    rc = lib().amm_timestep_noalloc(int(dim), int(n_cells), ctypes.c_void_p(int(W_ptr)), ctypes.c_void_p(int(V_ptr)),
+                                    ctypes.c_void_p(int(wmesh_ptr)) if wmesh_ptr else None, float(gamma), float(cfl),
+                                    ctypes.c_void_p(int(dt_ptr)), ctypes.c_void_p(int(stream)) if stream else None)
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_timestep_noalloc failed")
 
 
 def create_from_mesh(mesh, Q, gamma, precision="fp64", mesh_motion="lagrangian", **kw):
