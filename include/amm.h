@@ -210,6 +210,52 @@ int amm_get_tuning(amm_ctx* ctx, amm_tuning* t);
  * (may be NULL).  Synchronises; allocates one state-sized temporary. */
 int amm_autotune(amm_ctx* ctx, double cfl, int reps, amm_tuning* out);
 
+/* ---------------------------------------------------------------------------
+ * Learned starting value for the Riemann star pressure (FP32 learned form).
+ * The paper has no such component: a 6 -> 64 -> 64 -> 1 perceptron with SiLU
+ * activations maps the normalised face state
+ *   x = (log(rho_L/rhobar), log(p_L/pbar), u_L/cbar, log(rho_R/rhobar), log(p_R/pbar), u_R/cbar)
+ * (rhobar, pbar the two-sided means, cbar = sqrt(gamma pbar/rhobar)) to
+ * y = log(pstar / pbar); Newton then starts from pbar exp(y) and still runs to the
+ * same tolerance.  Weights are BF16 on BF16 tensor cores with FP32
+ * accumulation; FP32 master parameters are kept for training.
+ * Parameter vector (AMM_MLP_NPARAMS floats): W1[64][6], b1[64], W2[64][64],
+ * b2[64], W3[64], b3 (row = output unit).
+ * Face states are [n][6] floats (rho_L, u_L, p_L, rho_R, u_R, p_R), u along
+ * the face normal in the face frame.  *_device pointers are device memory;
+ * calls on a handle run on its stream and the ones returning data to the
+ * host synchronise it. */
+#define AMM_MLP_NPARAMS 4673
+typedef struct amm_mlp amm_mlp;
+int amm_mlp_create(amm_mlp** out, double gamma, void* stream);
+void amm_mlp_destroy(amm_mlp* net);
+const char* amm_mlp_last_error(const amm_mlp* net);
+int amm_mlp_num_params(void);
+int amm_mlp_set_params(amm_mlp* net, const float* params);          /* host [AMM_MLP_NPARAMS] */
+int amm_mlp_get_params(amm_mlp* net, float* params);                /* host [AMM_MLP_NPARAMS] */
+/* y_device[i] = network(x_device[i]) for n feature rows [n][6] (tensor cores) */
+int amm_mlp_forward(amm_mlp* net, const float* x_device, int64_t n, float* y_device);
+/* Loss L = sum_i (y_i - t_i)^2 / n over the samples idx_device[0..n) (or
+ * 0..n when idx_device is NULL) of x_device [.][6] and targets t_device, and
+ * its gradient (host [AMM_MLP_NPARAMS], same order as the parameters) from
+ * the tensor-core forward and backward passes.  Synchronises. */
+int amm_mlp_grads(amm_mlp* net, const float* x_device, const float* t_device, const int32_t* idx_device, int64_t n,
+                  float* grads, float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * FP32 master parameters with the gradient of that minibatch; the BF16
+ * weights are refreshed.  Asynchronous; loss_device (may be NULL) receives
+ * the minibatch loss.  amm_mlp_sync waits and reports a timed-out wait. */
+int amm_mlp_train_step(amm_mlp* net, const float* x_device, const float* t_device, const int32_t* idx_device,
+                       int64_t n, float lr, float* loss_device);
+int amm_mlp_sync(amm_mlp* net);
+/* features [n][6] and pbar [n] (may be NULL) from face states */
+int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
+                     void* stream);
+/* exact star pressure of each face state in FP64 (Newton from the standard
+ * guess to the relative tolerance tol); NaN where the states generate vacuum */
+int amm_riemann_pstar(double gamma, int64_t n, const float* states_device, double tol, float* pstar_device,
+                      void* stream);
+
 /* Allocation-free Courant time step.  The paper has no counterpart to this
  * entry point: it exists for callers that cannot allocate device memory --
  * code whose device memory is owned by another allocator (for example a

@@ -88,6 +88,18 @@ _SIGS = {
     "amm_get_tuning": (_I, [_P, _P]),
     "amm_autotune": (_I, [_P, _D, _I, _P]),
     "amm_timestep_noalloc": (_I, [_I, _I64, _P, _P, _P, _D, _D, _P, _P]),
+    "amm_mlp_create": (_I, [ctypes.POINTER(_P), _D, _P]),
+    "amm_mlp_destroy": (None, [_P]),
+    "amm_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "amm_mlp_num_params": (_I, []),
+    "amm_mlp_set_params": (_I, [_P, _P]),
+    "amm_mlp_get_params": (_I, [_P, _P]),
+    "amm_mlp_forward": (_I, [_P, _P, _I64, _P]),
+    "amm_mlp_grads": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
+    "amm_mlp_train_step": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, _P]),
+    "amm_mlp_sync": (_I, [_P]),
+    "amm_mlp_features": (_I, [_D, _I64, _P, _P, _P, _P]),
+    "amm_riemann_pstar": (_I, [_D, _I64, _P, _D, _P, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
 }
 
@@ -352,6 +364,102 @@ def amm_timestep_noalloc(dim, n_cells, W_ptr, V_ptr, wmesh_ptr, gamma, cfl, dt_p
                                     ctypes.c_void_p(int(dt_ptr)), ctypes.c_void_p(int(stream)) if stream else None)
     if rc != AMM_OK:
         raise AmmError(rc, "amm_timestep_noalloc failed")
+
+
+class Mlp:
+    """Owns an amm_mlp* (the learned p* proposal network)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().amm_mlp_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _mcheck(net, rc):
+    if rc != AMM_OK:
+        raise AmmError(rc, lib().amm_mlp_last_error(net.handle).decode())
+
+
+def _ptr(p):
+    return ctypes.c_void_p(int(p)) if p else None
+
+
+def amm_mlp_create(gamma, stream=None):
+    h = ctypes.c_void_p()
+    rc = lib().amm_mlp_create(ctypes.byref(h), float(gamma), _ptr(stream))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_mlp_create failed")
+    return Mlp(h)
+
+
+def amm_mlp_num_params():
+    return int(lib().amm_mlp_num_params())
+
+
+def amm_mlp_set_params(net, params):
+    p = _arr(params, np.float32)
+    assert p.shape == (amm_mlp_num_params(),)
+    _mcheck(net, lib().amm_mlp_set_params(net.handle, p.ctypes.data))
+
+
+def amm_mlp_get_params(net):
+    p = np.empty(amm_mlp_num_params(), np.float32)
+    _mcheck(net, lib().amm_mlp_get_params(net.handle, p.ctypes.data))
+    return p
+
+
+def amm_mlp_forward(net, x_ptr, n, y_ptr):
+    _mcheck(net, lib().amm_mlp_forward(net.handle, _ptr(x_ptr), int(n), _ptr(y_ptr)))
+
+
+def amm_mlp_grads(net, x_ptr, t_ptr, idx_ptr, n):
+    g = np.empty(amm_mlp_num_params(), np.float32)
+    loss = ctypes.c_float(0.0)
+    _mcheck(net, lib().amm_mlp_grads(net.handle, _ptr(x_ptr), _ptr(t_ptr), _ptr(idx_ptr), int(n), g.ctypes.data,
+                                     ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def amm_mlp_train_step(net, x_ptr, t_ptr, idx_ptr, n, lr, loss_ptr=0):
+    _mcheck(net, lib().amm_mlp_train_step(net.handle, _ptr(x_ptr), _ptr(t_ptr), _ptr(idx_ptr), int(n), float(lr),
+                                          _ptr(loss_ptr)))
+
+
+def amm_mlp_sync(net):
+    _mcheck(net, lib().amm_mlp_sync(net.handle))
+
+
+def amm_mlp_features(gamma, n, states_ptr, x_ptr, pbar_ptr=0, stream=None):
+    rc = lib().amm_mlp_features(float(gamma), int(n), _ptr(states_ptr), _ptr(x_ptr), _ptr(pbar_ptr), _ptr(stream))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_mlp_features failed")
+
+
+def amm_riemann_pstar(gamma, n, states_ptr, tol, pstar_ptr, stream=None):
+    rc = lib().amm_riemann_pstar(float(gamma), int(n), _ptr(states_ptr), float(tol), _ptr(pstar_ptr), _ptr(stream))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_riemann_pstar failed")
+
+
+def pack_params(p):
+    """oracle-style dict (W1,b1,W2,b2,W3,b3) -> flat parameter vector"""
+    return np.concatenate([np.asarray(p[k], np.float64).reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def unpack_params(v):
+    v = np.asarray(v, np.float64)
+    out, o = {}, 0
+    for k, shp in (("W1", (64, 6)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (1, 64)), ("b3", (1,))):
+        size = int(np.prod(shp))
+        out[k] = v[o:o + size].reshape(shp)
+        o += size
+    return out
 
 
 def create_from_mesh(mesh, Q, gamma, precision="fp64", mesh_motion="lagrangian", **kw):
