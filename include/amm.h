@@ -248,6 +248,15 @@ int amm_mlp_grads(amm_mlp* net, const float* x_device, const float* t_device, co
 int amm_mlp_train_step(amm_mlp* net, const float* x_device, const float* t_device, const int32_t* idx_device,
                        int64_t n, float lr, float* loss_device);
 int amm_mlp_sync(amm_mlp* net);
+/* Copies the network's BF16 weights into a context of the FP32 learned form
+ * (AMM_FP32_LEARNED); its steps then start every Newton solve from the
+ * network's proposal.  Steps of that form fail with AMM_ERR_NOT_READY before. */
+int amm_mlp_attach(amm_ctx* ctx, const amm_mlp* net);
+/* One step with device-side Courant time step (coefficient cfl), recording
+ * every face's Riemann inputs after extrapolation, prediction and rotation
+ * into states_device [n_faces][6] (internal face order) -- training data for
+ * the proposal network.  FP32 forms only. */
+int amm_harvest(amm_ctx* ctx, double cfl, float* states_device);
 /* features [n][6] and pbar [n] (may be NULL) from face states */
 int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
                      void* stream);

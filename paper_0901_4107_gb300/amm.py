@@ -98,6 +98,8 @@ _SIGS = {
     "amm_mlp_grads": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
     "amm_mlp_train_step": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, _P]),
     "amm_mlp_sync": (_I, [_P]),
+    "amm_mlp_attach": (_I, [_P, _P]),
+    "amm_harvest": (_I, [_P, _D, _P]),
     "amm_mlp_features": (_I, [_D, _I64, _P, _P, _P, _P]),
     "amm_riemann_pstar": (_I, [_D, _I64, _P, _D, _P, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
@@ -433,6 +435,14 @@ def amm_mlp_train_step(net, x_ptr, t_ptr, idx_ptr, n, lr, loss_ptr=0):
 
 def amm_mlp_sync(net):
     _mcheck(net, lib().amm_mlp_sync(net.handle))
+
+
+def amm_mlp_attach(ctx, net):
+    _check(ctx, lib().amm_mlp_attach(ctx.handle, net.handle))
+
+
+def amm_harvest(ctx, cfl, states_ptr):
+    _check(ctx, lib().amm_harvest(ctx.handle, float(cfl), _ptr(states_ptr)))
 
 
 def amm_mlp_features(gamma, n, states_ptr, x_ptr, pbar_ptr=0, stream=None):

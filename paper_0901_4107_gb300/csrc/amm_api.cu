@@ -540,6 +540,8 @@ int amm_timestep(amm_ctx* c, double cfl, double* dt_out) {
 }
 
 static int step_with_dt_box(amm_ctx* c) {
+  if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
+    return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
   if (!c->grads_fresh) CU(run_gradients(c));
   CU(run_step_tail(c, 0.0));
   c->grads_fresh = false;
@@ -606,6 +608,22 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
     }
     for (int64_t s = 0; s < nsteps; s++) CU(cudaGraphLaunch(c->graph, c->stream));
   }
+  c->grads_fresh = false;
+  c->totals_fresh = true;
+  c->have_step = true;
+  return AMM_OK;
+}
+
+int amm_harvest(amm_ctx* c, double cfl, float* states_device) {
+  if (!c || !(cfl > 0.0) || !states_device) return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
+  if (c->opt.precision == AMM_FP64) return fail(c, AMM_ERR_INVALID_ARG, "harvest needs an FP32 form");
+  if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
+    return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
+  c->harvest = states_device;
+  cudaError_t e = run_gradients(c);
+  if (e == cudaSuccess) e = run_step_tail(c, cfl);
+  c->harvest = nullptr;
+  if (e != cudaSuccess) return cuda_fail(c, e, "harvest step");
   c->grads_fresh = false;
   c->totals_fresh = true;
   c->have_step = true;

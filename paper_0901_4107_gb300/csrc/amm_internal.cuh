@@ -128,6 +128,7 @@ struct HydroView {
   DeviceStats* stats;
   // learned proposal (FP32 learned form only)
   const void* mlp;
+  float* harvest;              // if set, the flux kernel records each face's Riemann inputs [nf][6]
 };
 
 }  // namespace amm
@@ -182,7 +183,8 @@ struct amm_ctx {
   double* totals = nullptr;
   amm::DeviceStats* stats = nullptr;
   float* closure = nullptr;        // [n] relative closure error (creation only)
-  void* mlp = nullptr;             // device copy of the proposal weights
+  void* mlp = nullptr;             // device copy of the proposal weights (MlpDevice)
+  float* harvest = nullptr;        // set only during amm_harvest
   bool mlp_loaded = false;
   double* scratch = nullptr;       // layout conversions for getters/setters
   size_t scratch_size = 0;         // in doubles
@@ -233,5 +235,9 @@ template <typename real>
 cudaError_t launch_get_flux(amm_ctx* c, double* F_device);
 template <typename real>
 cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
+
+// flux_learned.cu: the FP32 flux kernel with the fused proposal network
+cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
+cudaError_t prepare_flux_learned();
 
 }  // namespace amm

@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include "amm_internal.cuh"
-#include "learned.cuh"
 #include "riemann.cuh"
 
 namespace amm {
@@ -257,26 +256,32 @@ __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real
            hdt * ((real)v.gamma * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
 }
 
-// B threads (faces) per CTA; a tile of FACE_TILE faces spans FACE_TILE/B CTAs
-template <typename real, bool LEARNED, int B>
-__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
-  constexpr int SUB = FACE_TILE / B;
-  const Tile t = v.ftiles[blockIdx.x / SUB];
-  const int k0 = t.begin + (int)(blockIdx.x % SUB) * B + (int)threadIdx.x;
-  const bool valid = k0 < t.end;
-  const int k = valid ? k0 : t.begin;
-  const GasC<real>& G = v.gas;
-  __shared__ real s_hdt;
-  if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
-  __syncthreads();
-  const real hdt = s_hdt;
+// Per-face state between the extrapolation (face_prepare) and the Riemann
+// solve + flux (face_finish); the learned form runs the proposal network
+// between the two on the tensor cores.
+template <typename real>
+struct FaceWork {
+  int k;
+  bool valid;
+  int2 lr;
+  real n[3], A, w[3];
+  real WppL[5], WppR[5];
+  real uL, uR;
+  int fallback;
+};
+
+template <typename real>
+__device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdt, FaceWork<real>& f) {
+  f.k = k;
+  f.valid = valid;
   const int2 lr = v.lr[k];
+  f.lr = lr;
   const R4<real> G0 = v.fgeo[2 * (size_t)k];
   const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
   const real n[3] = {G0.x, G0.y, G0.z};
   const real sep = G0.w;
   const real c[3] = {G1.x, G1.y, G1.z};
-  const real A = G1.w;
+  f.A = G1.w;
   // face velocity: mean of the generators' velocities plus the normal motion
   // of the face centroid from their relative motion about the midpoint
   real w[3] = {(real)0, (real)0, (real)0};
@@ -295,52 +300,62 @@ __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FAC
 #pragma unroll
     for (int d = 0; d < 3; d++) w[d] = (real)0.5 * (wl[d] + wr[d]) + rot * n[d];
   }
-  real WpL[5], WppL[5], WpR[5], WppR[5];
-  side_state(v, lr.x, (real)0.5, n, sep, c, w, hdt, WpL, WppL);
-  side_state(v, lr.y, (real)-0.5, n, sep, c, w, hdt, WpR, WppR);
-  FaceStats st = {0, 0, 0, 0, 0};
-  if (!(WppL[0] > (real)0) || !(WppL[4] > (real)0) || !(WppR[0] > (real)0) || !(WppR[4] > (real)0)) {
+  real WpL[5], WpR[5];
+  side_state(v, lr.x, (real)0.5, n, sep, c, w, hdt, WpL, f.WppL);
+  side_state(v, lr.y, (real)-0.5, n, sep, c, w, hdt, WpR, f.WppR);
+  f.fallback = 0;
+  if (!(f.WppL[0] > (real)0) || !(f.WppL[4] > (real)0) || !(f.WppR[0] > (real)0) || !(f.WppR[4] > (real)0)) {
 #pragma unroll
     for (int a = 0; a < 5; a++) {
-      WppL[a] = WpL[a];
-      WppR[a] = WpR[a];
+      f.WppL[a] = WpL[a];
+      f.WppR[a] = WpR[a];
     }
-    st.fallback = 1;
+    f.fallback = 1;
   }
   // rotate: normal component and transverse vector
-  const real uL = WppL[1] * n[0] + WppL[2] * n[1] + WppL[3] * n[2];
-  const real uR = WppR[1] * n[0] + WppR[2] * n[1] + WppR[3] * n[2];
-  real guess = (real)0;
-  bool have_guess = false;
-  if constexpr (LEARNED) {
-    guess = learned_guess<real>(v.mlp, WppL[0], WppL[4], uL, WppR[0], WppR[4], uR, G);
-    have_guess = true;
+  f.uL = f.WppL[1] * n[0] + f.WppL[2] * n[1] + f.WppL[3] * n[2];
+  f.uR = f.WppR[1] * n[0] + f.WppR[2] * n[1] + f.WppR[3] * n[2];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    f.n[d] = n[d];
+    f.w[d] = w[d];
   }
+  if (v.harvest && valid) {
+    float* h = v.harvest + 6 * (size_t)k;
+    h[0] = (float)f.WppL[0]; h[1] = (float)f.uL; h[2] = (float)f.WppL[4];
+    h[3] = (float)f.WppR[0]; h[4] = (float)f.uR; h[5] = (float)f.WppR[4];
+  }
+}
+
+// Riemann solve, flux of the moving face, stores, and the CTA's reductions
+// (largest |A F| per component, Newton statistics).  All B threads call it.
+template <typename real, int B>
+__device__ __forceinline__ void face_finish(const HydroView<real>& v, const FaceWork<real>& f, int box, int nf_here,
+                                            bool have_guess, real guess) {
+  const GasC<real>& G = v.gas;
+  const bool valid = f.valid;
   real rhoF, uF, pF;
   RiemannInfo info;
-  const int side = riemann_sample(WppL[0], uL, WppL[4], WppR[0], uR, WppR[4], G, v.tol, v.maxit, have_guess,
-                                  guess, rhoF, uF, pF, info);
-  st.iters = info.iters;
-  st.guard = info.guard;
-  st.vacuum = info.vacuum;
-  st.fail = info.fail;
-  const real* Wt = side ? WppR : WppL;
-  const real ut = side ? uR : uL;
+  const int side = riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.maxit,
+                                  have_guess, guess, rhoF, uF, pF, info);
+  const real* Wt = side ? f.WppR : f.WppL;
+  const real ut = side ? f.uR : f.uL;
   real vlab[3];
 #pragma unroll
-  for (int d = 0; d < 3; d++) vlab[d] = uF * n[d] + (Wt[1 + d] - ut * n[d]) + w[d];
+  for (int d = 0; d < 3; d++) vlab[d] = uF * f.n[d] + (Wt[1 + d] - ut * f.n[d]) + f.w[d];
   const real v2 = vlab[0] * vlab[0] + vlab[1] * vlab[1] + vlab[2] * vlab[2];
-  const real vn = vlab[0] * n[0] + vlab[1] * n[1] + vlab[2] * n[2];
+  const real vn = vlab[0] * f.n[0] + vlab[1] * f.n[1] + vlab[2] * f.n[2];
   const real mflux = rhoF * uF;
+  const real A = f.A;
   R4<real> fout;
   fout.x = A * mflux;
-  fout.y = A * (mflux * vlab[0] + pF * n[0]);
-  fout.z = A * (mflux * vlab[1] + pF * n[1]);
-  fout.w = A * (mflux * vlab[2] + pF * n[2]);
+  fout.y = A * (mflux * vlab[0] + pF * f.n[0]);
+  fout.z = A * (mflux * vlab[1] + pF * f.n[1]);
+  fout.w = A * (mflux * vlab[2] + pF * f.n[2]);
   const real fE = A * (((real)0.5 * rhoF * v2 + pF * G.inv_gm1) * uF + pF * vn);
   if (valid) {
-    v.flux[k] = fout;
-    v.fluxE[k] = fE;
+    v.flux[f.k] = fout;
+    v.fluxE[f.k] = fE;
   }
   if (sizeof(real) == 4 && v.fixed_acc) {
     // largest |A F| per component for the exact fixed-point sums (float bits
@@ -363,22 +378,22 @@ __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FAC
     if (threadIdx.x < 5) {
       unsigned r = 0u;
       for (int w = 0; w < B / 32; w++) r = wm[w][threadIdx.x] > r ? wm[w][threadIdx.x] : r;
-      atomicMax(v.fmax_bits + 5 * t.box + threadIdx.x, r);
+      atomicMax(v.fmax_bits + 5 * box + threadIdx.x, r);
     }
   }
   // statistics: warp reductions (no contended shared-memory atomics), one
   // slot per warp in shared memory, then a few global atomics per CTA
   const unsigned full = 0xffffffffu;
-  const unsigned it = valid ? (unsigned)st.iters : 0u;
+  const unsigned it = valid ? (unsigned)info.iters : 0u;
   unsigned mine[22];
 #pragma unroll
   for (int b = 0; b < 15; b++) mine[b] = __popc(__ballot_sync(full, valid && it == (unsigned)b));
   mine[15] = __popc(__ballot_sync(full, valid && it >= 15u));
   mine[16] = __reduce_add_sync(full, it);
-  mine[17] = __popc(__ballot_sync(full, valid && st.guard));
-  mine[18] = __popc(__ballot_sync(full, valid && st.vacuum));
-  mine[19] = __popc(__ballot_sync(full, valid && st.fail));
-  mine[20] = __popc(__ballot_sync(full, valid && st.fallback));
+  mine[17] = __popc(__ballot_sync(full, valid && info.guard));
+  mine[18] = __popc(__ballot_sync(full, valid && info.vacuum));
+  mine[19] = __popc(__ballot_sync(full, valid && info.fail));
+  mine[20] = __popc(__ballot_sync(full, valid && f.fallback));
   mine[21] = __reduce_max_sync(full, it);
   __shared__ unsigned sh[B / 32][22];
   const int wid = (int)threadIdx.x >> 5;
@@ -397,7 +412,6 @@ __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FAC
       if (tot) atomicAdd(&S->hist[s], (unsigned long long)tot);
     } else if (s == 16) {
       atomicAdd(&S->newton_iters, (unsigned long long)tot);
-      const int nf_here = min(B, t.end - (t.begin + (int)(blockIdx.x % SUB) * B));
       if (nf_here > 0) atomicAdd(&S->faces, (unsigned long long)nf_here);
     } else if (s == 17) {
       if (tot) atomicAdd(&S->guard, (unsigned long long)tot);
@@ -414,6 +428,22 @@ __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FAC
       if (tot) atomicMax(&S->newton_max, tot);
     }
   }
+}
+
+// B threads (faces) per CTA; a tile of FACE_TILE faces spans FACE_TILE/B CTAs
+template <typename real, int B>
+__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
+  constexpr int SUB = FACE_TILE / B;
+  const Tile t = v.ftiles[blockIdx.x / SUB];
+  const int first = t.begin + (int)(blockIdx.x % SUB) * B;
+  const int k0 = first + (int)threadIdx.x;
+  const bool valid = k0 < t.end;
+  __shared__ real s_hdt;
+  if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
+  __syncthreads();
+  FaceWork<real> f;
+  face_prepare(v, valid ? k0 : t.begin, valid, s_hdt, f);
+  face_finish<real, B>(v, f, t.box, min(B, t.end - first), false, (real)0);
 }
 
 // ------------------------------------------------------------ A8+A1+A9
@@ -737,6 +767,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.box_first_ctile = c->box_first_ctile;
   v.stats = c->stats;
   v.mlp = c->mlp;
+  v.harvest = c->harvest;
   return v;
 }
 
@@ -771,18 +802,15 @@ cudaError_t launch_flux(amm_ctx* c, double cfl) {
   const bool b128 = c->flux_block == 128;
   if (c->opt.precision == AMM_FP32_LEARNED) {
     if constexpr (sizeof(real) == 4) {
-      if (b128)
-        k_flux<real, true, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
-      else
-        k_flux<real, true, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
+      return launch_flux_learned(c, v);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
     if (b128)
-      k_flux<real, false, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+      k_flux<real, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
     else
-      k_flux<real, false, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
+      k_flux<real, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
   }
   return cudaGetLastError();
 }

@@ -14,7 +14,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include "riemann.cuh"
 
 namespace amm {
 
@@ -31,38 +30,5 @@ struct MlpDevice {
   float b2[MLP_HID];
   float b3;
 };
-
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
-
-// Per-thread inference on the CUDA cores (reference form of the fused
-// inference; the flux kernel of the learned form uses the tensor-core tile
-// version in learned_tc.cuh).
-template <typename real>
-__device__ __forceinline__ real learned_guess(const void* mlp, real rhoL, real pL, real uL, real rhoR, real pR,
-                                              real uR, const GasC<real>& G) {
-  const MlpDevice* M = (const MlpDevice*)mlp;
-  const float rb = 0.5f * ((float)rhoL + (float)rhoR);
-  const float pb = 0.5f * ((float)pL + (float)pR);
-  const float cb = sqrtf((float)G.g * pb / rb);
-  const float x[6] = {__logf((float)rhoL / rb), __logf((float)pL / pb), (float)uL / cb,
-                      __logf((float)rhoR / rb), __logf((float)pR / pb), (float)uR / cb};
-  float h1[MLP_HID];
-#pragma unroll 8
-  for (int o = 0; o < MLP_HID; o++) {
-    float z = M->b1[o];
-#pragma unroll
-    for (int k = 0; k < 6; k++) z += __bfloat162float(M->W1[o * 16 + k]) * x[k];
-    h1[o] = silu_f(z);
-  }
-  float y = M->b3;
-  for (int o = 0; o < MLP_HID; o++) {
-    float z = M->b2[o];
-#pragma unroll 16
-    for (int k = 0; k < MLP_HID; k++) z += __bfloat162float(M->W2[o * MLP_HID + k]) * h1[k];
-    y += __bfloat162float(M->W3[o]) * silu_f(z);
-  }
-  y = fminf(fmaxf(y, -40.0f), 40.0f);
-  return (real)(pb * __expf(y));
-}
 
 }  // namespace amm

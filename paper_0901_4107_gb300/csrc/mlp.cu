@@ -669,6 +669,29 @@ int amm_mlp_sync(amm_mlp* m) {
   return AMM_OK;
 }
 
+int amm_mlp_attach(amm_ctx* c, const amm_mlp* m) {
+  if (!c || !m) return AMM_ERR_INVALID_ARG;
+  if (c->opt.precision != AMM_FP32_LEARNED) {
+    c->err = "amm_mlp_attach: the context is not of the FP32 learned form";
+    return AMM_ERR_INVALID_ARG;
+  }
+  if (!c->mlp && cudaMalloc(&c->mlp, sizeof(amm::MlpDevice)) != cudaSuccess) {
+    c->err = "amm_mlp_attach: cudaMalloc failed";
+    return AMM_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(c->mlp, m->packed, sizeof(amm::MlpDevice), cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess ||
+      cudaStreamSynchronize(m->stream) != cudaSuccess || amm::prepare_flux_learned() != cudaSuccess) {
+    c->err = "amm_mlp_attach: copy failed";
+    return AMM_ERR_CUDA;
+  }
+  c->mlp_loaded = true;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return AMM_OK;
+}
+
 int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
                      void* stream) {
   if (!(gamma > 1.0) || n < 1 || !states_device || !x_device) return AMM_ERR_INVALID_ARG;

@@ -57,10 +57,15 @@ __device__ __forceinline__ void wave_curve(real p, real rhoK, real pK, real cK, 
 // Standard starting value: the linearised (primitive-variable) estimate when
 // the pressure ratio is small and it lies between p_L and p_R, else the
 // two-rarefaction estimate when it lies below both, else the two-shock
-// estimate evaluated at the linearised pressure; floored positive.
+// estimate evaluated at the linearised pressure; floored positive.  With a
+// proposal (`have`), the proposal replaces the two-shock estimate -- the one
+// approximate branch: the two-rarefaction estimate is the exact star pressure
+// when both waves are rarefactions, and the linearised one is kept where it
+// passes its own test.
 template <typename real>
 __device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real cL, real rhoR, real uR, real pR,
-                                               real cR, const GasC<real>& G) {
+                                               real cR, const GasC<real>& G, bool have = false,
+                                               real proposal = (real)0) {
   const real du = uR - uL;
   real ppv = (real)0.5 * (pL + pR) - (real)0.125 * du * (rhoL + rhoR) * (cL + cR);
   ppv = ppv > (real)0 ? ppv : (real)0;
@@ -72,6 +77,8 @@ __device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real
     const real num = cL + cR - (real)0.5 * G.gm1 * du;
     const real den = cL / xpow(pL, G.z) + cR / xpow(pR, G.z);
     p0 = xpow(num / den, G.inv_z);
+  } else if (have) {
+    p0 = proposal;
   } else {
     const real gL = xsqrt((G.two_gp1 / rhoL) / (ppv + G.gm1_gp1 * pL));
     const real gR = xsqrt((G.two_gp1 / rhoR) / (ppv + G.gm1_gp1 * pR));
@@ -220,7 +227,7 @@ __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real 
     rhoF = (real)0; uF = (real)0.5 * (frontL + frontR); pF = (real)0;
     return 0;
   }
-  real p0 = have_guess ? guess : standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G);
+  const real p0 = standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, have_guess, guess);
   NewtonTail<real> nt;
   const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, maxit, info, nt);
   const real us = (real)0.5 * (uL + uR) + (real)0.5 * ((nt.fR - nt.fL) + (nt.dR - nt.dL) * nt.dp);
