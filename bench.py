@@ -368,6 +368,34 @@ def main():
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": "%d full oracle steps of the workload (%d faces each), one host thread"
                                               % (kcpu, nf)}
+        # FP32 learned form: proposal trained on the method's own face states
+        # (harvested from the 2D shock tube and 3D turbulent boxes), then the
+        # same timed loop
+        from paper_0901_4107_gb300 import learned
+        from harness import ics as _ics
+        t_tr = time.perf_counter()
+        net, tstats = learned.train_proposal(_ics, torch, small=False, epochs=4)
+        tstats["train_seconds"] = time.perf_counter() - t_tr
+        ctxl = make("fp32_learned")
+        amm.amm_mlp_attach(ctxl, net)
+        amm.amm_autotune(ctxl, CFL, reps=2)
+        kl = max(3, min(args.steps, 500))
+        msl, kerl, walll = timed_form(amm, torch, ctxl, Q0d, kl, min(args.warmup, 5), stream, flush)
+        forms["fp32_learned"] = {"value": nf / (statistics.mean(msl) * 1e-3), "ms_per_step": statistics.mean(msl),
+                                 "steps": kl, "kernels_ms": kerl, "training": tstats}
+        # Newton iterations per face from the same input, each form
+        for name, ctx in (("fp32", ctx32), ("fp32_learned", ctxl), ("fp64", ctx64)):
+            amm.amm_set_state(ctx, Q0)
+            amm.amm_reset_stats(ctx)
+            amm.amm_advance(ctx, CFL, 1, False)
+            s = amm.amm_get_stats(ctx)
+            forms[name]["newton_iters_per_face"] = s["newton_iters"] / max(1, s["faces"])
+            forms[name]["newton_hist"] = s["newton_hist"][:8]
+        if not args.no_cpu:
+            amm.amm_set_state(ctxl, Q0)
+            amm.amm_step(ctxl, dt)
+            emax, e999 = parity_errors(amm.amm_get_state(ctxl), ref, Q0, W0, 3, P.gamma)
+            forms["fp32_learned"].update({"err_max": emax, "err_p999": e999})
         # end to end through the C ABI with pinned host buffers
         Qh = torch.from_numpy(Q0.copy()).pin_memory()
         Qo = torch.empty_like(Qh).pin_memory()
@@ -385,8 +413,6 @@ def main():
         e2e_s = (time.perf_counter() - t0) / ke
         line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": Q0.nbytes,
                        "d2h_bytes_per_step": Q0.nbytes, "ms_per_step": 1e3 * e2e_s, "steps": ke}
-        st = amm.amm_get_stats(ctx32)
-        line["newton_iters_per_face"] = st["newton_iters"] / max(1, st["faces"])
         line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -181,3 +181,53 @@ def boosted(problem, v0):
     v0 = np.asarray(v0, np.float64)
     return Problem(problem.name + "_boosted", problem.dim, problem.gamma, problem.tess, problem.rho.copy(),
                    problem.vel + v0[None, :], problem.pres.copy(), dict(problem.meta, boost=v0.tolist()))
+
+
+@dataclass
+class Ensemble:
+    """Independent periodic boxes concatenated into one face list: global cell
+    indices, per-box box lengths and the cell/face offsets of each box."""
+    dim: int
+    points: np.ndarray
+    cells: np.ndarray
+    shift: np.ndarray
+    area: np.ndarray
+    centroid: np.ndarray
+    box: np.ndarray            # [n_boxes, dim]
+    Q: np.ndarray
+    box_cells: np.ndarray      # [n_boxes+1]
+    box_faces: np.ndarray      # [n_boxes+1]
+    gamma: float
+    problems: list
+
+    @property
+    def n_cells(self):
+        return len(self.points)
+
+    @property
+    def n_faces(self):
+        return len(self.area)
+
+
+def concat(problems):
+    """Concatenates problems (same dim and gamma) into an Ensemble."""
+    dim = problems[0].dim
+    gamma = problems[0].gamma
+    pts, cells, sh, ar, cen, boxes, Qs = [], [], [], [], [], [], []
+    bc, bf = [0], [0]
+    for P in problems:
+        assert P.dim == dim and P.gamma == gamma
+        T = P.tess
+        off = bc[-1]
+        pts.append(T.points)
+        cells.append(T.cells + off)
+        sh.append(T.shift)
+        ar.append(T.area)
+        cen.append(T.centroid)
+        boxes.append(T.box)
+        Qs.append(P.conserved())
+        bc.append(off + T.n_cells)
+        bf.append(bf[-1] + T.n_faces)
+    return Ensemble(dim, np.concatenate(pts), np.concatenate(cells).astype(np.int32), np.concatenate(sh),
+                    np.concatenate(ar), np.concatenate(cen), np.stack(boxes), np.concatenate(Qs),
+                    np.asarray(bc, np.int64), np.asarray(bf, np.int64), gamma, list(problems))

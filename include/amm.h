@@ -178,6 +178,10 @@ int amm_get_totals(amm_ctx* ctx, double* tot);              /* [n_boxes][dim+2],
 int amm_get_dt(amm_ctx* ctx, double* dt);                   /* [n_boxes], time step of the last step */
 int amm_get_generators(amm_ctx* ctx, double* gen);          /* [n_cells][dim] */
 int amm_get_stats(amm_ctx* ctx, amm_stats* stats);
+/* Per-box status bits since the last reset, host [n_boxes] (bit 0 Newton cap,
+ * bit 1 non-positive cell): boxes are independent, so a failed box does not
+ * affect the others, which complete normally. */
+int amm_get_box_status(amm_ctx* ctx, uint32_t* status);
 int amm_reset_stats(amm_ctx* ctx);
 
 /* Per-kernel timing for roofline measurements.  With profiling on, every
@@ -198,6 +202,9 @@ typedef struct amm_tuning {
   int grad_lanes;
   int update_lanes;
   int flux_block;
+  int persistent;  /* 1: amm_advance runs each step as ONE cooperative launch whose CTAs walk
+                      every phase (gradients, fluxes, update, totals) with grid barriers between
+                      them (bounded waits); 0: one launch per phase.  Not for AMM_FP32_LEARNED. */
   float step_ms;   /* amm_autotune: sum of the chosen kernels' median times */
 } amm_tuning;
 
@@ -206,8 +213,10 @@ int amm_get_tuning(amm_ctx* ctx, amm_tuning* t);
 
 /* Times every launch shape on this context's own mesh and state (reps steps
  * each from the same state, restored afterwards; device events on the
- * context's stream), keeps the fastest per kernel and returns it in *out
- * (may be NULL).  Synchronises; allocates one state-sized temporary. */
+ * context's stream), keeps the fastest per kernel, then times whole steps
+ * of that kernel sequence against the persistent single launch and keeps
+ * the faster; returns the choice in *out (may be NULL).  Synchronises;
+ * allocates one state-sized temporary. */
 int amm_autotune(amm_ctx* ctx, double cfl, int reps, amm_tuning* out);
 
 /* ---------------------------------------------------------------------------

@@ -83,6 +83,7 @@ _SIGS = {
     "amm_get_generators": (_I, [_P, _P]),
     "amm_get_stats": (_I, [_P, _P]),
     "amm_reset_stats": (_I, [_P]),
+    "amm_get_box_status": (_I, [_P, _P]),
     "amm_profile": (_I, [_P, _I]),
     "amm_set_tuning": (_I, [_P, _P]),
     "amm_get_tuning": (_I, [_P, _P]),
@@ -315,6 +316,12 @@ def amm_get_stats(ctx):
     return d
 
 
+def amm_get_box_status(ctx):
+    s = np.empty(ctx.nboxes, np.uint32)
+    _check(ctx, lib().amm_get_box_status(ctx.handle, s.ctypes.data))
+    return s
+
+
 def amm_reset_stats(ctx):
     _check(ctx, lib().amm_reset_stats(ctx.handle))
 
@@ -334,15 +341,15 @@ def amm_get_kernel_times(ctx):
 
 class amm_tuning(ctypes.Structure):
     _fields_ = [("grad_lanes", ctypes.c_int), ("update_lanes", ctypes.c_int), ("flux_block", ctypes.c_int),
-                ("step_ms", ctypes.c_float)]
+                ("persistent", ctypes.c_int), ("step_ms", ctypes.c_float)]
 
 
 def _tuning_dict(t):
     return {f: getattr(t, f) for f, _ in amm_tuning._fields_}
 
 
-def amm_set_tuning(ctx, grad_lanes=4, update_lanes=4, flux_block=256):
-    t = amm_tuning(int(grad_lanes), int(update_lanes), int(flux_block), 0.0)
+def amm_set_tuning(ctx, grad_lanes=4, update_lanes=4, flux_block=256, persistent=0):
+    t = amm_tuning(int(grad_lanes), int(update_lanes), int(flux_block), int(persistent), 0.0)
     _check(ctx, lib().amm_set_tuning(ctx.handle, ctypes.byref(t)))
 
 

@@ -92,6 +92,7 @@ template <typename real>
 struct HydroView {
   int dim, mode, limit, maxit, nboxes;
   int n, nf;
+  int n_ctiles, n_ftiles;
   double gamma, tol;
   real tol_r;                  // tol in the bulk type
   GasC<real> gas;
@@ -126,6 +127,7 @@ struct HydroView {
   double* totals;             // [nboxes][5]
   const int* box_first_ctile; // [nboxes+1]
   DeviceStats* stats;
+  unsigned* box_status;        // [nboxes] StatusBits of each box
   // learned proposal (FP32 learned form only)
   const void* mlp;
   float* harvest;              // if set, the flux kernel records each face's Riemann inputs [nf][6]
@@ -177,11 +179,14 @@ struct amm_ctx {
   int update_lanes = 4;            // lanes per cell in the update kernel
   int flux_block = 256;            // threads (faces) per CTA of the flux kernel
   float tuned_ms = 0.f;
+  int persistent = 0;              // 1: one cooperative launch per step (amm_advance)
+  unsigned* barrier = nullptr;     // grid-barrier counter and generation
   double* dt_box = nullptr;
   double* dt_used = nullptr;
   double* partial = nullptr;
   double* totals = nullptr;
   amm::DeviceStats* stats = nullptr;
+  unsigned* box_status = nullptr;  // [nboxes]
   float* closure = nullptr;        // [n] relative closure error (creation only)
   void* mlp = nullptr;             // device copy of the proposal weights (MlpDevice)
   float* harvest = nullptr;        // set only during amm_harvest
@@ -196,6 +201,7 @@ struct amm_ctx {
   cudaGraphExec_t graph = nullptr;
   double graph_cfl = -1.0;
   bool graph_profiled = false;
+  bool graph_persistent = false;
   // per-kernel timing: events recorded between the kernels of a step
   bool profiling = false;
   cudaEvent_t prof_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -239,5 +245,9 @@ cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
 // flux_learned.cu: the FP32 flux kernel with the fused proposal network
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
 cudaError_t prepare_flux_learned();
+
+// persistent.cu: the whole step as one cooperative launch
+template <typename real>
+cudaError_t launch_step_persistent(amm_ctx* c, double cfl);
 
 }  // namespace amm

@@ -98,13 +98,14 @@ __device__ __forceinline__ T group_min(T x) {
   return x;
 }
 
+// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads)
 template <typename real, int G>
-__global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradients(HydroView<real> v) {
+__device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
   constexpr int UNR = 1;                               // incidences in flight per lane
-  const Tile t = v.ctiles[blockIdx.x / G];
+  const Tile t = v.ctiles[wi / G];
   const int lane = (int)threadIdx.x % G;
-  const int i = t.begin + (int)(blockIdx.x % G) * CELLS + (int)threadIdx.x / G;
+  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
   const bool valid = i < t.end;
   const int ii = valid ? i : t.begin;
   const R4<real> Wi = v.W[ii];
@@ -221,6 +222,12 @@ __global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradie
     if (md > 0.0 && md < 1.0e300)
       atomicMin(v.cour_bits + t.box, (unsigned long long)__double_as_longlong(md));
   }
+  __syncthreads();   // `wmin` is reused by the next work item of a persistent CTA
+}
+
+template <typename real, int G>
+__global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradients(HydroView<real> v) {
+  grad_item<real, G>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ A5+A6+A7
@@ -421,6 +428,7 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
       if (tot) {
         atomicAdd(&S->newton_fail, (unsigned long long)tot);
         atomicOr(&S->status, (unsigned)ST_NEWTON_CAP);
+        atomicOr(v.box_status + box, (unsigned)ST_NEWTON_CAP);
       }
     } else if (s == 20) {
       if (tot) atomicAdd(&S->fallback, (unsigned long long)tot);
@@ -432,10 +440,10 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
 
 // B threads (faces) per CTA; a tile of FACE_TILE faces spans FACE_TILE/B CTAs
 template <typename real, int B>
-__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
+__device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
   constexpr int SUB = FACE_TILE / B;
-  const Tile t = v.ftiles[blockIdx.x / SUB];
-  const int first = t.begin + (int)(blockIdx.x % SUB) * B;
+  const Tile t = v.ftiles[wi / SUB];
+  const int first = t.begin + (int)(wi % SUB) * B;
   const int k0 = first + (int)threadIdx.x;
   const bool valid = k0 < t.end;
   __shared__ real s_hdt;
@@ -444,6 +452,11 @@ __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FAC
   FaceWork<real> f;
   face_prepare(v, valid ? k0 : t.begin, valid, s_hdt, f);
   face_finish<real, B>(v, f, t.box, min(B, t.end - first), false, (real)0);
+}
+
+template <typename real, int B>
+__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
+  flux_item<real, B>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ A8+A1+A9
@@ -481,11 +494,11 @@ __device__ __forceinline__ double fixed_scale(int eb, int headroom) {
 // the cell's incidences l, l+G, ...; the lane partial sums are combined with
 // shuffles and lane 0 applies the update.
 template <typename real, int G>
-__global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
+__device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   constexpr int CELLS = CELL_TILE / G;
-  const Tile t = v.ctiles[blockIdx.x / G];
+  const Tile t = v.ctiles[wi / G];
   const int lane = (int)threadIdx.x % G;
-  const int i = t.begin + (int)(blockIdx.x % G) * CELLS + (int)threadIdx.x / G;
+  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
   const bool valid = i < t.end;
   const int q0 = valid ? v.csr_off[i] : 0;
   const int q1 = valid ? v.csr_off[i + 1] : 0;
@@ -567,12 +580,19 @@ __global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
   if (threadIdx.x < 5) {
     double s = red[0][threadIdx.x];
     for (int w = 1; w < CELL_TILE / 32; w++) s += red[w][threadIdx.x];
-    v.partial[5 * (size_t)blockIdx.x + threadIdx.x] = s;
+    v.partial[5 * (size_t)wi + threadIdx.x] = s;
   }
   if (threadIdx.x == 0 && nbad) {
     atomicAdd(&v.stats->nonpos, (unsigned long long)nbad);
     atomicOr(&v.stats->status, (unsigned)ST_NONPOS);
+    atomicOr(v.box_status + t.box, (unsigned)ST_NONPOS);
   }
+  __syncthreads();   // `red` is reused by the next work item of a persistent CTA
+}
+
+template <typename real, int G>
+__global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
+  update_item<real, G>(v, blockIdx.x);
 }
 
 // per-tile sums of the current Q (used when no step has produced them)
@@ -601,19 +621,18 @@ __global__ void __launch_bounds__(CELL_TILE) k_partial_sums(HydroView<real> v) {
 
 // one CTA per box: ordered sum of the box's block partials; time step record
 constexpr int FINISH_THREADS = 512;
-template <typename real>
-__global__ void k_finish(HydroView<real> v, int count_step) {
-  const int b = blockIdx.x;
+template <typename real, int NT>
+__device__ __forceinline__ void finish_item(const HydroView<real>& v, int b, int count_step) {
   const int t0 = v.box_first_ctile[b] * v.update_lanes, t1 = v.box_first_ctile[b + 1] * v.update_lanes;
-  __shared__ double red[5][FINISH_THREADS];
+  __shared__ double red[5][NT];
   double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int tt = t0 + (int)threadIdx.x; tt < t1; tt += FINISH_THREADS)
+  for (int tt = t0 + (int)threadIdx.x; tt < t1; tt += NT)
 #pragma unroll
     for (int a = 0; a < 5; a++) s[a] += v.partial[5 * (size_t)tt + a];
 #pragma unroll
   for (int a = 0; a < 5; a++) red[a][threadIdx.x] = s[a];
   __syncthreads();
-  for (int st = FINISH_THREADS / 2; st > 0; st >>= 1) {
+  for (int st = NT / 2; st > 0; st >>= 1) {
     if ((int)threadIdx.x < st) {
 #pragma unroll
       for (int a = 0; a < 5; a++) red[a][threadIdx.x] += red[a][threadIdx.x + st];
@@ -625,6 +644,12 @@ __global__ void k_finish(HydroView<real> v, int count_step) {
     v.dt_used[b] = box_dt(v, b);
     if (b == 0) atomicAdd(&v.stats->steps, 1ull);
   }
+  __syncthreads();   // `red` is reused when one CTA finishes several boxes
+}
+
+template <typename real>
+__global__ void k_finish(HydroView<real> v, int count_step) {
+  finish_item<real, FINISH_THREADS>(v, blockIdx.x, count_step);
 }
 
 // ------------------------------------------------------------ layout moves
@@ -731,6 +756,8 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.nboxes = c->nboxes;
   v.n = (int)c->n;
   v.nf = (int)c->nf;
+  v.n_ctiles = c->n_ctiles;
+  v.n_ftiles = c->n_ftiles;
   v.gamma = c->gamma;
   v.tol = c->opt.riemann_tol;
   v.tol_r = (real)c->opt.riemann_tol;
@@ -766,6 +793,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.totals = c->totals;
   v.box_first_ctile = c->box_first_ctile;
   v.stats = c->stats;
+  v.box_status = c->box_status;
   v.mlp = c->mlp;
   v.harvest = c->harvest;
   return v;
