@@ -18,11 +18,70 @@
  * gradients grad[i][var][axis] with var over the D+2 primitives.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define NV_MAX 5 /* D + 2 primitives for D <= 3 */
+
+/* ------------------------------------------------------------ host threads
+ * The per-cell and per-face loops have independent iterations.  They may run
+ * on several host threads: [0, n) is cut into contiguous chunks, one per
+ * thread, and every element runs the same code whatever the thread count.
+ * The only results shared between elements are integer counters (summed per
+ * chunk, then over the chunks) and the time-step minimum (taken afterwards
+ * over the per-cell values), so the output does not depend on the thread
+ * count.  One thread by default. */
+typedef void (*elem_fn)(const void* args, long i, int64_t* counters);
+
+typedef struct {
+  elem_fn fn;
+  const void* args;
+  long lo, hi;
+  int64_t cnt[4];
+} chunk_job;
+
+static int ora_threads = 1;
+
+void ora_set_threads(int t) { ora_threads = t < 1 ? 1 : (t > 256 ? 256 : t); }
+int ora_get_threads(void) { return ora_threads; }
+
+static void* run_chunk(void* p) {
+  chunk_job* j = (chunk_job*)p;
+  for (long i = j->lo; i < j->hi; i++) j->fn(j->args, i, j->cnt);
+  return NULL;
+}
+
+/* fn(args, i, counters) for i in [0, n); counters (4 slots, may be NULL)
+ * receive the sums of the per-chunk counters */
+static void par_for(long n, elem_fn fn, const void* args, int64_t* counters) {
+  int T = ora_threads;
+  if ((long)T > n) T = n > 0 ? (int)n : 1;
+  chunk_job* jobs = (chunk_job*)calloc((size_t)T, sizeof(chunk_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+  char* started = (char*)calloc((size_t)T, 1);
+  for (int c = 0; c < T; c++) {
+    jobs[c].fn = fn;
+    jobs[c].args = args;
+    jobs[c].lo = n * c / T;
+    jobs[c].hi = n * (c + 1) / T;
+  }
+  for (int c = 1; c < T; c++) started[c] = pthread_create(&th[c], NULL, run_chunk, &jobs[c]) == 0;
+  run_chunk(&jobs[0]);
+  for (int c = 1; c < T; c++) {
+    if (started[c])
+      pthread_join(th[c], NULL);
+    else
+      run_chunk(&jobs[c]);
+  }
+  if (counters)
+    for (int c = 0; c < T; c++)
+      for (int q = 0; q < 4; q++) counters[q] += jobs[c].cnt[q];
+  free(jobs);
+  free(th);
+  free(started);
+}
 
 /* ------------------------------------------------------------------ helpers */
 
@@ -135,9 +194,22 @@ int ora_geometry(int dim, long n, const double* gen, long nf, const int32_t* cel
 /* ------------------------------------------------ A1: conserved -> primitive
  * Sec. 3, step 2 and the equation of state P = (gamma-1) rho u:
  * rho = m/V, v = p/m, P = (gamma-1) (E/V - rho |v|^2 / 2). */
-void ora_primitives(int dim, long n, const double* Q, const double* V, double gamma, double* W) {
+typedef struct {
+  int dim;
+  const double *Q, *V;
+  double gamma;
+  double* W;
+} prim_args;
+
+static void prim_cell(const void* a, long i, int64_t* counters) {
+  (void)counters;
+  const prim_args* A = (const prim_args*)a;
+  const int dim = A->dim;
+  const double *Q = A->Q, *V = A->V;
+  const double gamma = A->gamma;
+  double* W = A->W;
   const int nv = dim + 2;
-  for (long i = 0; i < n; i++) {
+  {
     const double m = Q[i * nv];
     const double rho = m / V[i];
     double v2 = 0.0;
@@ -152,6 +224,11 @@ void ora_primitives(int dim, long n, const double* Q, const double* V, double ga
   }
 }
 
+void ora_primitives(int dim, long n, const double* Q, const double* V, double gamma, double* W) {
+  const prim_args A = {dim, Q, V, gamma, W};
+  par_for(n, prim_cell, &A, NULL);
+}
+
 /* ---------------------------------------------- A2 + A3: gradients, limiter
  * Gradient, eq. (eqngrad2), Sec. 3.1:
  *   <grad phi>_i = (1/V_i) sum_j A_ij ( [phi_j - phi_i] c_ij / r_ij
@@ -162,12 +239,30 @@ void ora_primitives(int dim, long n, const double* Q, const double* V, double ga
  * (phi_min - phi_i)/dphi for dphi<0, 1 for dphi=0, dphi = grad . (f_ij - s_i);
  * phi_max/phi_min over the neighbours and the cell itself (the paper's second
  * "max" is read as "min").  grad: [n][dim+2][dim]. */
-void ora_gradients(int dim, long n, const double* W, const double* gen, const double* V, const double* s, long nf,
-                   const int32_t* cells, const int8_t* shift, const double* area, const double* cen,
-                   const double* box, int limit, double* grad) {
+typedef struct {
+  int dim;
+  const double *W, *gen, *V, *s;
+  const int32_t* cells;
+  const int8_t* shift;
+  const double *area, *cen, *box;
+  int limit;
+  double* grad;
+  const incidence* I;
+} grad_args;
+
+static void grad_cell(const void* a, long i, int64_t* counters) {
+  (void)counters;
+  const grad_args* A = (const grad_args*)a;
+  const int dim = A->dim;
+  const double *W = A->W, *gen = A->gen, *V = A->V, *s = A->s;
+  const int32_t* cells = A->cells;
+  const int8_t* shift = A->shift;
+  const double *area = A->area, *cen = A->cen, *box = A->box;
+  const int limit = A->limit;
+  double* grad = A->grad;
+  const incidence I = *A->I;
   const int nv = dim + 2;
-  incidence I = build_incidence(n, nf, cells);
-  for (long i = 0; i < n; i++) {
+  {
     double g[NV_MAX][3];
     for (int v = 0; v < nv; v++)
       for (int d = 0; d < 3; d++) g[v][d] = 0.0;
@@ -226,6 +321,14 @@ void ora_gradients(int dim, long n, const double* W, const double* gen, const do
     for (int v = 0; v < nv; v++)
       for (int d = 0; d < dim; d++) grad[(i * nv + v) * dim + d] = g[v][d];
   }
+}
+
+void ora_gradients(int dim, long n, const double* W, const double* gen, const double* V, const double* s, long nf,
+                   const int32_t* cells, const int8_t* shift, const double* area, const double* cen,
+                   const double* box, int limit, double* grad) {
+  incidence I = build_incidence(n, nf, cells);
+  const grad_args A = {dim, W, gen, V, s, cells, shift, area, cen, box, limit, grad, &I};
+  par_for(n, grad_cell, &A, NULL);
   free_incidence(&I);
 }
 
@@ -233,11 +336,21 @@ void ora_gradients(int dim, long n, const double* W, const double* gen, const do
  * Eq. (EqnTiStep), Sec. 7.1: dt_i = C_CFL R_i / (c_i + |v_i - w_i|), with
  * R_i = (3 V_i / 4 pi)^(1/3) in 3D, (V_i / pi)^(1/2) in 2D, c_i = sqrt(gamma
  * P/rho); the global step is the minimum over cells.  wmesh may be NULL (0). */
-double ora_timestep(int dim, long n, const double* W, const double* V, const double* wmesh, double gamma,
-                    double cfl, double* dt_cell) {
+typedef struct {
+  int dim;
+  const double *W, *V, *wmesh;
+  double gamma, cfl;
+  double* dt_cell;
+} ts_args;
+
+static void ts_cell(const void* a, long i, int64_t* counters) {
+  (void)counters;
+  const ts_args* A = (const ts_args*)a;
+  const int dim = A->dim;
+  const double *W = A->W, *V = A->V, *wmesh = A->wmesh;
+  const double gamma = A->gamma, cfl = A->cfl;
   const int nv = dim + 2;
-  double dtmin = INFINITY;
-  for (long i = 0; i < n; i++) {
+  {
     const double rho = W[i * nv], P = W[i * nv + dim + 1];
     const double R = (dim == 3) ? cbrt(3.0 * V[i] / (4.0 * M_PI)) : sqrt(V[i] / M_PI);
     const double c = sqrt(gamma * P / rho);
@@ -247,9 +360,19 @@ double ora_timestep(int dim, long n, const double* W, const double* V, const dou
       vr += dv * dv;
     }
     const double dt = cfl * R / (c + sqrt(vr));
-    if (dt_cell) dt_cell[i] = dt;
-    if (dt < dtmin) dtmin = dt;
+    A->dt_cell[i] = dt;
   }
+}
+
+double ora_timestep(int dim, long n, const double* W, const double* V, const double* wmesh, double gamma,
+                    double cfl, double* dt_cell) {
+  double* dtc = dt_cell ? dt_cell : (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  const ts_args A = {dim, W, V, wmesh, gamma, cfl, dtc};
+  par_for(n, ts_cell, &A, NULL);
+  double dtmin = INFINITY;
+  for (long i = 0; i < n; i++)
+    if (dtc[i] < dtmin) dtmin = dtc[i];
+  if (!dt_cell) free(dtc);
   return dtmin;
 }
 
@@ -482,9 +605,23 @@ long ora_riemann_batch(double g, long m, const double* WL, const double* WR, dou
  * Sec. 3.3 (Fig. FigSketchVelFace): w = (w_L + w_R)/2 + w', with
  * w' = [(w_L - w_R) . (f - (r_R + r_L)/2)] / |r_R - r_L| * (r_R - r_L)/|r_R - r_L|.
  * wface: [nf][dim].  wmesh NULL means a static mesh. */
-void ora_face_velocities(int dim, long nf, const int32_t* cells, const int8_t* shift, const double* gen,
-                         const double* cen, const double* box, const double* wmesh, double* wface) {
-  for (long k = 0; k < nf; k++) {
+typedef struct {
+  int dim;
+  const int32_t* cells;
+  const int8_t* shift;
+  const double *gen, *cen, *box, *wmesh;
+  double* wface;
+} fv_args;
+
+static void fv_face(const void* a, long k, int64_t* counters) {
+  (void)counters;
+  const fv_args* A = (const fv_args*)a;
+  const int dim = A->dim;
+  const int32_t* cells = A->cells;
+  const int8_t* shift = A->shift;
+  const double *gen = A->gen, *cen = A->cen, *box = A->box, *wmesh = A->wmesh;
+  double* wface = A->wface;
+  {
     const int L = cells[2 * k], R = cells[2 * k + 1];
     double rL[3], rR[3];
     face_positions(dim, k, gen, cells, shift, box, rL, rR);
@@ -503,6 +640,12 @@ void ora_face_velocities(int dim, long nf, const int32_t* cells, const int8_t* s
       wface[k * dim + d] = 0.5 * (wR + wL) + proj / sep * (rR[d] - rL[d]) / sep;
     }
   }
+}
+
+void ora_face_velocities(int dim, long nf, const int32_t* cells, const int8_t* shift, const double* gen,
+                         const double* cen, const double* box, const double* wmesh, double* wface) {
+  const fv_args A = {dim, cells, shift, gen, cen, box, wmesh, wface};
+  par_for(nf, fv_face, &A, NULL);
 }
 
 /* ------------------------------------------------- A6: MUSCL-Hancock flux
@@ -527,17 +670,46 @@ void ora_face_velocities(int dim, long nf, const int32_t* cells, const int8_t* s
  * F: [nf][dim+2] per unit area (not multiplied by A).
  * counters: [0] fallback faces, [1] vacuum faces, [2] Newton iterations,
  * [3] Newton failures.  Returns 0, or -1 if any Newton solve failed. */
+typedef struct {
+  int dim;
+  const double *W, *grad, *gen, *s, *wface;
+  const int32_t* cells;
+  const int8_t* shift;
+  const double *cen, *box;
+  double gamma, dt, tol;
+  int maxit;
+  double* F;
+} flux_args;
+
+static void flux_face(const void* a, long k, int64_t* counters);
+
 int ora_fluxes(int dim, long n, const double* W, const double* grad, const double* gen, const double* s,
                const double* wmesh, long nf, const int32_t* cells, const int8_t* shift, const double* area,
                const double* cen, const double* box, double gamma, double dt, double tol, int maxit, double* F,
                int64_t* counters) {
   (void)n;
   (void)area;
-  const int nv = dim + 2;
   double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
   ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
-  int rc = 0;
-  for (long k = 0; k < nf; k++) {
+  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F};
+  const int64_t fails_before = counters[3];
+  par_for(nf, flux_face, &A, counters);
+  free(wface);
+  return counters[3] > fails_before ? -1 : 0;
+}
+
+static void flux_face(const void* a, long k, int64_t* counters) {
+  const flux_args* A = (const flux_args*)a;
+  const int dim = A->dim;
+  const double *W = A->W, *grad = A->grad, *gen = A->gen, *s = A->s, *wface = A->wface;
+  const int32_t* cells = A->cells;
+  const int8_t* shift = A->shift;
+  const double *cen = A->cen, *box = A->box;
+  const double gamma = A->gamma, dt = A->dt, tol = A->tol;
+  const int maxit = A->maxit;
+  double* F = A->F;
+  const int nv = dim + 2;
+  {
     const int cellK[2] = {cells[2 * k], cells[2 * k + 1]};
     double rL[3], rR[3];
     face_positions(dim, k, gen, cells, shift, box, rL, rR);
@@ -608,10 +780,7 @@ int ora_fluxes(int dim, long n, const double* W, const double* grad, const doubl
     int it = 0;
     const int st = ora_riemann(gamma, WLr, WRr, tol, maxit, out, &it);
     counters[2] += it;
-    if (st < 0) {
-      counters[3]++;
-      rc = -1;
-    }
+    if (st < 0) counters[3]++;
     if (st == 1) counters[1]++;
     const double rhoF = out[0], uF = out[1], PF = out[2];
     const int up = (out[5] > 0.5) ? 1 : 0;
@@ -627,19 +796,40 @@ int ora_fluxes(int dim, long n, const double* W, const double* grad, const doubl
     for (int d = 0; d < dim; d++) Fk[1 + d] = rhoF * vlab[d] * uF + PF * nrm[d];
     Fk[dim + 1] = (0.5 * rhoF * v2 + PF / (gamma - 1.0)) * uF + PF * vn;
   }
-  free(wface);
-  return rc;
 }
 
 /* ------------------------------------------------- A8: conservative update
  * Eq. (eqnupdate): Q_i^{n+1} = Q_i^n - dt sum_j A_ij F_ij, where the flux
  * F_ij leaves cell i through face (i,j); with the face normal pointing from
  * L to R that is +F for the left cell and -F for the right cell. */
+typedef struct {
+  int dim;
+  const double *Q, *area, *F;
+  double dt;
+  double* Qnew;
+  const incidence* I;
+} upd_args;
+
+static void upd_cell(const void* a, long i, int64_t* counters);
+
 void ora_update(int dim, long n, const double* Q, long nf, const int32_t* cells, const double* area,
                 const double* F, double dt, double* Qnew) {
-  const int nv = dim + 2;
   incidence I = build_incidence(n, nf, cells);
-  for (long i = 0; i < n; i++) {
+  const upd_args A = {dim, Q, area, F, dt, Qnew, &I};
+  par_for(n, upd_cell, &A, NULL);
+  free_incidence(&I);
+}
+
+static void upd_cell(const void* a, long i, int64_t* counters) {
+  (void)counters;
+  const upd_args* A = (const upd_args*)a;
+  const int dim = A->dim;
+  const double *Q = A->Q, *area = A->area, *F = A->F;
+  const double dt = A->dt;
+  double* Qnew = A->Qnew;
+  const incidence I = *A->I;
+  const int nv = dim + 2;
+  {
     double sum[NV_MAX] = {0, 0, 0, 0, 0};
     for (long q = I.off[i]; q < I.off[i + 1]; q++) {
       const long k = I.face[q];
@@ -648,7 +838,6 @@ void ora_update(int dim, long n, const double* Q, long nf, const int32_t* cells,
     }
     for (int v = 0; v < nv; v++) Qnew[i * nv + v] = Q[i * nv + v] - dt * sum[v];
   }
-  free_incidence(&I);
 }
 
 /* ------------------------------------------------ A9: conservation sums */

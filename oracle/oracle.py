@@ -46,8 +46,22 @@ def lib():
         L.ora_step.restype = _I
         L.ora_step.argtypes = [_I, _L, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _P, _D, _D, _I, _D, _I,
                                _P, _P, _P]
+        L.ora_set_threads.restype = None
+        L.ora_set_threads.argtypes = [_I]
+        L.ora_get_threads.restype = _I
+        L.ora_get_threads.argtypes = []
         _lib = L
     return _lib
+
+
+def set_threads(t):
+    """Host threads for the per-cell and per-face loops (default 1); the
+    results do not depend on it."""
+    lib().ora_set_threads(int(t))
+
+
+def get_threads():
+    return lib().ora_get_threads()
 
 
 def _c(a, dtype):

@@ -454,3 +454,22 @@ def test_sod_converges_to_exact_solution():
         errs.append(np.sum(np.abs(rho - ex) * V) / V.sum())
     assert errs[1] < 0.75 * errs[0]
     assert errs[1] < 0.02
+
+
+def test_thread_count_does_not_change_the_step():
+    """The oracle's per-cell and per-face loops may run on several host
+    threads; every output (state, time step, counters) is bit-identical to
+    the single-thread run."""
+    P = ics.turbulent_3d(12, seed=2)
+    M = O.Mesh(P.tess)
+    Q = P.conserved()
+    O.set_threads(1)
+    ref = O.step(M, Q, P.gamma, "lagrangian", cfl=0.3)
+    try:
+        for t in (3, 8):
+            O.set_threads(t)
+            out = O.step(M, Q, P.gamma, "lagrangian", cfl=0.3)
+            assert np.array_equal(out[0], ref[0]) and out[1] == ref[1]
+            assert np.array_equal(np.asarray(out[2]), np.asarray(ref[2])) and out[3] == ref[3]
+    finally:
+        O.set_threads(1)
