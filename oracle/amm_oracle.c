@@ -23,7 +23,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NV_MAX 5 /* D + 2 primitives for D <= 3 */
+#define NV_MAX 6 /* D + 2 primitives for D <= 3, and the entropic function */
 
 /* ------------------------------------------------------------ host threads
  * The per-cell and per-face loops have independent iterations.  They may run
@@ -248,6 +248,7 @@ typedef struct {
   int limit;
   double* grad;
   const incidence* I;
+  int nv;  /* variables per cell in W and grad */
 } grad_args;
 
 static void grad_cell(const void* a, long i, int64_t* counters) {
@@ -261,7 +262,7 @@ static void grad_cell(const void* a, long i, int64_t* counters) {
   const int limit = A->limit;
   double* grad = A->grad;
   const incidence I = *A->I;
-  const int nv = dim + 2;
+  const int nv = A->nv;
   {
     double g[NV_MAX][3];
     for (int v = 0; v < nv; v++)
@@ -327,7 +328,17 @@ void ora_gradients(int dim, long n, const double* W, const double* gen, const do
                    const int32_t* cells, const int8_t* shift, const double* area, const double* cen,
                    const double* box, int limit, double* grad) {
   incidence I = build_incidence(n, nf, cells);
-  const grad_args A = {dim, W, gen, V, s, cells, shift, area, cen, box, limit, grad, &I};
+  const grad_args A = {dim, W, gen, V, s, cells, shift, area, cen, box, limit, grad, &I, dim + 2};
+  par_for(n, grad_cell, &A, NULL);
+  free_incidence(&I);
+}
+
+/* the same for nvar variables per cell (W [n][nvar], grad [n][nvar][dim]) */
+static void gradients_nvar(int dim, long n, int nvar, const double* W, const double* gen, const double* V,
+                           const double* s, long nf, const int32_t* cells, const int8_t* shift, const double* area,
+                           const double* cen, const double* box, int limit, double* grad) {
+  incidence I = build_incidence(n, nf, cells);
+  const grad_args A = {dim, W, gen, V, s, cells, shift, area, cen, box, limit, grad, &I, nvar};
   par_for(n, grad_cell, &A, NULL);
   free_incidence(&I);
 }
@@ -679,6 +690,10 @@ typedef struct {
   double gamma, dt, tol;
   int maxit;
   double* F;
+  double* FS;  /* entropy flux per unit area (Sec. 3.5), or NULL */
+  double* MF;  /* largest shock Mach number of the face's Riemann problem, or NULL */
+  const double* Acell;  /* entropic function A = S/M per cell (with FS) */
+  const double* gA;     /* its limited gradient [n][dim] (with FS) */
 } flux_args;
 
 static void flux_face(const void* a, long k, int64_t* counters);
@@ -691,7 +706,7 @@ int ora_fluxes(int dim, long n, const double* W, const double* grad, const doubl
   (void)area;
   double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
   ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
-  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F};
+  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F, NULL, NULL, NULL, NULL};
   const int64_t fails_before = counters[3];
   par_for(nf, flux_face, &A, counters);
   free(wface);
@@ -720,6 +735,7 @@ static void flux_face(const void* a, long k, int64_t* counters) {
     const double* w = wface + k * dim;
 
     double Wp[2][NV_MAX], Wpp[2][NV_MAX];
+    double App[2] = {0.0, 0.0}; /* entropic function at the face (Sec. 3.5) */
     for (int side = 0; side < 2; side++) {
       const long i = cellK[side];
       const double* Wi = W + i * nv;
@@ -759,10 +775,26 @@ static void flux_face(const void* a, long k, int64_t* counters) {
         const double dva_dt = -adv - gi[(dim + 1) * dim + a] / rho;
         Wpp[side][1 + a] += 0.5 * dt * dva_dt;
       }
+      if (A->FS) {
+        /* A reconstructed like the other primitives; it is advected,
+         * dA/dt = -v'.grad A */
+        const double* ga = A->gA + i * dim;
+        double dA = 0.0, vgrad_A = 0.0;
+        for (int d = 0; d < dim; d++) {
+          dA += ga[d] * fs[d];
+          vgrad_A += vp[d] * ga[d];
+        }
+        App[side] = A->Acell[i] + dA + 0.5 * dt * (-vgrad_A);
+        if (!(App[side] > 0.0)) App[side] = A->Acell[i];
+      }
     }
     if (!(Wpp[0][0] > 0.0) || !(Wpp[0][dim + 1] > 0.0) || !(Wpp[1][0] > 0.0) || !(Wpp[1][dim + 1] > 0.0)) {
       for (int side = 0; side < 2; side++)
         for (int v = 0; v < nv; v++) Wpp[side][v] = Wp[side][v];
+      if (A->FS) {
+        App[0] = A->Acell[cellK[0]];
+        App[1] = A->Acell[cellK[1]];
+      }
       counters[0]++;
     }
     /* 3. rotate: normal component and transverse vector */
@@ -795,7 +827,44 @@ static void flux_face(const void* a, long k, int64_t* counters) {
     Fk[0] = rhoF * uF;
     for (int d = 0; d < dim; d++) Fk[1 + d] = rhoF * vlab[d] * uF + PF * nrm[d];
     Fk[dim + 1] = (0.5 * rhoF * v2 + PF / (gamma - 1.0)) * uF + PF * vn;
+    if (A->FS) {
+      /* Sec. 3.5: entropy flux rho_F u_F A_U with A_U the reconstructed
+       * entropic function of the upwind side; shock Mach numbers of the
+       * waves with p* above the pressure ahead of them */
+      A->FS[k] = rhoF * uF * ((uF > 0.0) ? App[0] : App[1]);
+      double mach = 1.0;
+      if (st == 0) {
+        const double ps = out[3];
+        for (int side = 0; side < 2; side++) {
+          const double pK = Wpp[side][dim + 1];
+          if (ps > pK) {
+            const double m = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (ps / pK - 1.0));
+            if (m > mach) mach = m;
+          }
+        }
+      }
+      A->MF[k] = mach;
+    }
   }
+}
+
+/* the same fluxes, plus the entropy flux and the face's shock Mach number;
+ * Acell: A = S/M per cell, gA: its limited gradient [n][dim] */
+int ora_fluxes_entropy(int dim, long n, const double* W, const double* grad, const double* gen, const double* s,
+                       const double* wmesh, long nf, const int32_t* cells, const int8_t* shift, const double* area,
+                       const double* cen, const double* box, double gamma, double dt, double tol, int maxit,
+                       const double* Acell, const double* gA, double* F, double* FS, double* MF,
+                       int64_t* counters) {
+  (void)n;
+  (void)area;
+  double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
+  ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
+  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F, FS, MF,
+                       Acell, gA};
+  const int64_t fails_before = counters[3];
+  par_for(nf, flux_face, &A, counters);
+  free(wface);
+  return counters[3] > fails_before ? -1 : 0;
 }
 
 /* ------------------------------------------------- A8: conservative update
@@ -838,6 +907,157 @@ static void upd_cell(const void* a, long i, int64_t* counters) {
     }
     for (int v = 0; v < nv; v++) Qnew[i * nv + v] = Q[i * nv + v] - dt * sum[v];
   }
+}
+
+/* ------------------------------- Sec. 3.5: entropy and the shock switch
+ * S_i = M_i A_i with the entropic function A = P / rho^gamma is advected as
+ * a further conserved quantity with the face fluxes rho_F u_F A_U.  At the
+ * end of the step each cell either keeps the advected entropy (when the
+ * largest shock Mach number among the Riemann problems of its faces is below
+ * mach_thresh: the flow around it is smooth; or, with alpha_s > 0, when the
+ * new thermal energy is below alpha_s times the largest kinetic energy around
+ * it: the flow is cold) and sets its thermal energy from it,
+ * P = (S/M) rho^gamma, E = M |v|^2/2 + P V/(gamma-1); or it keeps
+ * the conservative energy update and re-initialises S = M P / rho^gamma.
+ * Q, Qnew: [n][dim+2]; S, Snew: [n]; kept[i] = 1 where the entropy was kept. */
+void ora_entropy_init(int dim, long n, const double* Q, const double* V, double gamma, double* S) {
+  const int nv = dim + 2;
+  for (long i = 0; i < n; i++) {
+    const double m = Q[i * nv];
+    const double rho = m / V[i];
+    double v2 = 0.0;
+    for (int d = 0; d < dim; d++) {
+      const double v = Q[i * nv + 1 + d] / m;
+      v2 += v * v;
+    }
+    const double P = (gamma - 1.0) * (Q[i * nv + dim + 1] / V[i] - 0.5 * rho * v2);
+    S[i] = m * P / pow(rho, gamma);
+  }
+}
+
+typedef struct {
+  int dim;
+  const double *Q, *S, *V, *area, *F, *FS, *MF, *wmesh;
+  const int32_t* cells;
+  double dt, gamma, mach_thresh, alpha_s;
+  double *Qnew, *Snew;
+  int32_t* kept;
+  const incidence* I;
+} ent_args;
+
+static void ent_cell(const void* a, long i, int64_t* counters) {
+  const ent_args* A = (const ent_args*)a;
+  const int dim = A->dim;
+  const int nv = dim + 2;
+  const incidence I = *A->I;
+  double sum[NV_MAX] = {0, 0, 0, 0, 0}, sumS = 0.0, mach = 1.0;
+  for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+    const long k = I.face[q];
+    const double sgn = (I.side[q] == 0) ? 1.0 : -1.0;
+    for (int v = 0; v < nv; v++) sum[v] += sgn * A->area[k] * A->F[k * nv + v];
+    sumS += sgn * A->area[k] * A->FS[k];
+    if (A->MF[k] > mach) mach = A->MF[k];
+  }
+  double* Qn = A->Qnew + i * nv;
+  for (int v = 0; v < nv; v++) Qn[v] = A->Q[i * nv + v] - A->dt * sum[v];
+  const double Sadv = A->S[i] - A->dt * sumS;
+  const double m = Qn[0];
+  const double V = A->V[i];
+  const double rho = m / V;
+  double p2 = 0.0;
+  for (int d = 0; d < dim; d++) p2 += Qn[1 + d] * Qn[1 + d];
+  /* cold-flow criterion, eq. (eqnScrit1): the new thermal energy against the
+   * largest kinetic energy of the cell and its neighbours (start-of-step
+   * states), measured relative to the cell's own mesh velocity */
+  int cold = 0;
+  if (A->alpha_s > 0.0) {
+    double ekmax = 0.0;
+    for (long q = I.off[i] - 1; q < I.off[i + 1]; q++) {
+      const long j = (q < I.off[i]) ? i : (long)A->cells[2 * I.face[q] + (1 - I.side[q])];
+      const double mj = A->Q[j * nv];
+      double dv2 = 0.0;
+      for (int d = 0; d < dim; d++) {
+        const double dv = A->Q[j * nv + 1 + d] / mj - (A->wmesh ? A->wmesh[i * dim + d] : 0.0);
+        dv2 += dv * dv;
+      }
+      const double ek = 0.5 * mj * dv2;
+      if (ek > ekmax) ekmax = ek;
+    }
+    const double eth = Qn[dim + 1] - 0.5 * p2 / m;
+    cold = eth < A->alpha_s * ekmax;
+  }
+  if (mach < A->mach_thresh || cold) {
+    const double P = (Sadv / m) * pow(rho, A->gamma);
+    Qn[dim + 1] = 0.5 * p2 / m + P * V / (A->gamma - 1.0);
+    A->Snew[i] = Sadv;
+    A->kept[i] = 1;
+    counters[0]++;
+  } else {
+    const double P = (A->gamma - 1.0) * (Qn[dim + 1] / V - 0.5 * p2 / (m * V));
+    A->Snew[i] = m * P / pow(rho, A->gamma);
+    A->kept[i] = 0;
+  }
+}
+
+/* one whole step with the entropy switch; as ora_step, plus S in/out, the
+ * shock-Mach threshold, the cold-flow parameter alpha_s (0: off), and
+ * counters[4] = cells that kept their entropy */
+int ora_step_entropy(int dim, long n, const double* gen, long nf, const int32_t* cells, const int8_t* shift,
+                     const double* area, const double* cen, const double* box, const double* V, const double* s,
+                     const double* Q, const double* S, double gamma, int mode, const double* wmesh_in, double dt,
+                     double cfl, int limit, double tol, int maxit, double mach_thresh, double alpha_s, double* Qnew,
+                     double* Snew, int32_t* kept, double* dt_used, int64_t* counters) {
+  const int nv = dim + 2;
+  double* W = (double*)malloc(sizeof(double) * (size_t)(n * nv));
+  double* grad = (double*)malloc(sizeof(double) * (size_t)(n * nv * dim));
+  double* wm = (double*)malloc(sizeof(double) * (size_t)(n * dim));
+  double* F = (double*)malloc(sizeof(double) * (size_t)(nf * nv + 1));
+  double* FS = (double*)malloc(sizeof(double) * (size_t)(nf + 1));
+  double* MF = (double*)malloc(sizeof(double) * (size_t)(nf + 1));
+  double* Wx = (double*)malloc(sizeof(double) * (size_t)(n * (nv + 1)));
+  double* gx = (double*)malloc(sizeof(double) * (size_t)(n * (nv + 1) * dim));
+  double* Ac = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* gA = (double*)malloc(sizeof(double) * (size_t)(n * dim + 1));
+  ora_primitives(dim, n, Q, V, gamma, W);
+  /* the primitives and the entropic function A = S/M, gradients and limiter
+   * per variable (the first nv exactly as in ora_gradients) */
+  for (long i = 0; i < n; i++) {
+    for (int v = 0; v < nv; v++) Wx[i * (nv + 1) + v] = W[i * nv + v];
+    Ac[i] = S[i] / Q[i * nv];
+    Wx[i * (nv + 1) + nv] = Ac[i];
+  }
+  gradients_nvar(dim, n, nv + 1, Wx, gen, V, s, nf, cells, shift, area, cen, box, limit, gx);
+  for (long i = 0; i < n; i++) {
+    for (int v = 0; v < nv; v++)
+      for (int d = 0; d < dim; d++) grad[(i * nv + v) * dim + d] = gx[(i * (nv + 1) + v) * dim + d];
+    for (int d = 0; d < dim; d++) gA[i * dim + d] = gx[(i * (nv + 1) + nv) * dim + d];
+  }
+  for (long i = 0; i < n; i++)
+    for (int d = 0; d < dim; d++)
+      wm[i * dim + d] = (mode == 0) ? 0.0 : (mode == 1) ? W[i * nv + 1 + d] : wmesh_in[i * dim + d];
+  if (!(dt > 0.0)) dt = ora_timestep(dim, n, W, V, wm, gamma, cfl, NULL);
+  *dt_used = dt;
+  for (int c = 0; c < 5; c++) counters[c] = 0;
+  const int rc = ora_fluxes_entropy(dim, n, W, grad, gen, s, wm, nf, cells, shift, area, cen, box, gamma, dt, tol,
+                                    maxit, Ac, gA, F, FS, MF, counters);
+  free(Wx);
+  free(gx);
+  free(Ac);
+  free(gA);
+  incidence I = build_incidence(n, nf, cells);
+  const ent_args A = {dim, Q, S, V, area, F, FS, MF, wm, cells, dt, gamma, mach_thresh, alpha_s, Qnew, Snew, kept,
+                      &I};
+  int64_t c5[4] = {0, 0, 0, 0};
+  par_for(n, ent_cell, &A, c5);
+  counters[4] = c5[0];
+  free_incidence(&I);
+  free(W);
+  free(grad);
+  free(wm);
+  free(F);
+  free(FS);
+  free(MF);
+  return rc;
 }
 
 /* ------------------------------------------------ A9: conservation sums */

@@ -46,6 +46,14 @@ def lib():
         L.ora_step.restype = _I
         L.ora_step.argtypes = [_I, _L, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _P, _D, _D, _I, _D, _I,
                                _P, _P, _P]
+        L.ora_fluxes_entropy.restype = _I
+        L.ora_fluxes_entropy.argtypes = [_I, _L, _P, _P, _P, _P, _P, _L, _P, _P, _P, _P, _P, _D, _D, _D, _I, _P,
+                                         _P, _P, _P, _P, _P]
+        L.ora_entropy_init.restype = None
+        L.ora_entropy_init.argtypes = [_I, _L, _P, _P, _D, _P]
+        L.ora_step_entropy.restype = _I
+        L.ora_step_entropy.argtypes = [_I, _L, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _P, _D, _D,
+                                       _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]
         L.ora_set_threads.restype = None
         L.ora_set_threads.argtypes = [_I]
         L.ora_get_threads.restype = _I
@@ -163,6 +171,27 @@ def fluxes(mesh, W, grad, s, wmesh, gamma, dt, tol=1e-12, maxit=64):
     return F, cnt, rc
 
 
+def fluxes_entropy(mesh, W, grad, s, wmesh, gamma, dt, A, gA, tol=1e-12, maxit=64):
+    """fluxes() plus, per face, the entropy flux per unit area and the largest
+    shock Mach number of its Riemann problem (Sec. 3.5); A is the entropic
+    function per cell and gA its limited gradient [n, dim]."""
+    A = _c(A, np.float64)
+    gA = _c(gA, np.float64)
+    W = _c(W, np.float64)
+    grad = _c(grad, np.float64)
+    s = _c(s, np.float64)
+    wm = None if wmesh is None else _c(wmesh, np.float64)
+    F = np.empty((mesh.nf, mesh.dim + 2))
+    FS = np.empty(mesh.nf)
+    MF = np.empty(mesh.nf)
+    cnt = np.zeros(4, np.int64)
+    rc = lib().ora_fluxes_entropy(mesh.dim, mesh.n, W.ctypes.data, grad.ctypes.data, mesh.gen.ctypes.data,
+                                  s.ctypes.data, None if wm is None else wm.ctypes.data, mesh.nf, *mesh.args(), gamma,
+                                  dt, tol, maxit, A.ctypes.data, gA.ctypes.data, F.ctypes.data, FS.ctypes.data,
+                                  MF.ctypes.data, cnt.ctypes.data)
+    return F, FS, MF, cnt, rc
+
+
 def update(mesh, Q, F, dt):
     Q = _c(Q, np.float64)
     F = _c(F, np.float64)
@@ -198,3 +227,33 @@ def step(mesh, Q, gamma, mode="lagrangian", wmesh=None, dt=0.0, cfl=0.3, limit=T
                         s.ctypes.data, Q.ctypes.data, gamma, MODES[mode], None if wm is None else wm.ctypes.data,
                         dt, cfl, int(bool(limit)), tol, maxit, Qn.ctypes.data, ctypes.byref(dtu), cnt.ctypes.data)
     return Qn, dtu.value, cnt, rc
+
+
+def entropy_init(mesh, Q, V, gamma):
+    """S = M P / rho^gamma per cell (Sec. 3.5)."""
+    Q = _c(Q, np.float64)
+    S = np.empty(mesh.n)
+    lib().ora_entropy_init(mesh.dim, mesh.n, Q.ctypes.data, _c(V, np.float64).ctypes.data, gamma, S.ctypes.data)
+    return S
+
+
+def step_entropy(mesh, Q, S, gamma, mode="lagrangian", wmesh=None, dt=0.0, cfl=0.3, limit=True, tol=1e-12,
+                 maxit=64, mach_thresh=1.1, alpha_s=0.0, geom=None):
+    """One update with the entropy switch of Sec. 3.5.  Returns (Qnew, Snew,
+    kept [n] 0/1, dt_used, counters[5], rc); counters[4] = cells that kept
+    their advected entropy."""
+    V, s = geometry(mesh) if geom is None else geom
+    Q = _c(Q, np.float64)
+    S = _c(S, np.float64)
+    Qn = np.empty_like(Q)
+    Sn = np.empty_like(S)
+    kept = np.empty(mesh.n, np.int32)
+    dtu = ctypes.c_double(0.0)
+    cnt = np.zeros(5, np.int64)
+    wm = None if wmesh is None else _c(wmesh, np.float64)
+    rc = lib().ora_step_entropy(mesh.dim, mesh.n, mesh.gen.ctypes.data, mesh.nf, *mesh.args(), V.ctypes.data,
+                                s.ctypes.data, Q.ctypes.data, S.ctypes.data, gamma, MODES[mode],
+                                None if wm is None else wm.ctypes.data, dt, cfl, int(bool(limit)), tol, maxit,
+                                mach_thresh, alpha_s, Qn.ctypes.data, Sn.ctypes.data, kept.ctypes.data, ctypes.byref(dtu),
+                                cnt.ctypes.data)
+    return Qn, Sn, kept, dtu.value, cnt, rc
