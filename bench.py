@@ -1,23 +1,34 @@
 #!/usr/bin/env python
-"""Benchmark of one moving-mesh MUSCL-Hancock update on GB300.
+"""Benchmark of the moving-mesh MUSCL-Hancock update on GB300.
 
-Workload: a 64^3 jittered lattice (+-0.2 spacing, seed 2) in a periodic unit
-box, gamma = 5/3, rho = P = 1, a random-phase Gaussian velocity field with
-P(k) ~ k^-4 on 2 <= k <= 8 at rms Mach 2, mesh generators moving with the
-cells (Lagrangian); the Voronoi tessellation is built on the host before
-timing.  One "step" is one pass of the whole hot path on the device:
-gradients + limiter + Courant minimum, face velocities + fluxes (exact
-Riemann), signed FP64 cell update + primitives + conservation sums, replayed
-from a captured CUDA graph, with the time step kept on the device.
+Default workload (turbulent64): a 64^3 jittered lattice (+-0.2 spacing,
+seed 2) in a periodic unit box, gamma = 5/3, rho = P = 1, a random-phase
+Gaussian velocity field with P(k) ~ k^-4 on 2 <= k <= 8 at rms Mach 2, mesh
+generators moving with the cells (Lagrangian); the Voronoi tessellation is
+built on the host before timing.  One "step" is one pass of the whole hot
+path on the device: gradients + limiter + Courant minimum, face velocities +
+fluxes (exact Riemann), signed cell update + primitives + conservation sums,
+replayed from a captured CUDA graph, with the time step kept on the device.
 
 Metric: face-flux updates per second = faces x steps / device time.  The
-headline value is the FP32 form (FP32 bulk, FP64 accumulation and sums);
-the FP64 form is measured on the same workload and both are reported with
-their error against the FP64 CPU oracle.  Between timed steps the state is
-reset to the same input and the L2 is flushed (256 MiB write).
+headline value is the FP32 form (FP32 bulk, exact fixed-point flux sums,
+FP64 state and sums); the FP64 form and the FP32 form with the learned
+Riemann-pressure proposal are measured on the same workload, each with its
+error against the FP64 CPU oracle.  Between timed steps the state is reset
+to the same input and the L2 is flushed (256 MiB write).
 
-`--impl reference` times the FP64 CPU oracle instead (host cores, one
-thread) on a sample of the same workload.
+Other workloads (--workload), each printed as one line of the same shape:
+  lognormal192  192^3 log-normal density (sigma 1), P = rho^5/3, Mach-3
+                velocities, Eulerian; FP32 vs FP64 GPU forms, one step and
+                20 steps on the fixed tessellation, oracle on one step
+  learned192    the turbulent field at 192^3 (Lagrangian): FP32 learned
+                proposal vs the standard starting value, Newton iterations
+  ensemble      64 independent periodic boxes of 16^3..96^3 cells (log-
+                uniform), Mach 0.5..4, Eulerian, per-box Courant step, 50
+                steps, one persistent launch per step inside a CUDA graph
+
+`--impl reference` times the FP64 CPU oracle instead (all host cores) on a
+sample of the same workload.
 """
 import argparse
 import hashlib
@@ -27,7 +38,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -36,21 +46,46 @@ sys.path.insert(0, ROOT)
 METRIC = "Voronoi face-flux updates/s on 1 GB300 (FP32/learned vs plain FP64, same error)"
 UNIT = "face-flux updates/s"
 CFL = 0.3
-WORKLOAD = ("config-2 workload: 64^3 jittered lattice (+-0.2h, seed 2) in a periodic unit box, gamma=5/3, "
-            "rho=P=1, Gaussian velocity field P(k)~k^-4 (2<=k<=8) at rms Mach 2, Lagrangian mesh motion, "
-            "one MUSCL-Hancock step on the given tessellation")
+FIELD = "Gaussian velocity field P(k)~k^-4 (2<=k<=8)"
+WORKLOADS = {
+    "turbulent64": ("config-2 workload: 64^3 jittered lattice (+-0.2h, seed 2) in a periodic unit box, gamma=5/3, "
+                    "rho=P=1, " + FIELD + " at rms Mach 2, Lagrangian mesh motion, one MUSCL-Hancock step on the "
+                    "given tessellation"),
+    "lognormal192": ("config-3 workload: 192^3 jittered lattice (+-0.2h, seed 3), log-normal density sigma_lnrho=1 "
+                     "(same spectrum), P=rho^(5/3), " + FIELD + " at rms Mach 3, gamma=5/3, stationary mesh; one "
+                     "step and 20 steps on the fixed tessellation"),
+    "learned192": ("config-4 workload: the config-2 field at 192^3 (jittered lattice +-0.2h, seed 2, rms Mach 2, "
+                   "Lagrangian); FP32 flux with the learned p* proposal vs the standard starting value, Newton to "
+                   "1e-6 relative in both"),
+    "ensemble": ("config-5 workload: 64 independent periodic unit boxes, n^3 cells with n=round(exp(U(ln16,ln96))) "
+                 "(seed 5), each the config-2 field at rms Mach U[0.5,4], gamma=5/3, stationary mesh, per-box "
+                 "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, one persistent "
+                 "cooperative launch per step replayed from a CUDA graph"),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000; ensemble 50)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default 20; ensemble 5)")
     ap.add_argument("--impl", default="amm", choices=["amm", "reference"])
-    ap.add_argument("--n", type=int, default=64, help="lattice size per dimension")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
+    ap.add_argument("--workload", default="turbulent64", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="lattice size per dimension (single-box workloads)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle legs")
     ap.add_argument("--no-extras", action="store_true", help="headline form only (profiling runs)")
-    return ap.parse_args()
+    ap.add_argument("--proposal-epochs", type=int, default=4, help="training epochs of the learned p* proposal")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch shapes grad_lanes,update_lanes,flux_block,persistent instead of autotuning")
+    a = ap.parse_args()
+    ens = a.workload == "ensemble"
+    if a.steps is None:
+        a.steps = 50 if ens else 2000
+    if a.warmup is None:
+        a.warmup = 5 if ens else 20
+    if a.n is None:
+        a.n = {"turbulent64": 64, "lognormal192": 192, "learned192": 192}.get(a.workload, 0)
+    return a
 
 
 # ------------------------------------------------------------------ helpers
@@ -80,9 +115,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, n, nf):
+def ncu_traffic(kernel, nf):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources (else None), scaled to this launch's faces."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
@@ -94,7 +129,6 @@ def ncu_traffic(kernel, n, nf):
     k = t.get("kernels", {}).get(kernel)
     if not k:
         return None
-    # scale by the units one launch processes if the capture was on another size
     return k["dram_bytes"] * (nf / k["faces"])
 
 
@@ -117,6 +151,8 @@ def algorithmic_bytes(kernel, n, nf, rb):
         return inc * 8 + nf * 5 * rb + n * (4 + 80 + 8 + 5 * rb)
     if kernel == "finish":
         return 0
+    if kernel == "step":
+        return sum(algorithmic_bytes(k, n, nf, rb) for k in ("gradients", "flux", "update"))
     raise KeyError(kernel)
 
 
@@ -140,6 +176,7 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -175,20 +212,47 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0) for r in rows)}
 
 
-def parity_errors(out, ref, Q0, W0, dim, gamma):
+def floors(Q0, W0, dim, gamma):
+    """Per-component error floor: RMS |Q| for mass and energy, RMS(m c) for
+    the momentum components."""
     import numpy as np
     fl = np.sqrt(np.mean(Q0 * Q0, axis=0))
     c = np.sqrt(gamma * W0[:, dim + 1] / W0[:, 0])
     fl[1:1 + dim] = np.sqrt(np.mean((Q0[:, 0] * c) ** 2))
+    return fl
+
+
+def parity_errors(out, ref, fl):
+    import numpy as np
     e = np.abs(out - ref) / np.maximum(np.abs(ref), fl)
     return float(e.max()), float(np.quantile(e, 0.999))
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 # ------------------------------------------------------------------ oracle arm
-def oracle_rate(P, steps, budget_s=None):
-    """Times full oracle steps (one host thread) of problem P; returns
-    (faces/s, steps run, seconds, first-step output, its dt)."""
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(P, motion, steps, budget_s=None, threads=1):
+    """Times full oracle steps of problem P on `threads` host threads; returns
+    (faces/s, steps run, seconds, (first-step output, its dt, geometry))."""
     from oracle import oracle as O
+    O.set_threads(threads)
     M = O.Mesh(P.tess)
     geom = O.geometry(M)
     Q0 = P.conserved()
@@ -197,7 +261,7 @@ def oracle_rate(P, steps, budget_s=None):
     k = 0
     while k < steps:
         t0 = time.perf_counter()
-        Qn, dt, cnt, rc = O.step(M, Q0, P.gamma, "lagrangian", cfl=CFL, geom=geom)
+        Qn, dt, cnt, rc = O.step(M, Q0, P.gamma, motion, cfl=CFL, geom=geom)
         t_all += time.perf_counter() - t0
         if first is None:
             first = (Qn, dt, geom)
@@ -212,23 +276,33 @@ def run_reference(args):
     if rank != 0:
         return 0
     from harness import ics
-    # size the sample so warmup + steps stay within ~2 minutes of one core
-    calib = ics.turbulent_3d(16, seed=2)
-    r_cal, _, _, _ = oracle_rate(calib, 1)
+    # the oracle on all host cores; size the sample so warmup + steps stay
+    # within ~2 minutes
+    cores = host_threads()
+    calib = ics.turbulent_3d(24, seed=2)
+    r_cal, _, _, _ = oracle_rate(calib, "lagrangian", 2, threads=cores)
     total = max(1, args.steps + args.warmup)
     faces_budget = 120.0 * r_cal / total
-    n = int(max(8, min(args.n, round((faces_budget / 7.84) ** (1.0 / 3.0)))))
-    P = ics.turbulent_3d(n, seed=2)
+    n_max = args.n if args.n else 64
+    n = int(max(8, min(n_max, round((faces_budget / 7.84) ** (1.0 / 3.0)))))
+    if args.workload == "lognormal192":
+        P, motion = ics.lognormal_3d(n, seed=3), "eulerian"
+    elif args.workload == "ensemble":
+        P, motion = ics.turbulent_3d(n, seed=5, mach=2.25), "eulerian"
+    else:
+        P, motion = ics.turbulent_3d(n, seed=2), "lagrangian"
     if args.warmup:
-        oracle_rate(P, args.warmup)
-    rate, k, secs, _ = oracle_rate(P, args.steps)
+        oracle_rate(P, motion, args.warmup, threads=cores)
+    rate, k, secs, _ = oracle_rate(P, motion, args.steps, threads=cores)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": k,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / k, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_lattice": n, "cells": P.n_cells, "faces": P.n_faces},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d full oracle steps of the same recipe at %d^3 (%d faces)" % (k, n, P.n_faces)},
+        "config": {"workload": WORKLOADS[args.workload], "sample_lattice": n, "cells": P.n_cells,
+                   "faces": P.n_faces},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": "%d full oracle steps of the same recipe at %d^3 (%d faces), %d host threads"
+                                   % (k, n, P.n_faces, cores)},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -236,77 +310,178 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def timed_form(amm, torch, ctx, Q0d, steps, warmup, stream, flush):
-    """Event-timed steps of one context; state reset and L2 flushed between."""
-    amm.amm_profile(ctx, True)
-    for _ in range(warmup):
+class Gpu:
+    """Device, stream, L2-flush buffer and the library, shared by the forms."""
+
+    def __init__(self, local, epochs=4):
+        import torch
+        self.epochs = epochs
+        self.torch = torch
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_0901_4107_gb300 import amm
+        self.amm = amm
+        self.stream = torch.cuda.Stream()
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")   # 256 MiB > L2
+        self.net = None
+        self.train_stats = None
+
+    def proposal(self):
+        if self.net is None:
+            from harness import ics
+            from paper_0901_4107_gb300 import learned
+            t0 = time.perf_counter()
+            self.net, self.train_stats = learned.train_proposal(ics, self.torch, small=False, epochs=self.epochs)
+            self.train_stats["train_seconds"] = time.perf_counter() - t0
+        return self.net
+
+    def tune(self, ctx, fixed, reps):
+        if fixed:
+            g, u, fb, p = (int(x) for x in fixed.split(","))
+            self.amm.amm_set_tuning(ctx, g, u, fb, p)
+            return self.amm.amm_get_tuning(ctx)
+        return self.amm.amm_autotune(ctx, CFL, reps=reps)
+
+
+def timed_form(g, ctx, Q0d, steps, warmup, kernel_steps=200):
+    """Event-timed steps of one context; state reset and L2 flushed between.
+    The timed steps replay the plain step graph; the per-kernel times come
+    from a second pass whose graph also records events between the kernels.
+    Returns per-step ms, per-kernel median ms and wall seconds."""
+    amm, torch, stream = g.amm, g.torch, g.stream
+
+    def one(i, before=None, after=None):
         amm.amm_set_state_device(ctx, Q0d.data_ptr())
         with torch.cuda.stream(stream):
-            flush.fill_(1)
+            g.flush.fill_(i)
+            if before is not None:
+                before.record(stream)
         amm.amm_advance(ctx, CFL, 1, True)
+        if after is not None:
+            with torch.cuda.stream(stream):
+                after.record(stream)
+
+    amm.amm_profile(ctx, False)
+    for i in range(warmup):
+        one(i)
     torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    kt = []
     t0 = time.perf_counter()
     for i in range(steps):
-        amm.amm_set_state_device(ctx, Q0d.data_ptr())
-        with torch.cuda.stream(stream):
-            flush.fill_(i)
-            ev0[i].record(stream)
-        amm.amm_advance(ctx, CFL, 1, True)
-        with torch.cuda.stream(stream):
-            ev1[i].record(stream)
-        kt.append(amm.amm_get_kernel_times(ctx))
+        one(i, ev0[i], ev1[i])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    amm.amm_profile(ctx, True)
+    kt = []
+    for i in range(min(steps, kernel_steps) + 2):
+        one(i)
+        if i >= 2:
+            kt.append(amm.amm_get_kernel_times(ctx))
+    amm.amm_profile(ctx, False)
     ker = {k: statistics.median([d[k] for d in kt]) for k in kt[0]}
     return ms, ker, wall
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    world, rank, local = dist_env()
-    import numpy as np
-    import torch
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device")
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    import __graft_entry__
-    __graft_entry__.build()
-    from harness import ics
-    from paper_0901_4107_gb300 import amm
+def kernel_split(g, ctx, Q0d, tuning, steps=50):
+    """Per-kernel device times of the chosen shapes.  A persistent step is one
+    launch, so its phases are timed from the kernel sequence of the same
+    shapes (same per-item code)."""
+    amm = g.amm
+    if not tuning["persistent"]:
+        return None
+    amm.amm_set_tuning(ctx, tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 0)
+    _, ker, _ = timed_form(g, ctx, Q0d, steps, 3)
+    amm.amm_set_tuning(ctx, tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 1)
+    return ker
 
-    P = ics.turbulent_3d(args.n, seed=2 + rank)
+
+def kernel_table(ker, n, nf, rb):
+    tot = sum(ker.values())
+    out = {}
+    for k, t in ker.items():
+        b = algorithmic_bytes(k, n, nf, rb)
+        out[k] = {"ms": t, "share": t / tot if tot else None, "algorithmic_bytes": b,
+                  "gbs": (b / (t * 1e-3) / 1e9) if t > 0 else None}
+    return out
+
+
+def roofline(kern, nf, kernel_name_prefix=""):
+    hbm, src = peaks()
+    dom = max((k for k in kern if k != "finish"), key=lambda k: kern[k]["ms"])
+    achieved = kern[dom]["gbs"]
+    return {"kernel": kernel_name_prefix + dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": ncu_traffic(kernel_name_prefix + dom, nf),
+            "peak_source": src + " hbm_gbs (copy bandwidth)", "algorithmic_bytes": kern[dom]["algorithmic_bytes"]}
+
+
+def newton_stats(amm, ctx, Q0, steps=1):
+    amm.amm_set_state(ctx, Q0)
+    amm.amm_reset_stats(ctx)
+    amm.amm_advance(ctx, CFL, steps, False)
+    s = amm.amm_get_stats(ctx)
+    return {"newton_iters_per_face": s["newton_iters"] / max(1, s["faces"]), "newton_hist": s["newton_hist"][:8],
+            "fallback_faces": s["fallback_faces"] if "fallback_faces" in s else s.get("fallback"),
+            "vacuum_faces": s.get("vacuum"), "guard_faces": s.get("guard")}
+
+
+def e2e_rate(g, ctx, Q0, steps):
+    """Whole-step rate through the C ABI with pinned host buffers: host->device
+    state copy, one step, device->host state copy, every step."""
+    amm, torch = g.amm, g.torch
+    Qh = torch.from_numpy(Q0.copy()).pin_memory()
+    Qo = torch.empty_like(Qh).pin_memory()
+    amm.amm_profile(ctx, False)
+    for _ in range(3):
+        amm.amm_set_state(ctx, Qh.numpy())
+        amm.amm_advance(ctx, CFL, 1, True)
+        amm.amm_get_state(ctx, Qo.numpy())
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        amm.amm_set_state(ctx, Qh.numpy())
+        amm.amm_advance(ctx, CFL, 1, True)
+        amm.amm_get_state(ctx, Qo.numpy())
+    return (time.perf_counter() - t0) / steps, Q0.nbytes
+
+
+def bench_box(args, g, world, rank, local):
+    """Single-box workloads: turbulent64, lognormal192, learned192."""
+    import numpy as np
+    from harness import ics
+    amm, torch = g.amm, g.torch
+    wl = args.workload
+    if wl == "lognormal192":
+        P, motion, head = ics.lognormal_3d(args.n, seed=3 + rank), "eulerian", "fp32"
+    elif wl == "learned192":
+        P, motion, head = ics.turbulent_3d(args.n, seed=2 + rank), "lagrangian", "fp32_learned"
+    else:
+        P, motion, head = ics.turbulent_3d(args.n, seed=2 + rank), "lagrangian", "fp32"
     n, nf = P.n_cells, P.n_faces
     Q0 = P.conserved()
-    stream = torch.cuda.Stream()
     Q0d = torch.from_numpy(Q0).to("cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")   # 256 MiB
     torch.cuda.synchronize()
 
     def make(prec):
-        return amm.create_from_mesh(P.tess, Q0, P.gamma, precision=prec, mesh_motion="lagrangian",
-                                    stream=stream.cuda_stream)
+        ctx = amm.create_from_mesh(P.tess, Q0, P.gamma, precision=prec, mesh_motion=motion,
+                                   stream=g.stream.cuda_stream)
+        if prec == "fp32_learned":
+            amm.amm_mlp_attach(ctx, g.proposal())
+        return ctx
 
-    ctx32 = make("fp32")
-    tuning = amm.amm_autotune(ctx32, CFL, reps=5)
+    ctxs = {head: make(head)}
+    tuning = g.tune(ctxs[head], args.tuning, 5)
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.05)
     if world > 1:
         torch.distributed.barrier()
-    ms32, ker32, wall32 = timed_form(amm, torch, ctx32, Q0d, args.steps, args.warmup, stream, flush)
+    ms, ker, wall = timed_form(g, ctxs[head], Q0d, args.steps, args.warmup)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    step_ms = statistics.mean(ms32)
+    step_ms = statistics.mean(ms)
+    faces_all = float(nf)
     if world > 1:
         t = torch.tensor([step_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -314,106 +489,300 @@ def main():
         tot = torch.tensor([float(nf)], device="cuda")
         torch.distributed.all_reduce(tot)
         faces_all = float(tot.item())
-    else:
-        faces_all = float(nf)
     value = faces_all / (step_ms * 1e-3)
-
-    hbm, peak_src = peaks()
-    kern = {}
-    for k, t in ker32.items():
-        b = algorithmic_bytes(k, n, nf, 4)
-        kern[k] = {"ms": t, "share": t / sum(ker32.values()), "algorithmic_bytes": b,
-                   "gbs": (b / (t * 1e-3) / 1e9) if t > 0 else None}
-    dom = max(ker32, key=lambda k: ker32[k])
-    achieved = kern[dom]["gbs"]
-    traffic = ncu_traffic(dom, n, nf)
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " hbm_gbs (copy bandwidth)",
-            "algorithmic_bytes": kern[dom]["algorithmic_bytes"]}
+    split = kernel_split(g, ctxs[head], Q0d, tuning)
+    kern = kernel_table(split or ker, n, nf, 4)
+    prefix = "learned_" if head == "fp32_learned" else ""
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n, "faces": nf, "form": "fp32 (FP64 accumulation and sums)",
+        "config": {"workload": WORKLOADS[wl], "cells": n, "faces": nf,
+                   "form": head + (" (learned p* proposal, " if head == "fp32_learned" else " (")
+                   + "FP32 bulk, exact fixed-point flux sums, FP64 state and sums)",
                    "l2": "flushed between timed steps (256 MiB write); state reset to the same input",
                    "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "tuning": tuning},
-        "cells_per_s": n * world / (step_ms * 1e-3),
-        "roofline": roof,
+        "cells_per_s": n * (faces_all / nf) / (step_ms * 1e-3),
+        "roofline": roofline(kern, nf, prefix),
         "kernels": kern,
-        "gpu_launches": 4 * args.steps,
+        "kernel_times_from": "per-phase launches of the same shapes" if split else "the timed steps",
+        "gpu_launches": (1 if tuning["persistent"] else 4) * args.steps,
         "clocks": clocks,
     }
-    if rank == 0 and not args.no_extras:
-        from oracle import oracle as O
-        forms = {"fp32": {"value": value, "ms_per_step": step_ms, "wall_s": wall32}}
-        # FP64 form on the same workload
-        ctx64 = make("fp64")
-        amm.amm_autotune(ctx64, CFL, reps=2)
-        k64 = max(3, min(args.steps, 200))
-        ms64, ker64, wall64 = timed_form(amm, torch, ctx64, Q0d, k64, min(args.warmup, 5), stream, flush)
-        forms["fp64"] = {"value": nf / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
-                         "steps": k64, "kernels_ms": ker64}
-        # error of each form against the oracle on one step (oracle dt)
-        if not args.no_cpu:
-            rate, kcpu, secs, first = oracle_rate(P, 8, budget_s=12.0)
-            ref, dt, geom = first
-            M = O.Mesh(P.tess)
-            W0 = O.primitives(M, Q0, geom[0], P.gamma)
-            for name, ctx in (("fp32", ctx32), ("fp64", ctx64)):
-                amm.amm_set_state(ctx, Q0)
-                amm.amm_step(ctx, dt)
-                emax, e999 = parity_errors(amm.amm_get_state(ctx), ref, Q0, W0, 3, P.gamma)
-                forms[name].update({"err_max": emax, "err_p999": e999})
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "%d full oracle steps of the workload (%d faces each), one host thread"
-                                              % (kcpu, nf)}
-        # FP32 learned form: proposal trained on the method's own face states
-        # (harvested from the 2D shock tube and 3D turbulent boxes), then the
-        # same timed loop
-        from paper_0901_4107_gb300 import learned
-        from harness import ics as _ics
-        t_tr = time.perf_counter()
-        net, tstats = learned.train_proposal(_ics, torch, small=False, epochs=4)
-        tstats["train_seconds"] = time.perf_counter() - t_tr
-        ctxl = make("fp32_learned")
-        amm.amm_mlp_attach(ctxl, net)
-        amm.amm_autotune(ctxl, CFL, reps=2)
-        kl = max(3, min(args.steps, 500))
-        msl, kerl, walll = timed_form(amm, torch, ctxl, Q0d, kl, min(args.warmup, 5), stream, flush)
-        forms["fp32_learned"] = {"value": nf / (statistics.mean(msl) * 1e-3), "ms_per_step": statistics.mean(msl),
-                                 "steps": kl, "kernels_ms": kerl, "training": tstats}
-        # Newton iterations per face from the same input, each form
-        for name, ctx in (("fp32", ctx32), ("fp32_learned", ctxl), ("fp64", ctx64)):
+    if rank != 0 or args.no_extras:
+        return line
+    from oracle import oracle as O
+    forms = {head: {"value": value, "ms_per_step": step_ms, "wall_s": wall}}
+    others = {"turbulent64": ("fp64", "fp32_learned"), "lognormal192": ("fp64",),
+              "learned192": ("fp32", "fp64")}[wl]
+    for prec in others:
+        ctxs[prec] = make(prec)
+        g.tune(ctxs[prec], args.tuning, 2)
+        # at most a few seconds of device time per extra form
+        k = max(3, min(args.steps, 200 if prec == "fp64" else 500, int((4e8 if prec == "fp64" else 2e9) / nf)))
+        msf, kerf, _ = timed_form(g, ctxs[prec], Q0d, k, min(args.warmup, 5))
+        forms[prec] = {"value": nf / (statistics.mean(msf) * 1e-3), "ms_per_step": statistics.mean(msf),
+                       "steps": k, "kernels_ms": kerf}
+    if "fp32_learned" in ctxs:
+        forms["fp32_learned"]["training"] = g.train_stats
+    for prec, ctx in ctxs.items():
+        forms[prec].update(newton_stats(amm, ctx, Q0))
+    if not args.no_cpu:
+        # error of each form against the oracle on one step (oracle dt); the
+        # oracle's own rate on a bounded sample is the CPU baseline
+        cores = host_threads()
+        rate, kcpu, secs, first = oracle_rate(P, motion, 8, budget_s=12.0, threads=cores)
+        rate1, kcpu1, _, _ = oracle_rate(P, motion, 8, budget_s=12.0, threads=1) if P.n_cells <= 300000 else \
+            (None, 0, None, None)
+        ref, dt, geom = first
+        W0 = O.primitives(O.Mesh(P.tess), Q0, geom[0], P.gamma)
+        fl = floors(Q0, W0, 3, P.gamma)
+        for prec, ctx in ctxs.items():
             amm.amm_set_state(ctx, Q0)
-            amm.amm_reset_stats(ctx)
+            amm.amm_step(ctx, dt)
+            emax, e999 = parity_errors(amm.amm_get_state(ctx), ref, fl)
+            forms[prec].update({"err_max": emax, "err_p999": e999})
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                                "sample": "%d full oracle step(s) of the workload (%d faces each), %d host threads"
+                                          % (kcpu, nf, cores),
+                                "one_thread": {"value": rate1, "steps": kcpu1}}
+    if wl == "lognormal192":
+        # 20 steps on the fixed tessellation, FP32 vs FP64 GPU forms
+        res = {}
+        for prec in ("fp32", "fp64"):
+            ctx = ctxs[prec]
+            amm.amm_set_state(ctx, Q0)
+            t0 = amm.amm_get_totals(ctx)
+            amm.amm_advance(ctx, CFL, 20, True)
+            res[prec] = (amm.amm_get_state(ctx), amm.amm_get_totals(ctx), t0, amm.amm_get_box_status(ctx))
+        c2 = P.gamma * (P.gamma - 1) * (Q0[:, 4] / Q0[:, 0] - 0.5 * (Q0[:, 1:4] ** 2).sum(1) / Q0[:, 0] ** 2)
+        fl = np.sqrt(np.mean(Q0 * Q0, axis=0))
+        fl[1:4] = np.sqrt(np.mean(Q0[:, 0] ** 2 * c2))
+        emax, e999 = parity_errors(res["fp32"][0], res["fp64"][0], fl)
+        mag = np.abs(Q0).sum(0)
+        line["twenty_steps"] = {
+            "fp32_vs_fp64_err_max": emax, "fp32_vs_fp64_err_p999": e999,
+            "conservation_drift": {p: (np.abs(np.asarray(r[1]).ravel() - np.asarray(r[2]).ravel()) / mag).tolist()
+                                   for p, r in res.items()},
+            "box_status": {p: int(np.asarray(r[3]).max()) for p, r in res.items()}}
+    if "fp64" in forms:
+        for prec in forms:
+            forms[prec]["vs_fp64"] = forms[prec]["value"] / forms["fp64"]["value"]
+    ke = max(3, min(args.steps, 200))
+    e2e_s, nbytes = e2e_rate(g, ctxs[head], Q0, ke)
+    line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "ms_per_step": 1e3 * e2e_s, "steps": ke}
+    line["forms"] = forms
+    return line
+
+
+def state_and_failures(amm, ctx):
+    """The state even after a numeric failure, with what failed: the Newton
+    solves that hit the iteration cap, the non-positive cells and the boxes
+    whose status word is set."""
+    import numpy as np
+    Q = np.empty((ctx.n, ctx.dim + 2))
+    amm.lib().amm_get_state(ctx.handle, Q.ctypes.data)
+    st = amm.amm_get_stats(ctx)
+    boxes = np.nonzero(np.asarray(amm.amm_get_box_status(ctx)))[0].tolist()
+    return Q, {"newton_cap_faces": st["newton_fail"], "nonpositive_cells": st["nonpositive_cells"],
+               "boxes_flagged": boxes}
+
+
+def bench_ensemble(args, g, world, rank, local):
+    """64 boxes of uneven size advanced together: each timed step is one
+    ensemble step (every box one step, its own Courant dt) of a 50-step run
+    from the initial state; the footprint is far above L2, so no flush."""
+    import numpy as np
+    from harness import ics
+    from oracle import oracle as O
+    amm, torch = g.amm, g.torch
+    E = ics.concat(ics.ensemble(64, seed=5 + rank))
+    n, nf, nb = E.n_cells, E.n_faces, len(E.problems)
+    Q0d = torch.from_numpy(E.Q).to("cuda")
+
+    def make(prec):
+        opt = amm.amm_default_options(prec, "eulerian", stream=g.stream.cuda_stream, entropy=True)
+        ctx = amm.amm_create(3, E.points, E.cells, E.shift, E.area, E.centroid, E.box, E.Q, E.gamma, opt,
+                             box_cells=E.box_cells, box_faces=E.box_faces)
+        if prec == "fp32_learned":
+            amm.amm_mlp_attach(ctx, g.proposal())
+        return ctx
+
+    def run(ctx, steps, warmup, profile):
+        amm.amm_profile(ctx, profile)
+        amm.amm_set_state_device(ctx, Q0d.data_ptr())
+        amm.amm_advance(ctx, CFL, warmup, True)
+        amm.amm_set_state_device(ctx, Q0d.data_ptr())
+        amm.amm_reset_stats(ctx)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        with torch.cuda.stream(g.stream):
+            ev[0].record(g.stream)
+        kt = []
+        for i in range(steps):
+            amm.amm_advance(ctx, CFL, 1, True)
+            with torch.cuda.stream(g.stream):
+                ev[i + 1].record(g.stream)
+            if profile:
+                kt.append(amm.amm_get_kernel_times(ctx))
+        torch.cuda.synchronize()
+        ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        ker = {k: statistics.median([d[k] for d in kt]) for k in kt[0]} if kt else None
+        return ms, ker
+
+    head = "fp32_learned"
+    ctxs = {head: make(head)}
+    tuning = g.tune(ctxs[head], args.tuning, 3)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    ms, _ = run(ctxs[head], args.steps, args.warmup, False)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    status = amm.amm_get_box_status(ctxs[head])
+    stats = amm.amm_get_stats(ctxs[head])
+    _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
+    step_ms = statistics.mean(ms)
+    faces_all = float(nf)
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+        tot = torch.tensor([float(nf)], device="cuda")
+        torch.distributed.all_reduce(tot)
+        faces_all = float(tot.item())
+    value = faces_all / (step_ms * 1e-3)
+    # per-phase times of the same shapes for the roofline (a persistent step
+    # is one launch)
+    if tuning["persistent"]:
+        amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 0)
+        _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
+        amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 1)
+    kern = kernel_table(ker, n, nf, 4)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["ensemble"], "boxes": nb, "cells": n, "faces": nf,
+                   "box_cells_min_max": [int(np.diff(E.box_cells).min()), int(np.diff(E.box_cells).max())],
+                   "form": "fp32_learned (learned p* proposal, FP32 bulk, exact fixed-point flux sums)",
+                   "l2": "footprint far above L2 (no flush); consecutive steps of one run",
+                   "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "tuning": tuning},
+        "cells_per_s": n * (faces_all / nf) / (step_ms * 1e-3),
+        "roofline": roofline(kern, nf, "learned_"),
+        "kernels": kern,
+        "gpu_launches": (1 if tuning["persistent"] else 4) * args.steps,
+        "clocks": clocks,
+        "boxes_flagged": int((np.asarray(status) != 0).sum()),
+        "entropy_kept_per_cell_update": stats["entropy_kept"] / float(n * args.steps),
+        "newton_iters_per_face": stats["newton_iters"] / max(1, stats["faces"]),
+    }
+    if rank != 0 or args.no_extras:
+        return line
+    forms = {head: {"value": value, "ms_per_step": step_ms, "newton_iters_per_face": line["newton_iters_per_face"],
+                    "training": g.train_stats}}
+    finals = {}
+    finals[head], forms[head]["failures"] = state_and_failures(amm, ctxs[head])
+    for prec in ("fp32", "fp64"):
+        ctxs[prec] = make(prec)
+        tp = g.tune(ctxs[prec], args.tuning, 2)
+        msf, _ = run(ctxs[prec], args.steps, 2, False)
+        st = amm.amm_get_stats(ctxs[prec])
+        forms[prec] = {"value": nf / (statistics.mean(msf) * 1e-3), "ms_per_step": statistics.mean(msf),
+                       "tuning": tp, "newton_iters_per_face": st["newton_iters"] / max(1, st["faces"])}
+        finals[prec], forms[prec]["failures"] = state_and_failures(amm, ctxs[prec])
+    for prec in forms:
+        forms[prec]["vs_fp64"] = forms[prec]["value"] / forms["fp64"]["value"]
+    # after the whole run: FP32 forms against the FP64 GPU form, per box
+    ref = finals["fp64"]
+    errs = {}
+    for prec in (head, "fp32"):
+        worst, per_box = 0.0, []
+        skip = set(forms[prec]["failures"]["boxes_flagged"]) | set(forms["fp64"]["failures"]["boxes_flagged"])
+        for b, Pb in enumerate(E.problems):
+            if b in skip:
+                continue
+            s = slice(E.box_cells[b], E.box_cells[b + 1])
+            Qb = E.Q[s]
+            c2 = Pb.gamma * (Pb.gamma - 1) * (Qb[:, 4] / Qb[:, 0] - 0.5 * (Qb[:, 1:4] ** 2).sum(1) / Qb[:, 0] ** 2)
+            fl = np.sqrt(np.mean(Qb * Qb, axis=0))
+            fl[1:4] = np.sqrt(np.mean(Qb[:, 0] ** 2 * c2))
+            e = parity_errors(finals[prec][s], ref[s], fl)
+            per_box.append(e[1])
+            worst = max(worst, e[0])
+        errs[prec] = {"max": worst, "median_box_p999": float(np.median(per_box)) if per_box else None,
+                      "boxes_compared": len(per_box)}
+    line["after_%d_steps_vs_fp64_gpu" % args.steps] = errs
+    if not args.no_cpu:
+        # one step of the smallest boxes against the oracle (its own dt per box)
+        order = np.argsort(np.diff(E.box_cells))[:4]
+        cores = host_threads()
+        O.set_threads(cores)
+        t_cpu, faces_cpu, worst = 0.0, 0, {p: 0.0 for p in ctxs}
+        outs, kept, flips = {}, {}, {p: 0 for p in ctxs}
+        for prec, ctx in ctxs.items():
+            amm.amm_set_state(ctx, E.Q)
             amm.amm_advance(ctx, CFL, 1, False)
-            s = amm.amm_get_stats(ctx)
-            forms[name]["newton_iters_per_face"] = s["newton_iters"] / max(1, s["faces"])
-            forms[name]["newton_hist"] = s["newton_hist"][:8]
-        if not args.no_cpu:
-            amm.amm_set_state(ctxl, Q0)
-            amm.amm_step(ctxl, dt)
-            emax, e999 = parity_errors(amm.amm_get_state(ctxl), ref, Q0, W0, 3, P.gamma)
-            forms["fp32_learned"].update({"err_max": emax, "err_p999": e999})
-        # end to end through the C ABI with pinned host buffers
-        Qh = torch.from_numpy(Q0.copy()).pin_memory()
-        Qo = torch.empty_like(Qh).pin_memory()
-        ke = max(3, min(args.steps, 200))
-        amm.amm_profile(ctx32, False)
-        for _ in range(3):
-            amm.amm_set_state(ctx32, Qh.numpy())
-            amm.amm_advance(ctx32, CFL, 1, True)
-            amm.amm_get_state(ctx32, Qo.numpy())
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            amm.amm_set_state(ctx32, Qh.numpy())
-            amm.amm_advance(ctx32, CFL, 1, True)
-            amm.amm_get_state(ctx32, Qo.numpy())
-        e2e_s = (time.perf_counter() - t0) / ke
-        line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": Q0.nbytes,
-                       "d2h_bytes_per_step": Q0.nbytes, "ms_per_step": 1e3 * e2e_s, "steps": ke}
-        line["forms"] = forms
+            outs[prec] = amm.amm_get_state(ctx)
+            kept[prec] = amm.amm_get_entropy(ctx)[1]
+        for b in order:
+            Pb = E.problems[b]
+            s = slice(E.box_cells[b], E.box_cells[b + 1])
+            M = O.Mesh(Pb.tess)
+            geom = O.geometry(M)
+            S0 = O.entropy_init(M, E.Q[s], geom[0], Pb.gamma)
+            t0 = time.perf_counter()
+            refb, _, kb, dt, _, rc = O.step_entropy(M, E.Q[s], S0, Pb.gamma, "eulerian", cfl=CFL, geom=geom)
+            t_cpu += time.perf_counter() - t0
+            faces_cpu += Pb.n_faces
+            W0 = O.primitives(M, E.Q[s], geom[0], Pb.gamma)
+            fl = floors(E.Q[s], W0, 3, Pb.gamma)
+            for prec in ctxs:
+                # cells whose switch decision differs (a value within rounding
+                # of its threshold) are counted, not compared
+                kg = kept[prec][s]
+                same = kg == kb
+                flips[prec] += int((~same).sum())
+                e = np.abs(outs[prec][s] - refb) / np.maximum(np.abs(refb), fl)
+                worst[prec] = max(worst[prec], float(e[same].max()))
+        for prec in ctxs:
+            forms[prec]["err_max_first_step_sampled_boxes"] = worst[prec]
+            forms[prec]["switch_decisions_differing_from_oracle"] = flips[prec]
+        line["cpu_baseline"] = {"value": faces_cpu / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "cpu": cpu_model(),
+                                "sample": "one oracle step of the %d smallest boxes (%d faces), %d host threads"
+                                          % (len(order), faces_cpu, cores)}
+    # end to end: host state in, 1 ensemble step, host state out
+    ke = max(3, min(args.steps, 20))
+    e2e_s, nbytes = e2e_rate(g, ctxs[head], E.Q, ke)
+    line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "ms_per_step": 1e3 * e2e_s, "steps": ke}
+    line["forms"] = forms
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g = Gpu(local, args.proposal_epochs)
+    if args.workload == "ensemble":
+        line = bench_ensemble(args, g, world, rank, local)
+    else:
+        line = bench_box(args, g, world, rank, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

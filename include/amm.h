@@ -78,6 +78,19 @@ typedef struct amm_options {
                                as int64 multiples of a per-box, per-component power of two, so the
                                update conserves exactly and is order independent; 1: sums in FP64
                                floating point (about 20x slower on GB300's FP64 pipe) */
+  int entropy;              /* 1: entropy switch of Sec. 3.5.  The total entropy S = M A of each cell
+                               (A = P / rho^gamma, reconstructed at the faces like the primitives) is
+                               advected with the face fluxes rho_F u_F A_upwind; a cell keeps its
+                               advected S and takes its thermal energy from it, P = (S/M) rho^gamma,
+                               when the largest shock Mach number of its faces' Riemann problems is
+                               below mach_thresh, or when alpha_s > 0 and its new thermal energy is
+                               below alpha_s times the largest kinetic energy of the cell and its
+                               neighbours (relative to the cell's mesh velocity, eq. eqnScrit1); other
+                               cells keep the conservative energy update and re-initialise
+                               S = M P / rho^gamma.  Total energy is then conserved only where no cell
+                               kept its entropy.  0 (default): the plain energy update. */
+  double mach_thresh;       /* shock Mach threshold of the switch (default 1.1) */
+  double alpha_s;           /* cold-flow parameter (default 0.01; 0 disables that criterion) */
 } amm_options;
 
 typedef struct amm_stats {
@@ -92,6 +105,7 @@ typedef struct amm_stats {
   int32_t newton_max;        /* largest iteration count on one face */
   uint32_t status;           /* bit 0 Newton cap, bit 1 non-positive cell, bit 2 wait timeout */
   int64_t newton_hist[16];   /* faces by Newton iteration count 0..14, 15 and more */
+  int64_t entropy_kept;      /* cell updates that kept the advected entropy (amm_options.entropy) */
 } amm_stats;
 
 typedef struct amm_ctx amm_ctx;
@@ -130,9 +144,18 @@ const char* amm_last_error(const amm_ctx* ctx);
 
 /* Replaces the cell states; host [n_cells][dim+2] or device (same layout).
  * Checks m > 0 and P > 0 (AMM_ERR_NONPOSITIVE_STATE).  Used for
- * checkpoint/resume: a resumed run is bitwise identical to an uninterrupted one. */
+ * checkpoint/resume: a resumed run is bitwise identical to an uninterrupted one.
+ * With the entropy switch, also sets each cell's entropy to S = M P / rho^gamma
+ * (a resumed run then also needs amm_set_entropy). */
 int amm_set_state(amm_ctx* ctx, const double* Q);
 int amm_set_state_device(amm_ctx* ctx, const double* Q_device);
+
+/* Entropy switch (amm_options.entropy): the cells' total entropies S = M A,
+ * host [n_cells]; amm_get_entropy also returns, if kept != NULL, 1 for the
+ * cells that kept their advected entropy in the last step, else 0 ([n_cells]).
+ * AMM_ERR_INVALID_ARG on a context without the switch, or for S <= 0. */
+int amm_get_entropy(amm_ctx* ctx, double* S, uint8_t* kept);
+int amm_set_entropy(amm_ctx* ctx, const double* S);
 
 /* Mesh-generator velocities for AMM_EXPLICIT_W, host [n_cells][dim] (Sec. 3.2). */
 int amm_set_mesh_velocity(amm_ctx* ctx, const double* w);
@@ -204,7 +227,8 @@ typedef struct amm_tuning {
   int flux_block;
   int persistent;  /* 1: amm_advance runs each step as ONE cooperative launch whose CTAs walk
                       every phase (gradients, fluxes, update, totals) with grid barriers between
-                      them (bounded waits); 0: one launch per phase.  Not for AMM_FP32_LEARNED. */
+                      them (bounded waits); 0: one launch per phase.  Both modes give
+                      bit-identical states, in every precision. */
   float step_ms;   /* amm_autotune: sum of the chosen kernels' median times */
 } amm_tuning;
 

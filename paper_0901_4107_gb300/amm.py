@@ -40,7 +40,8 @@ class amm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mesh_motion", ctypes.c_int), ("limiter", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("riemann_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("n_boxes", ctypes.c_int64), ("box_cells", ctypes.POINTER(ctypes.c_int64)),
-                ("box_faces", ctypes.POINTER(ctypes.c_int64)), ("fp64_accumulate", ctypes.c_int)]
+                ("box_faces", ctypes.POINTER(ctypes.c_int64)), ("fp64_accumulate", ctypes.c_int),
+                ("entropy", ctypes.c_int), ("mach_thresh", ctypes.c_double), ("alpha_s", ctypes.c_double)]
 
 
 class amm_stats(ctypes.Structure):
@@ -48,7 +49,7 @@ class amm_stats(ctypes.Structure):
                 ("newton_fail", ctypes.c_int64), ("fallback_faces", ctypes.c_int64),
                 ("vacuum_faces", ctypes.c_int64), ("guard_faces", ctypes.c_int64),
                 ("nonpositive_cells", ctypes.c_int64), ("newton_max", ctypes.c_int32), ("status", ctypes.c_uint32),
-                ("newton_hist", ctypes.c_int64 * 16)]
+                ("newton_hist", ctypes.c_int64 * 16), ("entropy_kept", ctypes.c_int64)]
 
 
 _lib = None
@@ -82,6 +83,8 @@ _SIGS = {
     "amm_get_dt": (_I, [_P, _P]),
     "amm_get_generators": (_I, [_P, _P]),
     "amm_get_stats": (_I, [_P, _P]),
+    "amm_get_entropy": (_I, [_P, _P, _P]),
+    "amm_set_entropy": (_I, [_P, _P]),
     "amm_reset_stats": (_I, [_P]),
     "amm_get_box_status": (_I, [_P, _P]),
     "amm_profile": (_I, [_P, _I]),
@@ -155,7 +158,7 @@ def _arr(a, dtype):
 
 
 def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True, max_iter=64, riemann_tol=0.0,
-                        stream=None, fp64_accumulate=False):
+                        stream=None, fp64_accumulate=False, entropy=False, mach_thresh=1.1, alpha_s=0.01):
     o = amm_options()
     lib().amm_default_options(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -165,6 +168,9 @@ def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True
     o.riemann_tol = float(riemann_tol)
     o.stream = stream
     o.fp64_accumulate = int(bool(fp64_accumulate))
+    o.entropy = int(bool(entropy))
+    o.mach_thresh = float(mach_thresh)
+    o.alpha_s = float(alpha_s)
     return o
 
 
@@ -314,6 +320,19 @@ def amm_get_stats(ctx):
     d = {f: getattr(s, f) for f, _ in amm_stats._fields_ if f != "newton_hist"}
     d["newton_hist"] = list(s.newton_hist)
     return d
+
+
+def amm_get_entropy(ctx):
+    """(S [n], kept [n] 0/1) of a context with the entropy switch."""
+    S = np.empty(ctx.n)
+    kept = np.empty(ctx.n, np.uint8)
+    _check(ctx, lib().amm_get_entropy(ctx.handle, S.ctypes.data, kept.ctypes.data))
+    return S, kept
+
+
+def amm_set_entropy(ctx, S):
+    S = _arr(S, np.float64)
+    _check(ctx, lib().amm_set_entropy(ctx.handle, S.ctypes.data))
 
 
 def amm_get_box_status(ctx):

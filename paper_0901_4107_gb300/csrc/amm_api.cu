@@ -47,8 +47,8 @@ void free_ctx(amm_ctx* c) {
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
-                  c->ftiles, c->box_first_ctile, c->fgeo, c->cgeo64, c->W,   c->P,       c->grad,
-                  c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
+                  c->ftiles, c->box_first_ctile, c->fgeo, c->igA, c->igB, c->igz, c->nbr, c->cgeo64, c->W,   c->P,       c->grad,
+                  c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -141,6 +141,9 @@ void amm_default_options(amm_options* o) {
   o->n_boxes = 1;
   o->box_cells = nullptr;
   o->box_faces = nullptr;
+  o->entropy = 0;
+  o->mach_thresh = 1.1;
+  o->alpha_s = 0.01;
 }
 
 const char* amm_last_error(const amm_ctx* c) {
@@ -167,6 +170,9 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   if (opt.mesh_motion < AMM_EULERIAN || opt.mesh_motion > AMM_EXPLICIT_W) return AMM_ERR_INVALID_ARG;
   if (opt.max_iter < 1 || opt.max_iter > 10000) return AMM_ERR_INVALID_ARG;
   if (opt.n_boxes < 1 || opt.n_boxes > (1 << 20)) return AMM_ERR_INVALID_ARG;
+  if (opt.entropy != 0 && opt.entropy != 1) return AMM_ERR_INVALID_ARG;
+  if (opt.entropy && (!(opt.mach_thresh >= 0.0) || !(opt.alpha_s >= 0.0) || !std::isfinite(opt.alpha_s)))
+    return AMM_ERR_INVALID_ARG;
   if (!(opt.riemann_tol > 0.0)) opt.riemann_tol = (opt.precision == AMM_FP64) ? 1e-12 : 1e-6;
   const int nb = (int)opt.n_boxes;
   std::vector<int64_t> bc(nb + 1), bf(nb + 1);
@@ -385,6 +391,10 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   CUB(dalloc(&c->ftiles, ft.size()));
   CUB(dalloc(&c->box_first_ctile, (size_t)nb + 1));
   CUB(cudaMalloc(&c->fgeo, rs * 4 * 2 * (size_t)nf));
+  CUB(cudaMalloc(&c->igA, rs * 4 * 2 * (size_t)nf));
+  CUB(cudaMalloc(&c->igB, rs * 4 * 2 * (size_t)nf));
+  CUB(cudaMalloc(&c->igz, rs * 2 * (size_t)nf));
+  CUB(dalloc(&c->nbr, (size_t)2 * nf));
   CUB(dalloc(&c->cgeo64, (size_t)n));
   CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
   CUB(cudaMalloc(&c->crad, rs * (size_t)n));
@@ -398,9 +408,20 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
 
   CUB(cudaMalloc(&c->flux, rs * 4 * (size_t)nf));
   CUB(cudaMalloc(&c->fluxE, rs * (size_t)nf));
+  if (opt.entropy) {
+    CUB(dalloc(&c->S, (size_t)n));
+    CUB(cudaMalloc(&c->Aw, rs * (size_t)n));
+    CUB(cudaMalloc(&c->gradA, rs * 4 * (size_t)n));
+    CUB(cudaMalloc(&c->fluxS, rs * (size_t)nf));
+    CUB(cudaMalloc(&c->machf, rs * (size_t)nf));
+    CUB(cudaMalloc(&c->ekmax, rs * (size_t)n));
+    CUB(dalloc(&c->kept, (size_t)n));
+    CUB(cudaMemsetAsync(c->ekmax, 0, rs * (size_t)n, c->stream));
+    CUB(cudaMemsetAsync(c->kept, 0, (size_t)n, c->stream));
+  }
   CUB(dalloc(&c->cour_bits, (size_t)nb));
-  CUB(dalloc(&c->fmax_bits, (size_t)5 * nb));
-  CUB(cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * 5 * nb, c->stream));
+  CUB(dalloc(&c->fmax_bits, (size_t)amm::FMAX_STRIDE * nb));
+  CUB(cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * amm::FMAX_STRIDE * nb, c->stream));
   CUB(dalloc(&c->dt_box, (size_t)nb));
   CUB(dalloc(&c->dt_used, (size_t)nb));
   CUB(dalloc(&c->partial, (size_t)5 * 8 * ct.size()));
@@ -576,13 +597,17 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
   if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
     return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
   if (nsteps == 0) return AMM_OK;
-  const bool pers = c->persistent && c->opt.precision != AMM_FP32_LEARNED;
+  const bool pers = c->persistent != 0;
   auto one_step = [&]() -> cudaError_t {
     if (pers) {
       cudaError_t e = mark(c, 0);
-      if (e == cudaSuccess)
-        e = dispatch(c, [&] { return amm::launch_step_persistent<double>(c, cfl); },
-                     [&] { return amm::launch_step_persistent<float>(c, cfl); });
+      if (e == cudaSuccess) {
+        if (c->opt.precision == AMM_FP32_LEARNED)
+          e = amm::launch_step_persistent_learned(c, cfl);
+        else
+          e = dispatch(c, [&] { return amm::launch_step_persistent<double>(c, cfl); },
+                       [&] { return amm::launch_step_persistent<float>(c, cfl); });
+      }
       if (e == cudaSuccess) e = mark(c, 1);
       if (e == cudaSuccess) e = mark(c, 2);
       if (e == cudaSuccess) e = mark(c, 3);
@@ -770,6 +795,36 @@ int amm_get_generators(amm_ctx* c, double* gen) {
   return AMM_OK;
 }
 
+int amm_get_entropy(amm_ctx* c, double* S, uint8_t* kept) {
+  if (!c || !S) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->opt.entropy) return fail(c, AMM_ERR_INVALID_ARG, "the context has no entropy switch");
+  std::vector<double> s((size_t)c->n);
+  std::vector<unsigned char> k((size_t)c->n);
+  CU(cudaMemcpyAsync(s.data(), c->S, sizeof(double) * s.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(k.data(), c->kept, k.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < c->n; i++) {
+    S[c->perm_h[i]] = s[i];
+    if (kept) kept[c->perm_h[i]] = k[i];
+  }
+  return check_status(c);
+}
+
+int amm_set_entropy(amm_ctx* c, const double* S) {
+  if (!c || !S) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->opt.entropy) return fail(c, AMM_ERR_INVALID_ARG, "the context has no entropy switch");
+  std::vector<double> s((size_t)c->n);
+  for (int64_t i = 0; i < c->n; i++) {
+    s[i] = S[c->perm_h[i]];
+    if (!(s[i] > 0.0) || !std::isfinite(s[i])) return fail(c, AMM_ERR_INVALID_ARG, "entropy must be positive");
+  }
+  CU(cudaMemcpyAsync(c->S, s.data(), sizeof(double) * s.size(), cudaMemcpyHostToDevice, c->stream));
+  CU(dispatch(c, [&] { return amm::launch_primitives<double>(c); }, [&] { return amm::launch_primitives<float>(c); }));
+  CU(cudaStreamSynchronize(c->stream));
+  c->grads_fresh = false;
+  return AMM_OK;
+}
+
 int amm_get_stats(amm_ctx* c, amm_stats* s) {
   if (!c || !s) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
   amm::DeviceStats d;
@@ -787,6 +842,7 @@ int amm_get_stats(amm_ctx* c, amm_stats* s) {
   s->newton_max = (int32_t)d.newton_max;
   s->status = d.status;
   for (int b = 0; b < 16; b++) s->newton_hist[b] = (int64_t)d.hist[b];
+  s->entropy_kept = (int64_t)d.kept;
   return AMM_OK;
 }
 
@@ -898,7 +954,7 @@ int amm_autotune(amm_ctx* c, double cfl, int reps, amm_tuning* out) {
   rc = amm_set_tuning(c, &t);
   // then the whole step: the tuned kernel sequence against one persistent
   // launch (event-timed full steps from the same state)
-  if (rc == AMM_OK && c->opt.precision != AMM_FP32_LEARNED) {
+  if (rc == AMM_OK) {
     float best_ms[2] = {1e30f, 1e30f};
     cudaEvent_t e0, e1;
     CU(cudaMalloc((void**)&saved, sizeof(double) * qn));

@@ -14,6 +14,11 @@
 //              flux   R4<real> {A F_m, A F_px, A F_py, A F_pz}, fluxE real A F_E
 //   cell->face csr_off int [n+1], csr int2 {face << 1 | side, neighbour}
 //              (side 0: the cell is the face's left cell), in face order.
+//   per incidence (csr order; the gradient kernel streams them):
+//              igA R4<real> {A c / |d|, A s n_x / 2}
+//              igB R4<real> {A s n_y / 2, A s n_z / 2, (f - s_i)_x, (f - s_i)_y}
+//              igz real (f - s_i)_z     nbr int  the neighbour j
+//              (s = +1 for the face's left cell, -1 for its right cell)
 //   numbering  cells are renumbered along a Morton curve per box and faces
 //              sorted by their new left cell; cell_perm / face_perm map back
 //   tiles      contiguous cell / face ranges, each inside one box; one CTA
@@ -47,10 +52,14 @@ struct Tile {
 
 enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u };
 
+// per-box largest |A F| slots: m, p (3), E, and the entropy flux
+constexpr int FMAX_STRIDE = 6;
+
 struct DeviceStats {
   unsigned long long steps, faces, newton_iters, newton_fail, fallback, vacuum, guard, nonpos;
   unsigned int newton_max, status;
   unsigned long long hist[16];
+  unsigned long long kept;
 };
 
 // Ideal-gas constants in the bulk arithmetic type, derived once on the host.
@@ -99,7 +108,7 @@ struct HydroView {
   int fixed_acc;               // FP32 forms: exact int64 fixed-point flux sums
   int headroom;                // bits reserved for the incidence count in the fixed-point sums
   int update_lanes;            // lanes per cell of the update kernel (partial sums per block)
-  unsigned* fmax_bits;         // [nboxes][5] max |A F| per component (float bits) of the step
+  unsigned* fmax_bits;         // [nboxes][FMAX_STRIDE] max |A F| per component (float bits) of the step
   // dt source: dt_box[b] if cfl <= 0, else cfl * courant_min[b]
   double cfl;
   const double* dt_box;
@@ -119,6 +128,10 @@ struct HydroView {
   real* fluxE;
   const int* csr_off;
   const int2* csr;
+  const R4<real>* igA;
+  const R4<real>* igB;
+  const real* igz;
+  const int* nbr;
   const Tile* ctiles;
   const Tile* ftiles;
   const int* cell_perm;        // internal -> caller numbering
@@ -128,6 +141,16 @@ struct HydroView {
   const int* box_first_ctile; // [nboxes+1]
   DeviceStats* stats;
   unsigned* box_status;        // [nboxes] StatusBits of each box
+  // entropy switch (Sec. 3.5)
+  int entropy;
+  double mach_thresh, alpha_s;
+  double* S;                   // [n] total entropy M A
+  real* Aw;                    // [n] entropic function A = S / M of the current state
+  R4<real>* gradA;             // [n] {limited grad A, 0}
+  real* fluxS;                 // [nf] A F_S
+  real* machf;                 // [nf] largest shock Mach number of the face's Riemann problem
+  real* ekmax;                 // [n] largest kinetic energy of the cell and its neighbours
+  unsigned char* kept;         // [n] 1 where the last update kept the advected entropy
   // learned proposal (FP32 learned form only)
   const void* mlp;
   float* harvest;              // if set, the flux kernel records each face's Riemann inputs [nf][6]
@@ -163,6 +186,10 @@ struct amm_ctx {
   int* face_perm = nullptr;        // [nf] internal face -> caller's face
   std::vector<int> perm_h;         // host copy of cell_perm
   void* fgeo = nullptr;            // [nf][2] R4<real>
+  void* igA = nullptr;             // [2 nf] R4<real> per-incidence gradient weights
+  void* igB = nullptr;             // [2 nf] R4<real>
+  void* igz = nullptr;             // [2 nf] real
+  int* nbr = nullptr;              // [2 nf]
   void* cgeo = nullptr;            // [n] R4<real> {1/V, s - r}
   void* crad = nullptr;            // [n] real, effective radius
   amm::R4<double>* cgeo64 = nullptr;
@@ -173,7 +200,14 @@ struct amm_ctx {
   void* flux = nullptr;
   void* fluxE = nullptr;
   unsigned long long* cour_bits = nullptr;
-  unsigned* fmax_bits = nullptr;   // [nboxes][5]
+  unsigned* fmax_bits = nullptr;   // [nboxes][FMAX_STRIDE]
+  double* S = nullptr;             // entropy switch: [n] total entropy
+  void* Aw = nullptr;              // [n] real
+  void* gradA = nullptr;           // [n] R4<real>
+  void* fluxS = nullptr;           // [nf] real
+  void* machf = nullptr;           // [nf] real
+  void* ekmax = nullptr;           // [n] real
+  unsigned char* kept = nullptr;   // [n]
   int headroom = 7;
   int grad_lanes = 4;              // lanes per cell in the gradient kernel
   int update_lanes = 4;            // lanes per cell in the update kernel
@@ -242,11 +276,13 @@ cudaError_t launch_get_flux(amm_ctx* c, double* F_device);
 template <typename real>
 cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
 
-// flux_learned.cu: the FP32 flux kernel with the fused proposal network
+// flux_learned.cu: the FP32 flux kernel with the fused proposal network, and
+// the learned form's whole step as one cooperative launch
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
+cudaError_t launch_step_persistent_learned(amm_ctx* c, double cfl);
 cudaError_t prepare_flux_learned();
 
-// persistent.cu: the whole step as one cooperative launch
+// persistent_f32.cu / persistent_f64.cu: the whole step as one cooperative launch
 template <typename real>
 cudaError_t launch_step_persistent(amm_ctx* c, double cfl);
 

@@ -1,25 +1,33 @@
-// Face fluxes of the FP32 learned form: the flux kernel with the proposal
-// network fused in.  Each CTA of 128 threads walks 128-face tiles
-// (persistently); per tile every thread extrapolates its face (face_prepare),
-// writes the normalised features as row t of a BF16 operand, one thread
-// issues the two tensor-core layers (tcgen05, FP32 accumulators in tensor
-// memory, 64 columns reused by both layers), every thread reads its row back,
-// forms p0 = pbar exp(y) and runs the exact Riemann solver from it
-// (face_finish).  Newton still iterates to the same tolerance, so the result
-// does not depend on the network beyond the iteration count.
+// Face fluxes of the FP32 learned form: the flux work with the proposal
+// network fused in.  A CTA of H x 128 threads handles H x 128 faces at a
+// time: every thread extrapolates its face (face_prepare) and writes the
+// normalised features as row (t mod 128) of the BF16 operand of its group,
+// one thread issues the tensor-core layers of all groups (tcgen05, FP32
+// accumulators in tensor memory: group h owns columns 64h..64h+63, reused by
+// both layers), every thread reads its row back, forms p0 = pbar exp(y) and
+// runs the exact Riemann solver from it (face_finish).  Newton still iterates
+// to the same tolerance, so the result depends on the network only through
+// the iteration count.
+//
+// Two kernels use it: k_flux_learned (H = 1, the flux phase of the kernel
+// sequence) and k_step_persistent_learned (H = 2, the whole step as one
+// cooperative launch, the batched-ensemble form).  Both run the identical
+// per-face arithmetic, so the two step modes give bit-identical states.
 #include <cuda_runtime.h>
 
 #include "hydro.cuh"
 #include "learned.cuh"
+#include "persistent.cuh"
 #include "tc.cuh"
 
 namespace amm {
 
-constexpr int LT = 128;  // faces per tile = threads per CTA = MMA rows
+constexpr int LT = 128;  // faces per MMA group = MMA rows
 
+template <int H>
 struct LearnedSmem {
-  alignas(1024) uint8_t a1[LT * 16 * 2];
-  alignas(1024) uint8_t a2[LT * MLP_HID * 2];
+  alignas(1024) uint8_t a1[H][LT * 16 * 2];
+  alignas(1024) uint8_t a2[H][LT * MLP_HID * 2];
   alignas(1024) uint8_t b1[MLP_HID * 16 * 2];
   alignas(1024) uint8_t b2[MLP_HID * MLP_HID * 2];
   float bias1[MLP_HID], bias2[MLP_HID], w3[MLP_HID], bias3;
@@ -29,6 +37,16 @@ struct LearnedSmem {
   uint32_t ok;
 };
 
+template <int H>
+__host__ __device__ constexpr size_t learned_smem_bytes() {
+  return sizeof(LearnedSmem<H>) + 1024;  // + alignment slack of the dynamic block
+}
+
+template <int H>
+__device__ __forceinline__ LearnedSmem<H>& learned_smem_ref(uint8_t* raw) {
+  return *reinterpret_cast<LearnedSmem<H>*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+}
+
 // SiLU from one hardware tanh: z sigma(z) = z/2 (1 + tanh(z/2)); the
 // proposal only seeds Newton, so the approximate tanh is accurate enough
 __device__ __forceinline__ float silu_fast(float z) {
@@ -37,21 +55,19 @@ __device__ __forceinline__ float silu_fast(float z) {
   return 0.5f * z * (1.0f + t);
 }
 
-__global__ void __launch_bounds__(LT, 4) k_flux_learned(HydroView<float> v, int nsub) {
-  extern __shared__ uint8_t smem_raw[];
-  LearnedSmem& s =
-      *reinterpret_cast<LearnedSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const MlpDevice* M = (const MlpDevice*)v.mlp;
+// tensor-memory allocation (64 H columns), mbarrier, weights into shared
+// memory in the K-major core-matrix layout of the MMA operands
+template <int H>
+__device__ __forceinline__ void learned_setup(LearnedSmem<H>& s, const MlpDevice* M) {
   const int t = threadIdx.x;
-  const int warp = t >> 5;
-  if (t < 32) tc::tmem_alloc(&s.tmem, 64);
+  if (t < 32) tc::tmem_alloc(&s.tmem, 64 * H);
   if (t == 0) {
     tc::mbar_init(&s.mbar, 1);
     s.ok = 1;
   }
-  for (int i = t; i < MLP_HID * 16; i += LT)
+  for (int i = t; i < MLP_HID * 16; i += H * LT)
     *reinterpret_cast<__nv_bfloat16*>(s.b1 + tc::kmajor_offset(i / 16, i % 16, 16)) = M->W1[i];
-  for (int i = t; i < MLP_HID * MLP_HID; i += LT)
+  for (int i = t; i < MLP_HID * MLP_HID; i += H * LT)
     *reinterpret_cast<__nv_bfloat16*>(s.b2 + tc::kmajor_offset(i / MLP_HID, i % MLP_HID, MLP_HID)) = M->W2[i];
   if (t < MLP_HID) {
     s.bias1[t] = M->b1[t];
@@ -59,88 +75,157 @@ __global__ void __launch_bounds__(LT, 4) k_flux_learned(HydroView<float> v, int 
     s.w3[t] = __bfloat162float(M->W3[t]);
   }
   if (t == 0) s.bias3 = M->b3;
-  const uint32_t idesc = tc::make_idesc(128, 64);
+}
+
+// H x 128 faces starting at `first` (faces at or past `end` are padding)
+template <int H, bool ENT>
+__device__ __forceinline__ void learned_faces(const HydroView<float>& v, LearnedSmem<H>& s, const Tile& tile,
+                                              int first, uint32_t& phase) {
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int h = t / LT;       // MMA group of this thread
+  const int row = t % LT;     // its row in the group's tiles
+  const int quad = warp & 3;  // tensor-memory lane quadrant this warp may read
+  const uint32_t idesc = tc::make_idesc(LT, MLP_HID);
   const float g = v.gas.g;
+  const int k0 = first + t;
+  const bool valid = k0 < tile.end;
+  if (t == 0) s.hdt = (float)(0.5 * box_dt(v, tile.box));
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  FaceWork<float> f;
+  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, f);
+  // normalised features (the network's input)
+  const float rb = 0.5f * (f.WppL[0] + f.WppR[0]);
+  const float pb = 0.5f * (f.WppL[4] + f.WppR[4]);
+  const float icb = rsqrtf(g * pb / rb);
+  {
+    const float irb = 1.0f / rb, ipb = 1.0f / pb;
+    float x[16] = {__logf(f.WppL[0] * irb), __logf(f.WppL[4] * ipb), f.uL * icb, __logf(f.WppR[0] * irb),
+                   __logf(f.WppR[4] * ipb), f.uR * icb, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    tc::st_bf16x8(s.a1[h], tc::kmajor_offset(row, 0, 16), x);
+    tc::st_bf16x8(s.a1[h], tc::kmajor_offset(row, 8, 16), x + 8);
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < H; q++)
+      tc::mma_bf16(s.tmem + 64 * q, tc::kmajor_desc(tc::smem_addr(s.a1[q]), 16),
+                   tc::kmajor_desc(tc::smem_addr(s.b1), 16), idesc, false);
+    tc::mma_commit(&s.mbar);
+  }
+  if (!tc::mbar_wait(&s.mbar, phase)) s.ok = 0;
+  phase ^= 1u;
+  tc::fence_after_sync();
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    float z[16];
+    tc::tmem_ld16(tc::tmem_lane_addr(s.tmem, quad, 64 * h + 16 * c), z);
+#pragma unroll
+    for (int j = 0; j < 16; j++) z[j] = silu_fast(z[j] + s.bias1[16 * c + j]);
+    tc::st_bf16x8(s.a2[h], tc::kmajor_offset(row, 16 * c, MLP_HID), z);
+    tc::st_bf16x8(s.a2[h], tc::kmajor_offset(row, 16 * c + 8, MLP_HID), z + 8);
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < H; q++)
+#pragma unroll
+      for (int kb = 0; kb < MLP_HID / 16; kb++)
+        tc::mma_bf16(s.tmem + 64 * q, tc::kmajor_desc(tc::smem_addr(s.a2[q]) + 256 * kb, MLP_HID),
+                     tc::kmajor_desc(tc::smem_addr(s.b2) + 256 * kb, MLP_HID), idesc, kb > 0);
+    tc::mma_commit(&s.mbar);
+  }
+  if (!tc::mbar_wait(&s.mbar, phase)) s.ok = 0;
+  phase ^= 1u;
+  tc::fence_after_sync();
+  float y = s.bias3;
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    float z[16];
+    tc::tmem_ld16(tc::tmem_lane_addr(s.tmem, quad, 64 * h + 16 * c), z);
+#pragma unroll
+    for (int j = 0; j < 16; j++) y += s.w3[16 * c + j] * silu_fast(z[j] + s.bias2[16 * c + j]);
+  }
+  y = fminf(fmaxf(y, -30.0f), 30.0f);
+  const bool use = s.ok != 0;  // after a timed-out wait, fall back to the standard guess
+  face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), use, pb * __expf(y));
+}
+
+template <int H>
+__device__ __forceinline__ void learned_teardown(const HydroView<float>& v, LearnedSmem<H>& s) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0 && !s.ok) atomicOr(&v.stats->status, (unsigned)ST_TIMEOUT);
+  if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, 64 * H);
+}
+
+// flux phase alone: CTAs walk the 128-face halves of the face tiles
+template <bool ENT>
+__global__ void __launch_bounds__(LT, 4) k_flux_learned(HydroView<float> v, int nsub) {
+  extern __shared__ uint8_t smem_raw[];
+  LearnedSmem<1>& s = learned_smem_ref<1>(smem_raw);
+  learned_setup<1>(s, (const MlpDevice*)v.mlp);
   uint32_t phase = 0;
   for (int st = blockIdx.x; st < nsub; st += gridDim.x) {
     const Tile tile = v.ftiles[st >> 1];
-    const int first = tile.begin + (st & 1) * LT;
-    const int k0 = first + t;
-    const bool valid = k0 < tile.end;
-    if (t == 0) s.hdt = (float)(0.5 * box_dt(v, tile.box));
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    FaceWork<float> f;
-    face_prepare(v, valid ? k0 : tile.begin, valid, s.hdt, f);
-    // normalised features (the network's input)
-    const float rb = 0.5f * (f.WppL[0] + f.WppR[0]);
-    const float pb = 0.5f * (f.WppL[4] + f.WppR[4]);
-    const float icb = rsqrtf(g * pb / rb);
-    {
-      const float irb = 1.0f / rb, ipb = 1.0f / pb;
-      float row[16] = {__logf(f.WppL[0] * irb), __logf(f.WppL[4] * ipb), f.uL * icb, __logf(f.WppR[0] * irb),
-                       __logf(f.WppR[4] * ipb), f.uR * icb, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-      tc::st_bf16x8(s.a1, tc::kmajor_offset(t, 0, 16), row);
-      tc::st_bf16x8(s.a1, tc::kmajor_offset(t, 8, 16), row + 8);
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) {
-      tc::mma_bf16(s.tmem, tc::kmajor_desc(tc::smem_addr(s.a1), 16), tc::kmajor_desc(tc::smem_addr(s.b1), 16), idesc,
-                   false);
-      tc::mma_commit(&s.mbar);
-    }
-    if (!tc::mbar_wait(&s.mbar, phase)) s.ok = 0;
-    phase ^= 1u;
-    tc::fence_after_sync();
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      float z[16];
-      tc::tmem_ld16(tc::tmem_lane_addr(s.tmem, warp, 16 * c), z);
-#pragma unroll
-      for (int j = 0; j < 16; j++) z[j] = silu_fast(z[j] + s.bias1[16 * c + j]);
-      tc::st_bf16x8(s.a2, tc::kmajor_offset(t, 16 * c, MLP_HID), z);
-      tc::st_bf16x8(s.a2, tc::kmajor_offset(t, 16 * c + 8, MLP_HID), z + 8);
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) {
-#pragma unroll
-      for (int kb = 0; kb < MLP_HID / 16; kb++)
-        tc::mma_bf16(s.tmem, tc::kmajor_desc(tc::smem_addr(s.a2) + 256 * kb, MLP_HID),
-                     tc::kmajor_desc(tc::smem_addr(s.b2) + 256 * kb, MLP_HID), idesc, kb > 0);
-      tc::mma_commit(&s.mbar);
-    }
-    if (!tc::mbar_wait(&s.mbar, phase)) s.ok = 0;
-    phase ^= 1u;
-    tc::fence_after_sync();
-    float y = s.bias3;
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      float z[16];
-      tc::tmem_ld16(tc::tmem_lane_addr(s.tmem, warp, 16 * c), z);
-#pragma unroll
-      for (int j = 0; j < 16; j++) y += s.w3[16 * c + j] * silu_fast(z[j] + s.bias2[16 * c + j]);
-    }
-    y = fminf(fmaxf(y, -30.0f), 30.0f);
-    const bool use = s.ok != 0;   // after a timed-out wait, fall back to the standard guess
-    face_finish<float, LT>(v, f, tile.box, min(LT, tile.end - first), use, pb * __expf(y));
+    learned_faces<1, ENT>(v, s, tile, tile.begin + (st & 1) * LT, phase);
   }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (t == 0 && !s.ok) atomicOr(&v.stats->status, (unsigned)ST_TIMEOUT);
-  if (t < 32) tc::tmem_dealloc(s.tmem, 64);
+  learned_teardown<1>(v, s);
 }
 
-static size_t learned_smem() { return sizeof(LearnedSmem) + 1024; }
+// the whole step in one cooperative launch (see persistent.cuh), with the
+// flux phase on whole 256-face tiles, two MMA groups per CTA
+constexpr int PL_H = FACE_TILE / LT;
+static_assert(PL_H * LT == CELL_TILE, "the persistent CTA covers one face tile and one cell tile");
+
+template <bool ENT>
+__global__ void __launch_bounds__(CELL_TILE) k_step_persistent_learned(HydroView<float> v, unsigned* bar) {
+  extern __shared__ uint8_t smem_raw[];
+  LearnedSmem<PL_H>& s = learned_smem_ref<PL_H>(smem_raw);
+  learned_setup<PL_H>(s, (const MlpDevice*)v.mlp);
+  const int n_grad = v.n_ctiles * 4;
+  for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<float, 4, ENT>(v, wi);
+  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  uint32_t phase = 0;
+  for (int wi = blockIdx.x; wi < v.n_ftiles; wi += gridDim.x) {
+    const Tile tile = v.ftiles[wi];
+    learned_faces<PL_H, ENT>(v, s, tile, tile.begin, phase);
+  }
+  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) update_item<float, 1, ENT>(v, wi);
+  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  for (int b = blockIdx.x; b < v.nboxes; b += gridDim.x) finish_item<float, CELL_TILE>(v, b, 1);
+  learned_teardown<PL_H>(v, s);
+}
+
+// Tensor memory is 512 columns per SM and an allocation waits until enough
+// are free; the persistent kernel keeps its 128 columns until it ends, so at
+// most four of its CTAs may share an SM.  Its shared-memory block alone rules
+// out a fifth (GB300: 228 KB of shared memory per SM).
+static_assert(5 * learned_smem_bytes<PL_H>() > 228 * 1024, "more than 4 persistent learned CTAs could share an SM");
+static_assert(4 * 64 * PL_H <= 512, "tensor-memory columns of 4 co-resident CTAs");
 
 cudaError_t prepare_flux_learned() {
-  return cudaFuncSetAttribute(k_flux_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)learned_smem());
+  cudaError_t e = cudaFuncSetAttribute(k_flux_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)learned_smem_bytes<1>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)learned_smem_bytes<1>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step_persistent_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)learned_smem_bytes<PL_H>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step_persistent_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)learned_smem_bytes<PL_H>());
+  return e;
 }
 
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
@@ -150,8 +235,38 @@ cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int nsub = 2 * c->n_ftiles;
   const int grid = std::min(nsub, 4 * sms);
-  k_flux_learned<<<grid, LT, learned_smem(), c->stream>>>(v, nsub);
+  if (c->opt.entropy)
+    k_flux_learned<true><<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
+  else
+    k_flux_learned<false><<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
   return cudaGetLastError();
+}
+
+cudaError_t launch_step_persistent_learned(amm_ctx* c, double cfl) {
+  if (!c->mlp) return cudaErrorInvalidValue;
+  auto v = make_view<float>(c, cfl);
+  v.update_lanes = 1;
+  cudaError_t e = cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * FMAX_STRIDE * c->nboxes, c->stream);
+  if (e != cudaSuccess) return e;
+  const size_t smem = learned_smem_bytes<PL_H>();
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  auto kern = c->opt.entropy ? k_step_persistent_learned<true> : k_step_persistent_learned<false>;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CELL_TILE, smem)) != cudaSuccess) return e;
+  if (per_sm < 1 || per_sm > 4) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(per_sm * sms));
+  cfg.blockDim = dim3(CELL_TILE);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, v, c->barrier);
 }
 
 }  // namespace amm

@@ -103,6 +103,44 @@ __global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad,
   crad[i] = (real)((dim == 3) ? cbrt(3.0 * a.x / (4.0 * M_PI)) : sqrt(a.x / M_PI));
 }
 
+// Per-incidence weights of the gradient (eq. eqngrad2) and of the limiter,
+// in the order of the cell->face lists: for incidence q of cell i through
+// face k (sign s = +1 if i is the face's left cell, else -1, so s n points
+// out of i), A c / |d| and A s n / 2 multiply [phi_j - phi_i] and
+// (phi_i + phi_j) in the gradient sum, and f - s_i = s |d|/2 n + c - (s_i - r_i)
+// is the limiter's lever arm.  Computed once per tessellation from the
+// bulk-precision face and cell geometry.
+template <typename real>
+__global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr, const R4<real>* fgeo,
+                                     const R4<real>* cgeo, R4<real>* igA, R4<real>* igB, real* igz, int* nbr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R4<real> cg = cgeo[i];
+  for (int q = csr_off[i]; q < csr_off[i + 1]; q++) {
+    const int2 e = csr[q];
+    const int k = e.x >> 1;
+    const real sg = (e.x & 1) ? (real)-1 : (real)1;
+    const R4<real> G0 = fgeo[2 * (size_t)k];
+    const R4<real> G1 = fgeo[2 * (size_t)k + 1];
+    const real a_r = G1.w / G0.w;
+    const real a_h = (real)0.5 * G1.w * sg;
+    const real hs = (real)0.5 * sg * G0.w;
+    R4<real> a, b;
+    a.x = a_r * G1.x;
+    a.y = a_r * G1.y;
+    a.z = a_r * G1.z;
+    a.w = a_h * G0.x;
+    b.x = a_h * G0.y;
+    b.y = a_h * G0.z;
+    b.z = hs * G0.x + G1.x - cg.y;
+    b.w = hs * G0.y + G1.y - cg.z;
+    igA[q] = a;
+    igB[q] = b;
+    igz[q] = hs * G0.z + G1.z - cg.w;
+    nbr[q] = e.y;
+  }
+}
+
 // A10: r_i <- r_i + w_i dt, wrapped into the box; w from the mesh mode
 __global__ void k_drift(const Tile* ctiles, int mode, int precision, double* gen, const double* box,
                         const double* Q, int n, const void* wmesh, double dt) {
@@ -153,10 +191,16 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
   if (c->is_fp64()) {
     k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad, (int)c->n,
                                                        c->dim);
+    k_incidence_geometry<double><<<nbc, 256, 0, c->stream>>>(
+        (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igA,
+        (R4<double>*)c->igB, (double*)c->igz, c->nbr);
   } else {
     k_cast4<float><<<(unsigned)((nfg + 255) / 256), 256, 0, c->stream>>>(fg64, (R4<float>*)c->fgeo, nfg);
     k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad, (int)c->n,
                                                       c->dim);
+    k_incidence_geometry<float><<<nbc, 256, 0, c->stream>>>(
+        (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igA,
+        (R4<float>*)c->igB, (float*)c->igz, c->nbr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

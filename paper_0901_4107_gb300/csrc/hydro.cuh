@@ -65,6 +65,7 @@ __global__ void k_primitives(HydroView<real> v, unsigned long long* bad) {
   const double m = v.Q[i], px = v.Q[v.n + i], py = v.Q[2 * (size_t)v.n + i], pz = v.Q[3 * (size_t)v.n + i];
   const double E = v.Q[4 * (size_t)v.n + i];
   const real P = prims_from_Q(v, i, m, px, py, pz, E);
+  if (v.entropy) v.Aw[i] = (real)(v.S[i] / m);
   if (bad && (!(m > 0.0) || !(P > (real)0))) atomicAdd(bad, 1ull);
 }
 
@@ -98,54 +99,86 @@ __device__ __forceinline__ T group_min(T x) {
   return x;
 }
 
-// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads)
-template <typename real, int G>
+// Mesh velocity of cell i for the Courant step and the cold-flow criterion
+template <typename real>
+__device__ __forceinline__ void mesh_velocity(const HydroView<real>& v, int i, const R4<real>& Wi, real* w) {
+  w[0] = w[1] = w[2] = (real)0;
+  if (v.mode == AMM_LAGRANGIAN) {
+    w[0] = Wi.y; w[1] = Wi.z; w[2] = Wi.w;
+  } else if (v.mode == AMM_EXPLICIT_W) {
+    const R4<real> wm = v.wmesh[i];
+    w[0] = wm.x; w[1] = wm.y; w[2] = wm.z;
+  }
+}
+
+// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads).
+// ENT: the entropy switch is on, so the entropic function A is a sixth
+// limited variable and the largest kinetic energy around the cell is kept
+// for the cold-flow criterion.
+template <typename real, int G, bool ENT = false>
 __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
   constexpr int UNR = 1;                               // incidences in flight per lane
+  constexpr int NV = ENT ? 6 : 5;
   const Tile t = v.ctiles[wi / G];
   const int lane = (int)threadIdx.x % G;
   const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
   const bool valid = i < t.end;
   const int ii = valid ? i : t.begin;
   const R4<real> Wi = v.W[ii];
-  const real phi_i[5] = {Wi.x, Wi.y, Wi.z, Wi.w, v.P[ii]};
+  real phi_i[NV];
+  phi_i[0] = Wi.x; phi_i[1] = Wi.y; phi_i[2] = Wi.z; phi_i[3] = Wi.w; phi_i[4] = v.P[ii];
+  if constexpr (ENT) phi_i[5] = v.Aw[ii];
   const R4<real> cg = v.cgeo[ii];
   const int q0 = valid ? v.csr_off[ii] : 0;
   const int q1 = valid ? v.csr_off[ii + 1] : 0;
-  real g[5][3];
-  real mx[5], mn[5];
+  real g[NV][3];
+  real mx[NV], mn[NV];
 #pragma unroll
-  for (int a = 0; a < 5; a++) {
+  for (int a = 0; a < NV; a++) {
     g[a][0] = g[a][1] = g[a][2] = (real)0;
     mx[a] = mn[a] = phi_i[a];
   }
+  // cold-flow criterion: largest 1/2 m_j |v_j - w_i|^2 over the cell and
+  // its neighbours (start-of-step states)
+  real wi3[3];
+  real ekm = (real)0;
+  const bool cold = ENT && v.alpha_s > 0.0;
+  if (cold) {
+    mesh_velocity(v, ii, Wi, wi3);
+    const real dx = Wi.y - wi3[0], dy = Wi.z - wi3[1], dz = Wi.w - wi3[2];
+    ekm = (real)0.5 * (real)v.Q[ii] * (dx * dx + dy * dy + dz * dz);
+  }
 #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
-    const int2 e = v.csr[q];
-    const int k = e.x >> 1;
-    const real sg = (e.x & 1) ? (real)-1 : (real)1;
-    const R4<real> G0 = v.fgeo[2 * (size_t)k];
-    const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
-    const R4<real> Wj = v.W[e.y];
-    const real phi_j[5] = {Wj.x, Wj.y, Wj.z, Wj.w, v.P[e.y]};
-    // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out)
-    const real a_r = G1.w / G0.w;
-    const real a_h = (real)0.5 * G1.w * sg;
+    // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out),
+    // with the geometric weights of the incidence precomputed (igA, igB)
+    const int j = v.nbr[q];
+    const R4<real> a4 = v.igA[q];
+    const R4<real> b4 = v.igB[q];
+    const R4<real> Wj = v.W[j];
+    real phi_j[NV];
+    phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = v.P[j];
+    if constexpr (ENT) phi_j[5] = v.Aw[j];
+    if (cold) {
+      const real dx = Wj.y - wi3[0], dy = Wj.z - wi3[1], dz = Wj.w - wi3[2];
+      const real ek = (real)0.5 * (real)v.Q[j] * (dx * dx + dy * dy + dz * dz);
+      ekm = ek > ekm ? ek : ekm;
+    }
 #pragma unroll
-    for (int a = 0; a < 5; a++) {
-      const real d = (phi_j[a] - phi_i[a]) * a_r;
-      const real s = (phi_i[a] + phi_j[a]) * a_h;
-      g[a][0] += d * G1.x + s * G0.x;
-      g[a][1] += d * G1.y + s * G0.y;
-      g[a][2] += d * G1.z + s * G0.z;
+    for (int a = 0; a < NV; a++) {
+      const real d = phi_j[a] - phi_i[a];
+      const real s = phi_i[a] + phi_j[a];
+      g[a][0] += d * a4.x + s * a4.w;
+      g[a][1] += d * a4.y + s * b4.x;
+      g[a][2] += d * a4.z + s * b4.y;
       mx[a] = phi_j[a] > mx[a] ? phi_j[a] : mx[a];
       mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
     }
   }
   const real invV = cg.x;
 #pragma unroll
-  for (int a = 0; a < 5; a++) {
+  for (int a = 0; a < NV; a++) {
     g[a][0] = group_sum<G>(g[a][0]) * invV;
     g[a][1] = group_sum<G>(g[a][1]) * invV;
     g[a][2] = group_sum<G>(g[a][2]) * invV;
@@ -153,20 +186,16 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
     mn[a] = group_min<G>(mn[a]);
   }
   if (v.limit) {
-    real alpha[5] = {(real)1, (real)1, (real)1, (real)1, (real)1};
+    real alpha[NV];
+#pragma unroll
+    for (int a = 0; a < NV; a++) alpha[a] = (real)1;
   #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
-      const int2 e = v.csr[q];
-      const int k = e.x >> 1;
-      const real hs = (e.x & 1) ? (real)-0.5 : (real)0.5;
-      const R4<real> G0 = v.fgeo[2 * (size_t)k];
-      const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
-      // f - s_i = (f - r_i) - (s_i - r_i), f - r_i = |r_ij|/2 n_out + c
-      const real fx = hs * G0.w * G0.x + G1.x - cg.y;
-      const real fy = hs * G0.w * G0.y + G1.y - cg.z;
-      const real fz = hs * G0.w * G0.z + G1.z - cg.w;
+      // f - s_i of the incidence
+      const R4<real> b4 = v.igB[q];
+      const real fx = b4.z, fy = b4.w, fz = v.igz[q];
 #pragma unroll
-      for (int a = 0; a < 5; a++) {
+      for (int a = 0; a < NV; a++) {
         const real dphi = g[a][0] * fx + g[a][1] * fy + g[a][2] * fz;
         real psi = (real)1;
         if (dphi > (real)0)
@@ -177,7 +206,7 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
       }
     }
 #pragma unroll
-    for (int a = 0; a < 5; a++) {
+    for (int a = 0; a < NV; a++) {
       const real al = group_min<G>(alpha[a]);
       g[a][0] *= al;
       g[a][1] *= al;
@@ -194,18 +223,24 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
 #pragma unroll
     for (int r = 0; r < 4; r++)
       if (r % G == lane) go[r] = o[r];
+    if constexpr (ENT) {
+      if (lane == 0) {
+        R4<real> ga;
+        ga.x = g[5][0]; ga.y = g[5][1]; ga.z = g[5][2]; ga.w = (real)0;
+        v.gradA[i] = ga;
+      }
+    }
+  }
+  if (cold) {
+    ekm = group_max<G>(ekm);
+    if (valid && lane == 0) v.ekmax[i] = ekm;
   }
   // Courant time R_i / (c_i + |v_i - w_i|), one lane per cell
   real tc = (real)3.0e38;
   if (valid && lane == 0) {
-    real wx = 0, wy = 0, wz = 0;
-    if (v.mode == AMM_LAGRANGIAN) {
-      wx = Wi.y; wy = Wi.z; wz = Wi.w;
-    } else if (v.mode == AMM_EXPLICIT_W) {
-      const R4<real> wm = v.wmesh[i];
-      wx = wm.x; wy = wm.y; wz = wm.z;
-    }
-    const real dx = Wi.y - wx, dy = Wi.z - wy, dz = Wi.w - wz;
+    real w3[3];
+    mesh_velocity(v, i, Wi, w3);
+    const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
     const real cs = xsqrt(v.gas.g * phi_i[4] / Wi.x);
     tc = v.crad[i] / (cs + xsqrt(dx * dx + dy * dy + dz * dz));
   }
@@ -225,9 +260,9 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   __syncthreads();   // `wmin` is reused by the next work item of a persistent CTA
 }
 
-template <typename real, int G>
+template <typename real, int G, bool ENT>
 __global__ void __launch_bounds__(CELL_TILE, sizeof(real) == 4 ? 4 : 2) k_gradients(HydroView<real> v) {
-  grad_item<real, G>(v, blockIdx.x);
+  grad_item<real, G, ENT>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ A5+A6+A7
@@ -235,9 +270,10 @@ struct FaceStats {
   int iters, guard, vacuum, fail, fallback;
 };
 
-template <typename real>
+template <typename real, bool ENT>
 __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real hsgn, const real* n, real sep,
-                                           const real* c, const real* w, real hdt, real* Wp, real* Wpp) {
+                                           const real* c, const real* w, real hdt, real* Wp, real* Wpp,
+                                           real& Aface) {
   const R4<real> Wi = v.W[i];
   const real P = v.P[i];
   const R4<real>* gp = v.grad + 4 * (size_t)i;
@@ -261,6 +297,14 @@ __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real
   Wpp[3] = uz + (g3.x * fx + g3.y * fy + g3.z * fz) - hdt * (ux * g3.x + uy * g3.y + uz * g3.z + g2.w * ir);
   Wpp[4] = P + (g0.w * fx + g1.w * fy + g2.w * fz) -
            hdt * ((real)v.gamma * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
+  if constexpr (ENT) {
+    // entropic function A (Sec. 3.5): reconstructed like the primitives and
+    // advected, dA/dt = -v'.grad A; the cell value if that is not positive
+    const real A = v.Aw[i];
+    const R4<real> ga = v.gradA[i];
+    const real Ap = A + (ga.x * fx + ga.y * fy + ga.z * fz) - hdt * (ux * ga.x + uy * ga.y + uz * ga.z);
+    Aface = Ap > (real)0 ? Ap : A;
+  }
 }
 
 // Per-face state between the extrapolation (face_prepare) and the Riemann
@@ -274,10 +318,11 @@ struct FaceWork {
   real n[3], A, w[3];
   real WppL[5], WppR[5];
   real uL, uR;
+  real AL, AR;                 // entropic function of each side (entropy switch)
   int fallback;
 };
 
-template <typename real>
+template <typename real, bool ENT>
 __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdt, FaceWork<real>& f) {
   f.k = k;
   f.valid = valid;
@@ -308,14 +353,19 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
     for (int d = 0; d < 3; d++) w[d] = (real)0.5 * (wl[d] + wr[d]) + rot * n[d];
   }
   real WpL[5], WpR[5];
-  side_state(v, lr.x, (real)0.5, n, sep, c, w, hdt, WpL, f.WppL);
-  side_state(v, lr.y, (real)-0.5, n, sep, c, w, hdt, WpR, f.WppR);
+  f.AL = f.AR = (real)0;
+  side_state<real, ENT>(v, lr.x, (real)0.5, n, sep, c, w, hdt, WpL, f.WppL, f.AL);
+  side_state<real, ENT>(v, lr.y, (real)-0.5, n, sep, c, w, hdt, WpR, f.WppR, f.AR);
   f.fallback = 0;
   if (!(f.WppL[0] > (real)0) || !(f.WppL[4] > (real)0) || !(f.WppR[0] > (real)0) || !(f.WppR[4] > (real)0)) {
 #pragma unroll
     for (int a = 0; a < 5; a++) {
       f.WppL[a] = WpL[a];
       f.WppR[a] = WpR[a];
+    }
+    if constexpr (ENT) {
+      f.AL = v.Aw[lr.x];
+      f.AR = v.Aw[lr.y];
     }
     f.fallback = 1;
   }
@@ -336,15 +386,15 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
 
 // Riemann solve, flux of the moving face, stores, and the CTA's reductions
 // (largest |A F| per component, Newton statistics).  All B threads call it.
-template <typename real, int B>
+template <typename real, int B, bool ENT>
 __device__ __forceinline__ void face_finish(const HydroView<real>& v, const FaceWork<real>& f, int box, int nf_here,
                                             bool have_guess, real guess) {
   const GasC<real>& G = v.gas;
   const bool valid = f.valid;
-  real rhoF, uF, pF;
+  real rhoF, uF, pF, ps;
   RiemannInfo info;
   const int side = riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.maxit,
-                                  have_guess, guess, rhoF, uF, pF, info);
+                                  have_guess, guess, rhoF, uF, pF, info, ps);
   const real* Wt = side ? f.WppR : f.WppL;
   const real ut = side ? f.uR : f.uL;
   real vlab[3];
@@ -364,28 +414,51 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
     v.flux[f.k] = fout;
     v.fluxE[f.k] = fE;
   }
+  real fS = (real)0;
+  if constexpr (ENT) {
+    // Sec. 3.5: entropy flux rho_F u_F A_U (A_U of the upwind side by the
+    // sign of u_F) and the largest Mach number of the problem's shocks (the
+    // waves with p* above the pressure ahead of them)
+    fS = A * (rhoF * uF) * (uF > (real)0 ? f.AL : f.AR);
+    real mach = (real)1;
+    if (!info.vacuum) {
+      if (ps > f.WppL[4]) mach = xsqrt((real)1 + G.shock_a * (ps / f.WppL[4] - (real)1));
+      if (ps > f.WppR[4]) {
+        const real mr = xsqrt((real)1 + G.shock_a * (ps / f.WppR[4] - (real)1));
+        mach = mr > mach ? mr : mach;
+      }
+    }
+    if (valid) {
+      v.fluxS[f.k] = fS;
+      v.machf[f.k] = mach;
+    }
+  }
   if (sizeof(real) == 4 && v.fixed_acc) {
     // largest |A F| per component for the exact fixed-point sums (float bits
     // of non-negative values order like the values)
-    unsigned m[5] = {0u, 0u, 0u, 0u, 0u};
+    constexpr int NM = ENT ? 6 : 5;
+    unsigned m[NM];
+#pragma unroll
+    for (int a = 0; a < NM; a++) m[a] = 0u;
     if (valid) {
       m[0] = __float_as_uint(fabsf((float)fout.x));
       m[1] = __float_as_uint(fabsf((float)fout.y));
       m[2] = __float_as_uint(fabsf((float)fout.z));
       m[3] = __float_as_uint(fabsf((float)fout.w));
       m[4] = __float_as_uint(fabsf((float)fE));
+      if constexpr (ENT) m[NM - 1] = __float_as_uint(fabsf((float)fS));
     }
-    __shared__ unsigned wm[B / 32][5];
+    __shared__ unsigned wm[B / 32][NM];
 #pragma unroll
-    for (int a = 0; a < 5; a++) {
+    for (int a = 0; a < NM; a++) {
       const unsigned r = __reduce_max_sync(0xffffffffu, m[a]);
       if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5][a] = r;
     }
     __syncthreads();
-    if (threadIdx.x < 5) {
+    if (threadIdx.x < NM) {
       unsigned r = 0u;
       for (int w = 0; w < B / 32; w++) r = wm[w][threadIdx.x] > r ? wm[w][threadIdx.x] : r;
-      atomicMax(v.fmax_bits + 5 * box + threadIdx.x, r);
+      atomicMax(v.fmax_bits + FMAX_STRIDE * box + threadIdx.x, r);
     }
   }
   // statistics: warp reductions (no contended shared-memory atomics), one
@@ -439,7 +512,7 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
 }
 
 // B threads (faces) per CTA; a tile of FACE_TILE faces spans FACE_TILE/B CTAs
-template <typename real, int B>
+template <typename real, int B, bool ENT>
 __device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
   constexpr int SUB = FACE_TILE / B;
   const Tile t = v.ftiles[wi / SUB];
@@ -450,13 +523,13 @@ __device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
   if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
   __syncthreads();
   FaceWork<real> f;
-  face_prepare(v, valid ? k0 : t.begin, valid, s_hdt, f);
-  face_finish<real, B>(v, f, t.box, min(B, t.end - first), false, (real)0);
+  face_prepare<real, ENT>(v, valid ? k0 : t.begin, valid, s_hdt, f);
+  face_finish<real, B, ENT>(v, f, t.box, min(B, t.end - first), false, (real)0);
 }
 
-template <typename real, int B>
+template <typename real, int B, bool ENT>
 __global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
-  flux_item<real, B>(v, blockIdx.x);
+  flux_item<real, B, ENT>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ A8+A1+A9
@@ -490,12 +563,26 @@ __device__ __forceinline__ double fixed_scale(int eb, int headroom) {
   return __longlong_as_double((long long)(1023 + eb - 188 + headroom) << 52);
 }
 
+// rho^gamma in the bulk precision (the FP32 forms' entropy switch takes it
+// in FP32, like the rest of their bulk arithmetic)
+template <typename real>
+__device__ __forceinline__ double rho_pow_gamma(const HydroView<real>& v, double rho) {
+  if constexpr (sizeof(real) == 8) {
+    return pow(rho, v.gamma);
+  } else {
+    return (double)xpow((float)rho, v.gas.g);
+  }
+}
+
 // G consecutive lanes share a cell (as in the gradient kernel); lane l sums
 // the cell's incidences l, l+G, ...; the lane partial sums are combined with
-// shuffles and lane 0 applies the update.
-template <typename real, int G>
+// shuffles and lane 0 applies the update.  ENT: the entropy switch of
+// Sec. 3.5 (a sixth flux component, the entropy, and the per-cell choice
+// between the advected entropy and the energy update).
+template <typename real, int G, bool ENT = false>
 __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   constexpr int CELLS = CELL_TILE / G;
+  constexpr int NA = ENT ? 6 : 5;
   const Tile t = v.ctiles[wi / G];
   const int lane = (int)threadIdx.x % G;
   const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
@@ -504,7 +591,8 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   const int q1 = valid ? v.csr_off[i + 1] : 0;
   const size_t n = (size_t)v.n;
   double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  double d[5];
+  double d[NA];
+  real mach = (real)1;
   bool bad = false;
   if (sizeof(real) == 4 && v.fixed_acc) {
     // Exact sums: every face flux is converted once to an int64 multiple of
@@ -513,56 +601,99 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     // with opposite signs, so the update conserves exactly and does not
     // depend on the summation order.  One rounding per cell remains, when
     // the integer total is scaled back to FP64.
-    int eb[5];
+    int eb[NA];
 #pragma unroll
-    for (int a = 0; a < 5; a++) eb[a] = (int)((v.fmax_bits[5 * t.box + a] >> 23) & 0xffu);
-    long long acc[5] = {0, 0, 0, 0, 0};
+    for (int a = 0; a < NA; a++) eb[a] = (int)((v.fmax_bits[FMAX_STRIDE * t.box + a] >> 23) & 0xffu);
+    long long acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; a++) acc[a] = 0;
 #pragma unroll 4
     for (int e = q0 + lane; e < q1; e += G) {
       const int2 r = v.csr[e];
       const int k = r.x >> 1;
       const R4<real> f = v.flux[k];
-      const float fv[5] = {(float)f.x, (float)f.y, (float)f.z, (float)f.w, (float)v.fluxE[k]};
+      float fv[NA];
+      fv[0] = (float)f.x; fv[1] = (float)f.y; fv[2] = (float)f.z; fv[3] = (float)f.w; fv[4] = (float)v.fluxE[k];
+      if constexpr (ENT) {
+        fv[5] = (float)v.fluxS[k];
+        const real mf = v.machf[k];
+        mach = mf > mach ? mf : mach;
+      }
 #pragma unroll
-      for (int a = 0; a < 5; a++) {
+      for (int a = 0; a < NA; a++) {
         const long long x = to_fixed(fv[a], eb[a], v.headroom, bad);
         acc[a] += (r.x & 1) ? -x : x;
       }
     }
 #pragma unroll
-    for (int a = 0; a < 5; a++) acc[a] = group_sum<G>(acc[a]);
+    for (int a = 0; a < NA; a++) acc[a] = group_sum<G>(acc[a]);
     bad = group_max<G>((int)bad) != 0;
     if (lane == 0) {
 #pragma unroll
-      for (int a = 0; a < 5; a++) d[a] = __ll2double_rn(acc[a]) * fixed_scale(eb[a], v.headroom);
+      for (int a = 0; a < NA; a++) d[a] = __ll2double_rn(acc[a]) * fixed_scale(eb[a], v.headroom);
     }
   } else {
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; a++) acc[a] = 0.0;
 #pragma unroll 4
     for (int e = q0 + lane; e < q1; e += G) {
       const int2 r = v.csr[e];
       const int k = r.x >> 1;
       const R4<real> f = v.flux[k];
-      const double fe = (double)v.fluxE[k];
-      if (r.x & 1) {
-        acc[0] -= (double)f.x; acc[1] -= (double)f.y; acc[2] -= (double)f.z; acc[3] -= (double)f.w;
-        acc[4] -= fe;
-      } else {
-        acc[0] += (double)f.x; acc[1] += (double)f.y; acc[2] += (double)f.z; acc[3] += (double)f.w;
-        acc[4] += fe;
+      double fv[NA];
+      fv[0] = (double)f.x; fv[1] = (double)f.y; fv[2] = (double)f.z; fv[3] = (double)f.w;
+      fv[4] = (double)v.fluxE[k];
+      if constexpr (ENT) {
+        fv[5] = (double)v.fluxS[k];
+        const real mf = v.machf[k];
+        mach = mf > mach ? mf : mach;
+      }
+#pragma unroll
+      for (int a = 0; a < NA; a++) {
+        if (r.x & 1)
+          acc[a] -= fv[a];
+        else
+          acc[a] += fv[a];
       }
     }
 #pragma unroll
-    for (int a = 0; a < 5; a++) d[a] = group_sum<G>(acc[a]);
+    for (int a = 0; a < NA; a++) d[a] = group_sum<G>(acc[a]);
   }
-  unsigned nonpos = 0;
+  if constexpr (ENT) mach = group_max<G>(mach);
+  unsigned nonpos = 0, keep = 0;
   if (valid && lane == 0) {
     const double dt = box_dt(v, t.box);
 #pragma unroll
-    for (int a = 0; a < 5; a++) {
-      q[a] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v.Q[a * n + i] - dt * d[a];
-      v.Q[a * n + i] = q[a];
+    for (int a = 0; a < 5; a++) q[a] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v.Q[a * n + i] - dt * d[a];
+    if constexpr (ENT) {
+      // Sec. 3.5: keep the advected entropy where no shock above the
+      // threshold Mach number touches the cell, or where the new thermal
+      // energy is below alpha_s times the largest kinetic energy around it;
+      // then P = (S/M) rho^gamma sets the thermal energy.  Otherwise the
+      // energy update stands and S is re-initialised from it.
+      const double Sadv = v.S[i] - dt * d[5];
+      const double m = q[0];
+      const double V = v.cgeo64[i].x;
+      const double rho = m / V;
+      const double kin = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / m;
+      keep = ((double)mach < v.mach_thresh) ? 1u : 0u;
+      if (!keep && v.alpha_s > 0.0) keep = (q[4] - kin < v.alpha_s * (double)v.ekmax[i]) ? 1u : 0u;
+      double Snew;
+      if (keep) {
+        const double Pk = (Sadv / m) * rho_pow_gamma(v, rho);
+        q[4] = kin + Pk * V / (v.gamma - 1.0);
+        Snew = Sadv;
+      } else {
+        const double Pe = (v.gamma - 1.0) * (q[4] - kin) / V;
+        Snew = m * Pe / rho_pow_gamma(v, rho);
+      }
+      v.S[i] = Snew;
+      v.kept[i] = (unsigned char)keep;
+      v.Aw[i] = (real)(Snew / m);
     }
+#pragma unroll
+    for (int a = 0; a < 5; a++) v.Q[a * n + i] = q[a];
     const real P = prims_from_Q(v, i, q[0], q[1], q[2], q[3], q[4]);
     nonpos = (!(q[0] > 0.0) || !(P > (real)0)) ? 1u : 0u;
   }
@@ -577,6 +708,10 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][a] = s;
   }
   const unsigned nbad = __syncthreads_count(nonpos);
+  if constexpr (ENT) {
+    const unsigned nkeep = __syncthreads_count(keep);
+    if (threadIdx.x == 0 && nkeep) atomicAdd(&v.stats->kept, (unsigned long long)nkeep);
+  }
   if (threadIdx.x < 5) {
     double s = red[0][threadIdx.x];
     for (int w = 1; w < CELL_TILE / 32; w++) s += red[w][threadIdx.x];
@@ -590,9 +725,9 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   __syncthreads();   // `red` is reused by the next work item of a persistent CTA
 }
 
-template <typename real, int G>
+template <typename real, int G, bool ENT>
 __global__ void __launch_bounds__(CELL_TILE) k_update(HydroView<real> v) {
-  update_item<real, G>(v, blockIdx.x);
+  update_item<real, G, ENT>(v, blockIdx.x);
 }
 
 // per-tile sums of the current Q (used when no step has produced them)
@@ -669,6 +804,16 @@ __global__ void k_set_state(HydroView<real> v, const double* Qa, int dim, unsign
   v.Q[3 * n + i] = pz;
   v.Q[4 * n + i] = E;
   const real P = prims_from_Q(v, i, m, px, py, pz, E);
+  if (v.entropy) {
+    // S = M P / rho^gamma from the new state, in FP64
+    const double V = v.cgeo64[i].x;
+    const double rho = m / V;
+    const double P64 = (v.gamma - 1.0) * (E - 0.5 * (px * px + py * py + pz * pz) / m) / V;
+    const double S = m * P64 / pow(rho, v.gamma);
+    v.S[i] = S;
+    v.Aw[i] = (real)(S / m);
+    v.kept[i] = 0;
+  }
   if (!(m > 0.0) || !(P > (real)0)) atomicAdd(bad, 1ull);
 }
 
@@ -785,6 +930,10 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.fluxE = (real*)c->fluxE;
   v.csr_off = c->csr_off;
   v.csr = c->csr;
+  v.igA = (const R4<real>*)c->igA;
+  v.igB = (const R4<real>*)c->igB;
+  v.igz = (const real*)c->igz;
+  v.nbr = c->nbr;
   v.ctiles = c->ctiles;
   v.ftiles = c->ftiles;
   v.cell_perm = c->cell_perm;
@@ -794,6 +943,16 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.box_first_ctile = c->box_first_ctile;
   v.stats = c->stats;
   v.box_status = c->box_status;
+  v.entropy = c->opt.entropy;
+  v.mach_thresh = c->opt.mach_thresh;
+  v.alpha_s = c->opt.alpha_s;
+  v.S = c->S;
+  v.Aw = (real*)c->Aw;
+  v.gradA = (R4<real>*)c->gradA;
+  v.fluxS = (real*)c->fluxS;
+  v.machf = (real*)c->machf;
+  v.ekmax = (real*)c->ekmax;
+  v.kept = c->kept;
   v.mlp = c->mlp;
   v.harvest = c->harvest;
   return v;
@@ -813,13 +972,22 @@ cudaError_t launch_gradients(amm_ctx* c) {
   auto v = make_view<real>(c, 0.0);
   cudaError_t e = cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * 5 * c->nboxes, c->stream);
+  e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * FMAX_STRIDE * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
-  switch (c->grad_lanes) {
-    case 1: k_gradients<real, 1><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
-    case 2: k_gradients<real, 2><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
-    case 8: k_gradients<real, 8><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
-    default: k_gradients<real, 4><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+  if (c->opt.entropy) {
+    switch (c->grad_lanes) {
+      case 1: k_gradients<real, 1, true><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+      case 2: k_gradients<real, 2, true><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+      case 8: k_gradients<real, 8, true><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+      default: k_gradients<real, 4, true><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+    }
+  } else {
+    switch (c->grad_lanes) {
+      case 1: k_gradients<real, 1, false><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+      case 2: k_gradients<real, 2, false><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+      case 8: k_gradients<real, 8, false><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+      default: k_gradients<real, 4, false><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+    }
   }
   return cudaGetLastError();
 }
@@ -835,10 +1003,15 @@ cudaError_t launch_flux(amm_ctx* c, double cfl) {
       return cudaErrorInvalidValue;
     }
   } else {
-    if (b128)
-      k_flux<real, 128><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+    const bool ent = c->opt.entropy != 0;
+    if (b128 && ent)
+      k_flux<real, 128, true><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+    else if (b128)
+      k_flux<real, 128, false><<<c->n_ftiles * 2, 128, 0, c->stream>>>(v);
+    else if (ent)
+      k_flux<real, 256, true><<<c->n_ftiles, 256, 0, c->stream>>>(v);
     else
-      k_flux<real, 256><<<c->n_ftiles, 256, 0, c->stream>>>(v);
+      k_flux<real, 256, false><<<c->n_ftiles, 256, 0, c->stream>>>(v);
   }
   return cudaGetLastError();
 }
@@ -846,11 +1019,20 @@ cudaError_t launch_flux(amm_ctx* c, double cfl) {
 template <typename real>
 cudaError_t launch_update(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
-  switch (c->update_lanes) {
-    case 1: k_update<real, 1><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
-    case 2: k_update<real, 2><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
-    case 8: k_update<real, 8><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
-    default: k_update<real, 4><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+  if (c->opt.entropy) {
+    switch (c->update_lanes) {
+      case 1: k_update<real, 1, true><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+      case 2: k_update<real, 2, true><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+      case 8: k_update<real, 8, true><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+      default: k_update<real, 4, true><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+    }
+  } else {
+    switch (c->update_lanes) {
+      case 1: k_update<real, 1, false><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v); break;
+      case 2: k_update<real, 2, false><<<c->n_ctiles * 2, CELL_TILE, 0, c->stream>>>(v); break;
+      case 8: k_update<real, 8, false><<<c->n_ctiles * 8, CELL_TILE, 0, c->stream>>>(v); break;
+      default: k_update<real, 4, false><<<c->n_ctiles * 4, CELL_TILE, 0, c->stream>>>(v); break;
+    }
   }
   return cudaGetLastError();
 }

@@ -46,14 +46,14 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, volatile unsigned*
   __syncthreads();
 }
 
-template <typename real, int GG>
+template <typename real, int GG, bool ENT>
 __global__ void __launch_bounds__(CELL_TILE) k_step_persistent(HydroView<real> v, unsigned* bar) {
   const int n_grad = v.n_ctiles * GG;
-  for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<real, GG>(v, wi);
+  for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<real, GG, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
-  for (int wi = blockIdx.x; wi < v.n_ftiles; wi += gridDim.x) flux_item<real, FACE_TILE>(v, wi);
+  for (int wi = blockIdx.x; wi < v.n_ftiles; wi += gridDim.x) flux_item<real, FACE_TILE, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
-  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) update_item<real, 1>(v, wi);
+  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) update_item<real, 1, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
   for (int b = blockIdx.x; b < v.nboxes; b += gridDim.x) finish_item<real, CELL_TILE>(v, b, 1);
 }
@@ -63,9 +63,9 @@ cudaError_t launch_step_persistent(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
   v.update_lanes = 1;
   cudaError_t e = cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * 5 * c->nboxes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * FMAX_STRIDE * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
-  auto kern = k_step_persistent<real, 4>;
+  auto kern = c->opt.entropy ? k_step_persistent<real, 4, true> : k_step_persistent<real, 4, false>;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

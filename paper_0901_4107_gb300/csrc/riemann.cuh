@@ -185,11 +185,14 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
 
 // Sampled state at x/t = 0 of the Riemann problem (rho, u, p per side).
 // Returns side of the contact (0: left, 1: right) for the transverse
-// velocity; rho = P = 0 inside generated vacuum.
+// velocity; rho = P = 0 inside generated vacuum.  pstar: the star pressure
+// (0 when vacuum is generated).
 template <typename real>
 __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real rhoR, real uR, real pR,
                                               const GasC<real>& G, double tol, int maxit, bool have_guess,
-                                              real guess, real& rhoF, real& uF, real& pF, RiemannInfo& info) {
+                                              real guess, real& rhoF, real& uF, real& pF, RiemannInfo& info,
+                                              real& pstar) {
+  pstar = (real)0;
   info.iters = 0;
   info.guard = 0;
   info.vacuum = 0;
@@ -230,6 +233,7 @@ __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real 
   const real p0 = standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, have_guess, guess);
   NewtonTail<real> nt;
   const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, maxit, info, nt);
+  pstar = ps;
   const real us = (real)0.5 * (uL + uR) + (real)0.5 * ((nt.fR - nt.fL) + (nt.dR - nt.dL) * nt.dp);
   if ((real)0 <= us) {
     const real r = ps / pL;

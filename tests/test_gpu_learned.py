@@ -93,3 +93,47 @@ def test_trained_proposal_saves_newton_iterations(env, trained):
         s = amm.amm_get_stats(ctx)
         iters[prec] = s["newton_iters"] / s["faces"]
     assert iters["fp32_learned"] < iters["fp32"], iters
+
+
+def test_persistent_learned_ensemble_matches_kernel_sequence(env, trained):
+    """The learned form of the batched ensemble: one cooperative launch per
+    step (two tensor-core MMA groups per CTA) gives bit-identical states to
+    the per-phase launches, with and without graph capture, and each box's
+    first step keeps the FP32 parity bar against the oracle."""
+    torch, amm, learned = env
+    net, _ = trained
+    sizes, machs = (5, 9, 6, 11, 7, 8), (0.5, 2.0, 1.0, 2.0, 1.2, 1.5)
+    E = ics.concat([ics.turbulent_3d(n, seed=20 + k, mach=m) for k, (n, m) in enumerate(zip(sizes, machs))])
+
+    def create():
+        opt = amm.amm_default_options("fp32_learned", "lagrangian")
+        ctx = amm.amm_create(3, E.points, E.cells, E.shift, E.area, E.centroid, E.box, E.Q, E.gamma, opt,
+                             box_cells=E.box_cells, box_faces=E.box_faces)
+        amm.amm_mlp_attach(ctx, net)
+        return ctx
+
+    outs, stats = [], []
+    for persistent, graph in ((0, False), (1, False), (1, True)):
+        ctx = create()
+        amm.amm_set_tuning(ctx, 4, 1, 256, persistent)
+        amm.amm_advance(ctx, 0.3, 3, use_graph=graph)
+        amm.amm_sync(ctx)
+        outs.append(amm.amm_get_state(ctx))
+        stats.append(amm.amm_get_stats(ctx))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+    assert stats[0]["newton_iters"] == stats[1]["newton_iters"] == stats[2]["newton_iters"]
+    assert stats[1]["faces"] == 3 * E.n_faces
+    ctx = create()
+    amm.amm_set_tuning(ctx, 4, 1, 256, 1)
+    amm.amm_advance(ctx, 0.3, 1, use_graph=True)
+    out = amm.amm_get_state(ctx)
+    for b, P in enumerate(E.problems):
+        M = O.Mesh(P.tess)
+        Q = P.conserved()
+        ref, _, _, rc = O.step(M, Q, P.gamma, "lagrangian", cfl=0.3)
+        assert rc == 0
+        W = O.primitives(M, Q, P.tess.volume, P.gamma)
+        s = slice(E.box_cells[b], E.box_cells[b + 1])
+        e = np.max(np.abs(out[s] - ref) / np.maximum(np.abs(ref), floor_of(Q, W, P.gamma)))
+        assert e < 2e-5, (b, e)
