@@ -423,8 +423,7 @@ def newton_stats(amm, ctx, Q0, steps=1):
     amm.amm_advance(ctx, CFL, steps, False)
     s = amm.amm_get_stats(ctx)
     return {"newton_iters_per_face": s["newton_iters"] / max(1, s["faces"]), "newton_hist": s["newton_hist"][:8],
-            "fallback_faces": s["fallback_faces"] if "fallback_faces" in s else s.get("fallback"),
-            "vacuum_faces": s.get("vacuum"), "guard_faces": s.get("guard")}
+            "fallback_faces": s["fallback_faces"], "vacuum_faces": s["vacuum_faces"], "guard_faces": s["guard_faces"]}
 
 
 def e2e_rate(g, ctx, Q0, steps):
@@ -444,6 +443,49 @@ def e2e_rate(g, ctx, Q0, steps):
         amm.amm_advance(ctx, CFL, 1, True)
         amm.amm_get_state(ctx, Qo.numpy())
     return (time.perf_counter() - t0) / steps, Q0.nbytes
+
+
+# algorithmic FLOPs per sample of one training step of the 6-64-64-1
+# proposal network: forward 2(6*64 + 64*64 + 64), backward the three
+# transposed products (dH1, dW2, dW1) plus the output layer
+MLP_FLOP_FWD = 2 * (6 * 64 + 64 * 64 + 64)
+MLP_FLOP_STEP = MLP_FLOP_FWD + 2 * (64 * 64 + 64 * 64 + 6 * 64 + 64)
+
+
+def bench_training(g, P, motion, samples=1 << 20, reps=20):
+    """Device time of one training step (tcgen05 forward + backward over a
+    batch, gradient reduction, Adam) on `samples` harvested face states."""
+    from paper_0901_4107_gb300 import learned
+    amm, torch = g.amm, g.torch
+    st = learned.harvest(P.tess, P.conserved(), P.gamma, motion, 1, torch=torch)
+    x, t = learned.dataset(st, P.gamma, torch)
+    n = min(samples, x.shape[0])
+    idx = torch.arange(n, dtype=torch.int32, device="cuda")
+    net = amm.amm_mlp_create(P.gamma, g.stream.cuda_stream)
+    amm.amm_mlp_set_params(net, learned.init_params(7))
+    for _ in range(3):
+        amm.amm_mlp_train_step(net, x.data_ptr(), t.data_ptr(), idx.data_ptr(), n, 1e-4)
+    amm.amm_mlp_sync(net)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(g.stream):
+        e0.record(g.stream)
+    for _ in range(reps):
+        amm.amm_mlp_train_step(net, x.data_ptr(), t.data_ptr(), idx.data_ptr(), n, 1e-4)
+    with torch.cuda.stream(g.stream):
+        e1.record(g.stream)
+    amm.amm_mlp_sync(net)
+    ms = e0.elapsed_time(e1) / reps
+    bf16 = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    tflops = MLP_FLOP_STEP * n / (ms * 1e-3) / 1e12
+    return {"samples": n, "ms_per_step": ms, "samples_per_s": n / (ms * 1e-3),
+            "algorithmic_flop_per_sample": MLP_FLOP_STEP, "achieved_tflops": tflops,
+            "peak_tflops": bf16, "frac": (tflops / bf16) if bf16 else None,
+            "peak_source": "measured bf16_tflops (burst)"}
 
 
 def bench_box(args, g, world, rank, local):
@@ -569,6 +611,8 @@ def bench_box(args, g, world, rank, local):
     if "fp64" in forms:
         for prec in forms:
             forms[prec]["vs_fp64"] = forms[prec]["value"] / forms["fp64"]["value"]
+    if wl == "turbulent64":
+        line["proposal_training"] = bench_training(g, P, motion)
     ke = max(3, min(args.steps, 200))
     e2e_s, nbytes = e2e_rate(g, ctxs[head], Q0, ke)
     line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
@@ -726,6 +770,7 @@ def bench_ensemble(args, g, world, rank, local):
         t_cpu, faces_cpu, worst = 0.0, 0, {p: 0.0 for p in ctxs}
         outs, kept, flips = {}, {}, {p: 0 for p in ctxs}
         for prec, ctx in ctxs.items():
+            amm.amm_reset_stats(ctx)
             amm.amm_set_state(ctx, E.Q)
             amm.amm_advance(ctx, CFL, 1, False)
             outs[prec] = amm.amm_get_state(ctx)
