@@ -689,6 +689,7 @@ def bench_ensemble(args, g, world, rank, local):
     clocks = sampler.stop()
     status = amm.amm_get_box_status(ctxs[head])
     stats = amm.amm_get_stats(ctxs[head])
+    head_final, head_failures = state_and_failures(amm, ctxs[head])
     _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
     step_ms = statistics.mean(ms)
     faces_all = float(nf)
@@ -730,8 +731,8 @@ def bench_ensemble(args, g, world, rank, local):
         return line
     forms = {head: {"value": value, "ms_per_step": step_ms, "newton_iters_per_face": line["newton_iters_per_face"],
                     "training": g.train_stats}}
-    finals = {}
-    finals[head], forms[head]["failures"] = state_and_failures(amm, ctxs[head])
+    finals = {head: head_final}
+    forms[head]["failures"] = head_failures
     for prec in ("fp32", "fp64"):
         ctxs[prec] = make(prec)
         tp = g.tune(ctxs[prec], args.tuning, 2)

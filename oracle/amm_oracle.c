@@ -17,6 +17,7 @@
  * cell's frame.  Per-cell arrays: Q = (m, p_1..p_D, E), W = (rho, v_1..v_D, P),
  * gradients grad[i][var][axis] with var over the D+2 primitives.
  */
+#include <float.h>
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -396,7 +397,8 @@ double ora_timestep(int dim, long n, const double* W, const double* V, const dou
  *          = 2 c_K/(gamma-1) ((p/p_K)^((gamma-1)/(2gamma)) - 1)   (rarefaction)
  *   A_K = 2/((gamma+1) rho_K), B_K = (gamma-1)/(gamma+1) p_K,
  * found by Newton from the adaptive primitive-variable / two-rarefaction /
- * two-shock guess, to the relative change 2|dp|/(p_new+p_old) < tol; then
+ * two-shock guess, to the relative change 2|dp|/(p_new+p_old) < tol (or to a
+ * residual f(p) at the rounding level of its terms); then
  * u* = (u_L+u_R)/2 + (f_R(p*) - f_L(p*))/2 and the self-similar solution is
  * sampled at x/t = 0.  Vacuum: a vacuum side, or vacuum generated between two
  * rarefactions when 2(c_L+c_R)/(gamma-1) <= u_R - u_L; the sampled state in
@@ -528,12 +530,20 @@ int ora_riemann(double g, const double* WL, const double* WR, double tol, int ma
     const double pfloor = 1e-10 * 0.5 * (pL + pR);
     if (!(p0 > pfloor)) p0 = pfloor;
   }
-  /* Newton iteration on f(p) = 0 */
+  /* Newton iteration on f(p) = 0; it also stops when f(p) vanishes to
+   * rounding (|f| within 8 ulps of the size of its terms): p is then the root
+   * in working precision.  Near vacuum f is a small difference of large terms
+   * and the relative change of p cannot fall below tol. */
   double p = p0;
   int it = 0, conv = 0;
   while (it < maxit) {
     double dL, dR;
-    const double f = pfun(p, rhoL, pL, cL, g, &dL) + pfun(p, rhoR, pR, cR, g, &dR) + du;
+    const double fLp = pfun(p, rhoL, pL, cL, g, &dL), fRp = pfun(p, rhoR, pR, cR, g, &dR);
+    const double f = fLp + fRp + du;
+    if (fabs(f) <= 8.0 * DBL_EPSILON * (fabs(fLp) + fabs(fRp) + fabs(du))) {
+      conv = 1;
+      break;
+    }
     double pn = p - f / (dL + dR);
     if (!(pn > 0.0)) pn = 1e-3 * p;
     it++;

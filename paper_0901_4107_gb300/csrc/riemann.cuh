@@ -23,6 +23,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <float.h>
 
 #include "amm_internal.cuh"
 
@@ -104,6 +105,12 @@ struct NewtonTail {
   real fL, dL, fR, dR, dp;
 };
 
+// The FP64 Newton loops also stop when f(p) vanishes to rounding (|f| within
+// RESIDUAL_ULPS ulps of the size of its terms): p is then the root in working
+// precision.  Near vacuum f is a small difference of large terms and the
+// relative change of p cannot fall below a 1e-12 tolerance.
+constexpr double RESIDUAL_ULPS = 8.0;
+
 // Newton iteration for p*; returns p* in `real`, with the FP64 guard in the
 // FP32 form.  iterations counted in info.
 template <typename real>
@@ -118,7 +125,13 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
       real fL, dL, fR, dR;
       wave_curve(p, rhoL, pL, cL, G, fL, dL);
       wave_curve(p, rhoR, pR, cR, G, fR, dR);
-      real pn = p - (fL + fR + du) / (dL + dR);
+      const real f = fL + fR + du;
+      if (fabs(f) <= RESIDUAL_ULPS * DBL_EPSILON * (fabs(fL) + fabs(fR) + fabs(du))) {
+        tail.fL = fL; tail.dL = dL; tail.fR = fR; tail.dR = dR; tail.dp = (real)0;
+        conv = true;
+        break;
+      }
+      real pn = p - f / (dL + dR);
       if (!(pn > (real)0)) pn = (real)1e-3 * p;
       it++;
       const real ch = (real)2 * fabs(pn - p) / (pn + p);
@@ -164,7 +177,13 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
         double fL, dL, fR, dR;
         wave_curve(pd, rL, pLd, cLd, G64, fL, dL);
         wave_curve(pd, rR, pRd, cRd, G64, fR, dR);
-        double pn = pd - (fL + fR + dud) / (dL + dR);
+        const double f = fL + fR + dud;
+        if (fabs(f) <= RESIDUAL_ULPS * DBL_EPSILON * (fabs(fL) + fabs(fR) + fabs(dud))) {
+          tail.fL = (real)fL; tail.dL = (real)dL; tail.fR = (real)fR; tail.dR = (real)dR; tail.dp = (real)0;
+          conv = true;
+          break;
+        }
+        double pn = pd - f / (dL + dR);
         if (!(pn > 0.0)) pn = 1e-3 * pd;
         it++;
         const double ch = 2.0 * fabs(pn - pd) / (pn + pd);

@@ -287,6 +287,45 @@ def test_riemann_newton_matches_bisection():
     assert it.max() <= 12
 
 
+def test_riemann_converges_next_to_vacuum():
+    """Strong rarefactions just short of vacuum generation, with widely
+    different states on the two sides: f(p) near p* is a small difference of
+    large terms, so the relative change of a Newton step stays above 1e-12;
+    the iteration still ends (its residual reaches rounding) and p* is the
+    root found by bisection in log p, to the accuracy its conditioning
+    allows."""
+    gam = 5.0 / 3.0
+    rng = np.random.default_rng(17)
+    m = 4000
+    rL, rR = np.exp(rng.uniform(-25, 5, m)), np.exp(rng.uniform(-25, 5, m))
+    pL, pR = np.exp(rng.uniform(-30, 5, m)), np.exp(rng.uniform(-30, 5, m))
+    cL, cR = np.sqrt(gam * pL / rL), np.sqrt(gam * pR / rR)
+    du = rng.uniform(0.99, 0.99995, m) * 2 * (cL + cR) / (gam - 1)
+    WL = np.stack([rL, -0.5 * du, pL], 1)
+    WR = np.stack([rR, 0.5 * du, pR], 1)
+    out, it, bad = O.riemann(gam, WL, WR, tol=1e-12, maxit=64)
+    assert bad == 0 and np.asarray(it).max() < 64
+
+    def mismatch(p):
+        f = np.zeros(m)
+        for W in (WL, WR):
+            rho, u, pk = W.T
+            c = np.sqrt(gam * pk / rho)
+            f += np.where(p > pk, (p - pk) * np.sqrt(2 / ((gam + 1) * rho) / (p + (gam - 1) / (gam + 1) * pk)),
+                          2 * c / (gam - 1) * ((p / pk) ** ((gam - 1) / (2 * gam)) - 1))
+        return f + du
+
+    lo, hi = np.full(m, 1e-300), np.full(m, 1e6)
+    for _ in range(1100):
+        mid = np.sqrt(lo * hi)
+        neg = mismatch(mid) < 0                 # f increases with p
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+    pb = np.sqrt(lo * hi)
+    assert np.median(np.abs(out[:, 3] / pb - 1)) < 1e-9
+    assert np.max(np.abs(out[:, 3] / pb - 1)) < 1e-4
+
+
 def test_riemann_vacuum_cases():
     """Vacuum: left vacuum, right vacuum, and vacuum generated between two
     rarefactions; x/t=0 in vacuum gives rho = P = 0 and zero flux."""
