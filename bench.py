@@ -458,7 +458,7 @@ def bench_training(g, P, motion, samples=1 << 20, reps=20):
     from paper_0901_4107_gb300 import learned
     amm, torch = g.amm, g.torch
     st = learned.harvest(P.tess, P.conserved(), P.gamma, motion, 1, torch=torch)
-    x, t = learned.dataset(st, P.gamma, torch)
+    x, t = learned.dataset(st, P.gamma, torch, gate=-1.0)      # every face: throughput only
     n = min(samples, x.shape[0])
     idx = torch.arange(n, dtype=torch.int32, device="cuda")
     net = amm.amm_mlp_create(P.gamma, g.stream.cuda_stream)
@@ -690,6 +690,16 @@ def bench_ensemble(args, g, world, rank, local):
     status = amm.amm_get_box_status(ctxs[head])
     stats = amm.amm_get_stats(ctxs[head])
     head_final, head_failures = state_and_failures(amm, ctxs[head])
+    # both step modes of the same shapes: one cooperative launch per step,
+    # and the four-kernel sequence (the autotuner keeps the faster)
+    modes = {}
+    for pm in (0, 1):
+        amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], pm)
+        msm, _ = run(ctxs[head], min(args.steps, 20), 2, False)
+        modes["persistent" if pm else "kernel_sequence"] = {"ms_per_step": statistics.mean(msm),
+                                                            "value": nf / (statistics.mean(msm) * 1e-3)}
+    amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"],
+                       tuning["persistent"])
     _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
     step_ms = statistics.mean(ms)
     faces_all = float(nf)
@@ -724,6 +734,7 @@ def bench_ensemble(args, g, world, rank, local):
         "gpu_launches": (1 if tuning["persistent"] else 4) * args.steps,
         "clocks": clocks,
         "boxes_flagged": int((np.asarray(status) != 0).sum()),
+        "step_modes": modes,
         "entropy_kept_per_cell_update": stats["entropy_kept"] / float(n * args.steps),
         "newton_iters_per_face": stats["newton_iters"] / max(1, stats["faces"]),
     }

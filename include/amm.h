@@ -290,9 +290,14 @@ int amm_mlp_attach(amm_ctx* ctx, const amm_mlp* net);
  * into states_device [n_faces][6] (internal face order) -- training data for
  * the proposal network.  FP32 forms only. */
 int amm_harvest(amm_ctx* ctx, double cfl, float* states_device);
-/* features [n][6] and pbar [n] (may be NULL) from face states */
+/* From face states [n][6] (rho_L, u_L, p_L, rho_R, u_R, p_R): the network's
+ * features [n][6], and (each may be NULL) pbar [n], the two-shock estimate
+ * p_TS [n] that the proposal corrects (p0 = p_TS exp(y)), and the compression
+ * ratio ppv / max(p_L, p_R) [n] of the gate (the proposal is used where it
+ * exceeds AMM_PROPOSAL_GATE); FP32, as the flux kernel computes them. */
+#define AMM_PROPOSAL_GATE 1.25
 int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
-                     void* stream);
+                     float* pts_device, float* ratio_device, void* stream);
 /* exact star pressure of each face state in FP64 (Newton from the standard
  * guess to the relative tolerance tol); NaN where the states generate vacuum */
 int amm_riemann_pstar(double gamma, int64_t n, const float* states_device, double tol, float* pstar_device,

@@ -531,7 +531,7 @@ int ora_riemann(double g, const double* WL, const double* WR, double tol, int ma
     if (!(p0 > pfloor)) p0 = pfloor;
   }
   /* Newton iteration on f(p) = 0; it also stops when f(p) vanishes to
-   * rounding (|f| within 8 ulps of the size of its terms): p is then the root
+   * rounding (|f| within 64 ulps of the size of its terms): p is then the root
    * in working precision.  Near vacuum f is a small difference of large terms
    * and the relative change of p cannot fall below tol. */
   double p = p0;
@@ -540,7 +540,7 @@ int ora_riemann(double g, const double* WL, const double* WR, double tol, int ma
     double dL, dR;
     const double fLp = pfun(p, rhoL, pL, cL, g, &dL), fRp = pfun(p, rhoR, pR, cR, g, &dR);
     const double f = fLp + fRp + du;
-    if (fabs(f) <= 8.0 * DBL_EPSILON * (fabs(fLp) + fabs(fRp) + fabs(du))) {
+    if (fabs(f) <= 64.0 * DBL_EPSILON * (fabs(fLp) + fabs(fRp) + fabs(du))) {
       conv = 1;
       break;
     }

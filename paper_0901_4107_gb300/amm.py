@@ -104,7 +104,7 @@ _SIGS = {
     "amm_mlp_sync": (_I, [_P]),
     "amm_mlp_attach": (_I, [_P, _P]),
     "amm_harvest": (_I, [_P, _D, _P]),
-    "amm_mlp_features": (_I, [_D, _I64, _P, _P, _P, _P]),
+    "amm_mlp_features": (_I, [_D, _I64, _P, _P, _P, _P, _P, _P]),
     "amm_riemann_pstar": (_I, [_D, _I64, _P, _D, _P, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
 }
@@ -471,8 +471,9 @@ def amm_harvest(ctx, cfl, states_ptr):
     _check(ctx, lib().amm_harvest(ctx.handle, float(cfl), _ptr(states_ptr)))
 
 
-def amm_mlp_features(gamma, n, states_ptr, x_ptr, pbar_ptr=0, stream=None):
-    rc = lib().amm_mlp_features(float(gamma), int(n), _ptr(states_ptr), _ptr(x_ptr), _ptr(pbar_ptr), _ptr(stream))
+def amm_mlp_features(gamma, n, states_ptr, x_ptr, pbar_ptr=0, pts_ptr=0, ratio_ptr=0, stream=None):
+    rc = lib().amm_mlp_features(float(gamma), int(n), _ptr(states_ptr), _ptr(x_ptr), _ptr(pbar_ptr), _ptr(pts_ptr),
+                                _ptr(ratio_ptr), _ptr(stream))
     if rc != AMM_OK:
         raise AmmError(rc, "amm_mlp_features failed")
 

@@ -1,11 +1,12 @@
 // Face fluxes of the FP32 learned form: the flux work with the proposal
 // network fused in.  A CTA of H x 128 threads handles H x 128 faces at a
-// time: every thread extrapolates its face (face_prepare) and writes the
-// normalised features as row (t mod 128) of the BF16 operand of its group,
-// one thread issues the tensor-core layers of all groups (tcgen05, FP32
-// accumulators in tensor memory: group h owns columns 64h..64h+63, reused by
-// both layers), every thread reads its row back, forms p0 = pbar exp(y) and
-// runs the exact Riemann solver from it (face_finish).  Newton still iterates
+// time: every thread extrapolates its face (face_prepare) and, if any face of
+// the CTA passes the gate, writes the normalised features as row (t mod 128)
+// of the BF16 operand of its group, one thread issues the tensor-core layers
+// of all groups (tcgen05, FP32 accumulators in tensor memory: group h owns
+// columns 64h..64h+63, reused by both layers), every thread reads its row
+// back, forms p0 = p_TS exp(y) and runs the exact Riemann solver from it
+// (face_finish).  Newton still iterates
 // to the same tolerance, so the result depends on the network only through
 // the iteration count.
 //
@@ -96,9 +97,25 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
   tc::fence_after_sync();
   FaceWork<float> f;
   face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, f);
-  // normalised features (the network's input)
+  // does this face's Riemann problem take the proposal?  Only strong
+  // compression: the linearised estimate above PROPOSAL_GATE times the larger
+  // pressure (which also places it in the two-shock branch of the guess)
   const float rb = 0.5f * (f.WppL[0] + f.WppR[0]);
   const float pb = 0.5f * (f.WppL[4] + f.WppR[4]);
+  bool need = false;
+  float pts = pb;
+  {
+    const float cL = sqrtf(g * f.WppL[4] / f.WppL[0]), cR = sqrtf(g * f.WppR[4] / f.WppR[0]);
+    const float ppv = linearised_pstar(f.WppL[0], f.uL, f.WppL[4], cL, f.WppR[0], f.uR, f.WppR[4], cR);
+    need = valid && ppv > PROPOSAL_GATE * fmaxf(f.WppL[4], f.WppR[4]);
+    if (need) pts = two_shock_pstar(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], ppv, v.gas);
+  }
+  if (!__syncthreads_or(need)) {
+    // no face of the CTA takes the proposal: the plain solver
+    face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), false, 0.0f);
+    return;
+  }
+  // normalised features (the network's input)
   const float icb = rsqrtf(g * pb / rb);
   {
     const float irb = 1.0f / rb, ipb = 1.0f / pb;
@@ -155,8 +172,8 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
     for (int j = 0; j < 16; j++) y += s.w3[16 * c + j] * silu_fast(z[j] + s.bias2[16 * c + j]);
   }
   y = fminf(fmaxf(y, -30.0f), 30.0f);
-  const bool use = s.ok != 0;  // after a timed-out wait, fall back to the standard guess
-  face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), use, pb * __expf(y));
+  const bool use = need && s.ok != 0;  // after a timed-out wait, fall back to the standard guess
+  face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), use, pts * __expf(y));
 }
 
 template <int H>
@@ -214,6 +231,14 @@ static_assert(5 * learned_smem_bytes<PL_H>() > 228 * 1024, "more than 4 persiste
 static_assert(4 * 64 * PL_H <= 512, "tensor-memory columns of 4 co-resident CTAs");
 
 cudaError_t prepare_flux_learned() {
+  // the largest shared-memory carveout, so that the CTAs the launches assume
+  // per SM fit (the occupancy of the cooperative launch is computed with it)
+  for (const void* k : {(const void*)k_flux_learned<false>, (const void*)k_flux_learned<true>,
+                        (const void*)k_step_persistent_learned<false>, (const void*)k_step_persistent_learned<true>}) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = cudaFuncSetAttribute(k_flux_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)learned_smem_bytes<1>());
   if (e == cudaSuccess)
@@ -233,12 +258,12 @@ cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto kern = c->opt.entropy ? k_flux_learned<true> : k_flux_learned<false>;
+  // four CTAs per SM (128 registers x 128 threads each), each walking
+  // 128-face halves of the face tiles
   const int nsub = 2 * c->n_ftiles;
   const int grid = std::min(nsub, 4 * sms);
-  if (c->opt.entropy)
-    k_flux_learned<true><<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
-  else
-    k_flux_learned<false><<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
+  kern<<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
   return cudaGetLastError();
 }
 

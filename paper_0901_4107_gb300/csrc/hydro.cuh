@@ -149,11 +149,15 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
     const real dx = Wi.y - wi3[0], dy = Wi.z - wi3[1], dz = Wi.w - wi3[2];
     ekm = (real)0.5 * (real)v.Q[ii] * (dx * dx + dy * dy + dz * dz);
   }
+  // the neighbour index of the next incidence is loaded one iteration ahead,
+  // so the neighbour's state load does not wait behind its index load
+  int jn = (q0 + lane < q1) ? v.nbr[q0 + lane] : 0;
 #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
     // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out),
     // with the geometric weights of the incidence precomputed (igA, igB)
-    const int j = v.nbr[q];
+    const int j = jn;
+    if (q + G < q1) jn = v.nbr[q + G];
     const R4<real> a4 = v.igA[q];
     const R4<real> b4 = v.igB[q];
     const R4<real> Wj = v.W[j];
@@ -296,7 +300,7 @@ __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real
   Wpp[2] = uy + (g2.x * fx + g2.y * fy + g2.z * fz) - hdt * (ux * g2.x + uy * g2.y + uz * g2.z + g1.w * ir);
   Wpp[3] = uz + (g3.x * fx + g3.y * fy + g3.z * fz) - hdt * (ux * g3.x + uy * g3.y + uz * g3.z + g2.w * ir);
   Wpp[4] = P + (g0.w * fx + g1.w * fy + g2.w * fz) -
-           hdt * ((real)v.gamma * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
+           hdt * (v.gas.g * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
   if constexpr (ENT) {
     // entropic function A (Sec. 3.5): reconstructed like the primitives and
     // advected, dA/dt = -v'.grad A; the cell value if that is not positive
@@ -393,7 +397,7 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
   const bool valid = f.valid;
   real rhoF, uF, pF, ps;
   RiemannInfo info;
-  const int side = riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.maxit,
+  const int side = riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.tol_r, v.maxit,
                                   have_guess, guess, rhoF, uF, pF, info, ps);
   const real* Wt = side ? f.WppR : f.WppL;
   const real ut = side ? f.uR : f.uL;
@@ -594,6 +598,19 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   double d[NA];
   real mach = (real)1;
   bool bad = false;
+  // per tile (one box): the fixed-point exponents and dt times the scale of
+  // each component's sums, so a cell's update is one FMA per component
+  __shared__ int s_eb[6];
+  __shared__ double s_dts[6];
+  if (threadIdx.x == 0) {
+    const double dt = box_dt(v, t.box);
+    for (int a = 0; a < NA; a++) {
+      const int eb = (int)((v.fmax_bits[FMAX_STRIDE * t.box + a] >> 23) & 0xffu);
+      s_eb[a] = eb;
+      s_dts[a] = (sizeof(real) == 4 && v.fixed_acc) ? dt * fixed_scale(eb, v.headroom) : dt;
+    }
+  }
+  __syncthreads();
   if (sizeof(real) == 4 && v.fixed_acc) {
     // Exact sums: every face flux is converted once to an int64 multiple of
     // 2^-s (s per box and component, from the step's largest |A F|) and the
@@ -603,7 +620,7 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     // the integer total is scaled back to FP64.
     int eb[NA];
 #pragma unroll
-    for (int a = 0; a < NA; a++) eb[a] = (int)((v.fmax_bits[FMAX_STRIDE * t.box + a] >> 23) & 0xffu);
+    for (int a = 0; a < NA; a++) eb[a] = s_eb[a];
     long long acc[NA];
 #pragma unroll
     for (int a = 0; a < NA; a++) acc[a] = 0;
@@ -630,7 +647,7 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     bad = group_max<G>((int)bad) != 0;
     if (lane == 0) {
 #pragma unroll
-      for (int a = 0; a < NA; a++) d[a] = __ll2double_rn(acc[a]) * fixed_scale(eb[a], v.headroom);
+      for (int a = 0; a < NA; a++) d[a] = __ll2double_rn(acc[a]);
     }
   } else {
     double acc[NA];
@@ -663,16 +680,16 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
   if constexpr (ENT) mach = group_max<G>(mach);
   unsigned nonpos = 0, keep = 0;
   if (valid && lane == 0) {
-    const double dt = box_dt(v, t.box);
 #pragma unroll
-    for (int a = 0; a < 5; a++) q[a] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v.Q[a * n + i] - dt * d[a];
+    for (int a = 0; a < 5; a++)
+      q[a] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v.Q[a * n + i] - s_dts[a] * d[a];
     if constexpr (ENT) {
       // Sec. 3.5: keep the advected entropy where no shock above the
       // threshold Mach number touches the cell, or where the new thermal
       // energy is below alpha_s times the largest kinetic energy around it;
       // then P = (S/M) rho^gamma sets the thermal energy.  Otherwise the
       // energy update stands and S is re-initialised from it.
-      const double Sadv = v.S[i] - dt * d[5];
+      const double Sadv = v.S[i] - s_dts[5] * d[5];
       const double m = q[0];
       const double V = v.cgeo64[i].x;
       const double rho = m / V;

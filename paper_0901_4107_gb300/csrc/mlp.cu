@@ -447,10 +447,20 @@ __global__ void k_mlp_adam(float* p, const float* g, float* m, float* v, float l
 }
 
 // normalised features and pbar from face states (rhoL, uL, pL, rhoR, uR, pR)
-__global__ void k_mlp_features(double gamma, int64_t m, const float* st, float* x, float* pbar) {
+__global__ void k_mlp_features(double gamma, int64_t m, const float* st, float* x, float* pbar, float* pts,
+                               float* ratio) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   const float* s = st + 6 * i;
+  if (pts || ratio) {
+    // the two-shock estimate the proposal corrects, and the compression
+    // measure of the gate, in FP32 as the flux kernel takes them
+    const GasC<float> G(gamma);
+    const float cL = sqrtf(G.g * s[2] / s[0]), cR = sqrtf(G.g * s[5] / s[3]);
+    const float ppv = linearised_pstar(s[0], s[1], s[2], cL, s[3], s[4], s[5], cR);
+    if (pts) pts[i] = two_shock_pstar(s[0], s[1], s[2], s[3], s[4], s[5], ppv, G);
+    if (ratio) ratio[i] = ppv / fmaxf(s[2], s[5]);
+  }
   const float rb = 0.5f * (s[0] + s[3]);
   const float pb = 0.5f * (s[2] + s[5]);
   const float cb = sqrtf((float)gamma * pb / rb);
@@ -480,7 +490,7 @@ __global__ void k_riemann_pstar(double gamma, int64_t m, const float* st, double
   RiemannInfo info{0, 0, 0, 0};
   NewtonTail<double> nt;
   const double p0 = standard_guess(rL, uL, pL, cL, rR, uR, pR, cR, G);
-  const double p = newton_pstar(p0, rL, uL, pL, cL, rR, uR, pR, cR, G, tol, maxit, info, nt);
+  const double p = newton_pstar(p0, rL, uL, pL, cL, rR, uR, pR, cR, G, tol, tol, maxit, info, nt);
   pstar[i] = info.fail ? __int_as_float(0x7fc00000) : (float)p;
 }
 
@@ -693,10 +703,10 @@ int amm_mlp_attach(amm_ctx* c, const amm_mlp* m) {
 }
 
 int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
-                     void* stream) {
+                     float* pts_device, float* ratio_device, void* stream) {
   if (!(gamma > 1.0) || n < 1 || !states_device || !x_device) return AMM_ERR_INVALID_ARG;
-  amm::k_mlp_features<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(gamma, n, states_device,
-                                                                                    x_device, pbar_device);
+  amm::k_mlp_features<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      gamma, n, states_device, x_device, pbar_device, pts_device, ratio_device);
   return cudaGetLastError() == cudaSuccess ? AMM_OK : AMM_ERR_CUDA;
 }
 
