@@ -57,6 +57,8 @@ WORKLOADS = {
     "learned192": ("config-4 workload: the config-2 field at 192^3 (jittered lattice +-0.2h, seed 2, rms Mach 2, "
                    "Lagrangian); FP32 flux with the learned p* proposal vs the standard starting value, Newton to "
                    "1e-6 relative in both"),
+    "training": ("proposal-network training step: 2^20 face states harvested from one step of the config-2 workload "
+                 "(64^3), BF16 tcgen05 forward and backward of the 6-64-64-1 SiLU network, gradient reduction, Adam"),
     "ensemble": ("config-5 workload: 64 independent periodic unit boxes, n^3 cells with n=round(exp(U(ln16,ln96))) "
                  "(seed 5), each the config-2 field at rms Mach U[0.5,4], gamma=5/3, stationary mesh, per-box "
                  "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, one persistent "
@@ -105,29 +107,34 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def source_hash():
+# the sources each profiled kernel is compiled from (its DRAM traffic in
+# profiles/ncu_traffic.json holds only while these are unchanged)
+_COMMON = ["amm_internal.cuh", "hydro.cuh", "riemann.cuh", "hydro_f32.cu", "../../include/amm.h"]
+KERNEL_SOURCES = {
+    "gradients": _COMMON, "flux": _COMMON, "update": _COMMON,
+    "learned_flux": _COMMON + ["flux_learned.cu", "learned.cuh", "tc.cuh", "persistent.cuh"],
+}
+
+
+def source_hash(kernel):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0901_4107_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel, nf):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None), scaled to this launch's faces."""
+    on the kernel's current sources (else None), scaled to this launch's faces."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
-            t = json.load(f)
+            k = json.load(f)["kernels"][kernel]
     except Exception:
         return None
-    if t.get("source_hash") != source_hash():
-        return None
-    k = t.get("kernels", {}).get(kernel)
-    if not k:
+    if kernel not in KERNEL_SOURCES or k.get("source_hash") != source_hash(kernel):
         return None
     return k["dram_bytes"] * (nf / k["faces"])
 
@@ -138,9 +145,11 @@ def algorithmic_bytes(kernel, n, nf, rb):
     real type (4 FP32 form, 8 FP64 form)."""
     inc = 2 * nf                                  # cell->face incidences
     if kernel == "gradients":
-        # W, P, cell geometry read; gradients written; CSR and offsets read;
-        # face geometry (2 vectors of 4 reals) read once per face
-        return n * (5 * rb + 4 * rb + 16 * rb + 4) + inc * 8 + nf * 8 * rb
+        # per cell: W, P, 1/V and R read, CSR offset, the gradients written;
+        # per incidence: its precomputed weights and lever arm (2 vectors of
+        # 4 reals and 1 real) and the neighbour index streamed; the gathered
+        # neighbour W, P counted once per cell
+        return n * (5 * rb + 4 * rb + rb + 4 + 16 * rb) + n * 5 * rb + inc * (9 * rb + 4)
     if kernel == "flux":
         # left/right indices and face geometry read; 5-component flux written;
         # per cell: W, P, gradients, cell geometry read once
@@ -452,7 +461,7 @@ MLP_FLOP_FWD = 2 * (6 * 64 + 64 * 64 + 64)
 MLP_FLOP_STEP = MLP_FLOP_FWD + 2 * (64 * 64 + 64 * 64 + 6 * 64 + 64)
 
 
-def bench_training(g, P, motion, samples=1 << 20, reps=20):
+def bench_training(g, P, motion, samples=1 << 20, reps=20, warmup=3):
     """Device time of one training step (tcgen05 forward + backward over a
     batch, gradient reduction, Adam) on `samples` harvested face states."""
     from paper_0901_4107_gb300 import learned
@@ -463,7 +472,7 @@ def bench_training(g, P, motion, samples=1 << 20, reps=20):
     idx = torch.arange(n, dtype=torch.int32, device="cuda")
     net = amm.amm_mlp_create(P.gamma, g.stream.cuda_stream)
     amm.amm_mlp_set_params(net, learned.init_params(7))
-    for _ in range(3):
+    for _ in range(warmup):
         amm.amm_mlp_train_step(net, x.data_ptr(), t.data_ptr(), idx.data_ptr(), n, 1e-4)
     amm.amm_mlp_sync(net)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -486,6 +495,30 @@ def bench_training(g, P, motion, samples=1 << 20, reps=20):
             "algorithmic_flop_per_sample": MLP_FLOP_STEP, "achieved_tflops": tflops,
             "peak_tflops": bf16, "frac": (tflops / bf16) if bf16 else None,
             "peak_source": "measured bf16_tflops (burst)"}
+
+
+def bench_train_workload(args, g, world, rank, local):
+    """The proposal network's training step as its own workload (the dense
+    contraction of the learned form): samples per second and BF16 tensor
+    throughput against the measured peak."""
+    from harness import ics
+    P = ics.turbulent_3d(64, seed=2 + rank)
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = bench_training(g, P, "lagrangian", reps=args.steps, warmup=args.warmup)
+    clocks = sampler.stop()
+    rate = r["samples_per_s"] * world
+    return {
+        "metric": "proposal-network training samples/s on 1 GB300 (BF16 tcgen05 forward + backward + Adam)",
+        "value": rate, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOADS["training"], "batch": r["samples"]},
+        "roofline": {"kernel": "training step", "bound": "tensor", "achieved": r["achieved_tflops"],
+                     "peak": r["peak_tflops"], "unit": "TFLOP/s", "frac": r["frac"], "traffic": None,
+                     "peak_source": r["peak_source"], "algorithmic_flop_per_sample": r["algorithmic_flop_per_sample"]},
+        "gpu_launches": 4 * args.steps, "clocks": clocks,
+    }
 
 
 def bench_box(args, g, world, rank, local):
@@ -838,6 +871,8 @@ def main():
     g = Gpu(local, args.proposal_epochs)
     if args.workload == "ensemble":
         line = bench_ensemble(args, g, world, rank, local)
+    elif args.workload == "training":
+        line = bench_train_workload(args, g, world, rank, local)
     else:
         line = bench_box(args, g, world, rank, local)
     if rank == 0:

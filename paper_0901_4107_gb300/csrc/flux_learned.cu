@@ -24,6 +24,10 @@
 namespace amm {
 
 constexpr int LT = 128;  // faces per MMA group = MMA rows
+// CTAs of k_flux_learned per SM (launch bounds and grid); their tensor memory
+// (64 columns each) must fit the SM's 512
+constexpr int LEARNED_CTAS_PER_SM = 6;
+static_assert(LEARNED_CTAS_PER_SM * 64 <= 512, "tensor-memory columns of the co-resident CTAs");
 
 template <int H>
 struct LearnedSmem {
@@ -186,7 +190,7 @@ __device__ __forceinline__ void learned_teardown(const HydroView<float>& v, Lear
 
 // flux phase alone: CTAs walk the 128-face halves of the face tiles
 template <bool ENT>
-__global__ void __launch_bounds__(LT, 4) k_flux_learned(HydroView<float> v, int nsub) {
+__global__ void __launch_bounds__(LT, LEARNED_CTAS_PER_SM) k_flux_learned(HydroView<float> v, int nsub) {
   extern __shared__ uint8_t smem_raw[];
   LearnedSmem<1>& s = learned_smem_ref<1>(smem_raw);
   learned_setup<1>(s, (const MlpDevice*)v.mlp);
@@ -259,10 +263,10 @@ cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   auto kern = c->opt.entropy ? k_flux_learned<true> : k_flux_learned<false>;
-  // four CTAs per SM (128 registers x 128 threads each), each walking
-  // 128-face halves of the face tiles
+  // LEARNED_CTAS_PER_SM CTAs per SM, each walking 128-face halves of the
+  // face tiles
   const int nsub = 2 * c->n_ftiles;
-  const int grid = std::min(nsub, 4 * sms);
+  const int grid = std::min(nsub, LEARNED_CTAS_PER_SM * sms);
   kern<<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
   return cudaGetLastError();
 }
