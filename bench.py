@@ -555,15 +555,7 @@ def bench_box(args, g, world, rank, local):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    step_ms = statistics.mean(ms)
-    faces_all = float(nf)
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-        tot = torch.tensor([float(nf)], device="cuda")
-        torch.distributed.all_reduce(tot)
-        faces_all = float(tot.item())
+    step_ms, faces_all = reduce_replicas(torch, statistics.mean(ms), nf, world, "cuda")
     value = faces_all / (step_ms * 1e-3)
     split = kernel_split(g, ctxs[head], Q0d, tuning)
     kern = kernel_table(split or ker, n, nf, 4)
@@ -654,6 +646,19 @@ def bench_box(args, g, world, rank, local):
     return line
 
 
+def reduce_replicas(torch, step_ms, faces, world, device):
+    """N replicas, one per rank: the job's step time is the slowest rank's and
+    its work the sum of the ranks' faces (weak scaling).  Returns (step_ms,
+    faces of all ranks)."""
+    if world <= 1:
+        return step_ms, float(faces)
+    t = torch.tensor([step_ms, float(faces)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(t)
+    return float(mx[0].item()), float(t[1].item())
+
+
 def state_and_failures(amm, ctx):
     """The state even after a numeric failure, with what failed: the Newton
     solves that hit the iteration cap, the non-positive cells and the boxes
@@ -734,15 +739,7 @@ def bench_ensemble(args, g, world, rank, local):
     amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"],
                        tuning["persistent"])
     _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
-    step_ms = statistics.mean(ms)
-    faces_all = float(nf)
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-        tot = torch.tensor([float(nf)], device="cuda")
-        torch.distributed.all_reduce(tot)
-        faces_all = float(tot.item())
+    step_ms, faces_all = reduce_replicas(torch, statistics.mean(ms), nf, world, "cuda")
     value = faces_all / (step_ms * 1e-3)
     # per-phase times of the same shapes for the roofline (a persistent step
     # is one launch)

@@ -136,6 +136,17 @@ int amm_create(amm_ctx** out, int dim, int64_t n_cells, const double* generators
                const double* face_centroid, const double* box, const double* cell_Q, double gamma,
                const amm_options* opt);
 
+/* The same from device arrays: generators, face_cells, face_shift, face_area,
+ * face_centroid and cell_Q are device pointers (layouts as above), box (and
+ * the options' box offsets) stay on the host.  The arrays are borrowed for
+ * the call only: they are copied (through host memory, where the face list is
+ * ordered and checked), so the caller keeps ownership.  Errors as amm_create,
+ * plus AMM_ERR_CUDA if a copy fails.  Synchronises. */
+int amm_create_device(amm_ctx** out, int dim, int64_t n_cells, const double* generators_device, int64_t n_faces,
+                      const int32_t* face_cells_device, const int8_t* face_shift_device,
+                      const double* face_area_device, const double* face_centroid_device, const double* box,
+                      const double* cell_Q_device, double gamma, const amm_options* opt);
+
 /* Releases all device memory of the context.  NULL is accepted. */
 int amm_destroy(amm_ctx* ctx);
 

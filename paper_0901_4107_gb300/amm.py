@@ -62,6 +62,7 @@ _SIGS = {
     "amm_default_options": (None, [_P]),
     "amm_last_error": (ctypes.c_char_p, [_P]),
     "amm_create": (_I, [ctypes.POINTER(_P), _I, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _D, _P]),
+    "amm_create_device": (_I, [ctypes.POINTER(_P), _I, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _D, _P]),
     "amm_destroy": (_I, [_P]),
     "amm_set_state": (_I, [_P, _P]),
     "amm_set_state_device": (_I, [_P, _P]),
@@ -205,6 +206,23 @@ def amm_create(dim, generators, face_cells, face_shift, face_area, face_centroid
     if rc != AMM_OK:
         raise AmmError(rc, "amm_create failed (details on stderr)")
     return Context(h, dim, n, nf, boxa.shape[0])
+
+
+def amm_create_device(dim, n, nf, gen_ptr, cells_ptr, shift_ptr, area_ptr, cen_ptr, box, Q_ptr, gamma, opt=None):
+    """amm_create from device arrays (pointers); `box` is a host array
+    ([dim] or [n_boxes, dim]; several boxes need the options' offsets)."""
+    boxa = _arr(box, np.float64).reshape(-1, dim)
+    if opt is None:
+        opt = amm_default_options()
+    if boxa.shape[0] == 1:
+        opt.n_boxes = 1
+    h = ctypes.c_void_p()
+    rc = lib().amm_create_device(ctypes.byref(h), dim, int(n), _ptr(gen_ptr), int(nf), _ptr(cells_ptr), _ptr(shift_ptr),
+                                 _ptr(area_ptr), _ptr(cen_ptr), boxa.ctypes.data, _ptr(Q_ptr), float(gamma),
+                                 ctypes.byref(opt))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_create_device failed (details on stderr)")
+    return Context(h, dim, int(n), int(nf), boxa.shape[0])
 
 
 def amm_destroy(ctx):

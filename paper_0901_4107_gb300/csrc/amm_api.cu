@@ -492,6 +492,33 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   return AMM_OK;
 }
 
+int amm_create_device(amm_ctx** out, int dim, int64_t n, const double* gen_d, int64_t nf, const int32_t* cells_d,
+                      const int8_t* shift_d, const double* area_d, const double* cen_d, const double* box,
+                      const double* Q_d, double gamma, const amm_options* opt) {
+  if (!out) return AMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((dim != 2 && dim != 3) || n < 2 || n > (int64_t)1 << 30 || nf < 1 || nf > ((int64_t)1 << 30) - 1)
+    return AMM_ERR_INVALID_ARG;
+  if (!gen_d || !cells_d || !shift_d || !area_d || !cen_d || !box || !Q_d) return AMM_ERR_INVALID_ARG;
+  std::vector<double> gen((size_t)n * dim), area((size_t)nf), cen((size_t)nf * dim), Q((size_t)n * (dim + 2));
+  std::vector<int32_t> cells((size_t)nf * 2);
+  std::vector<int8_t> shift((size_t)nf * dim);
+  const struct {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } copies[] = {{gen.data(), gen_d, sizeof(double) * gen.size()},     {cells.data(), cells_d, sizeof(int32_t) * cells.size()},
+                {shift.data(), shift_d, shift.size()},                 {area.data(), area_d, sizeof(double) * area.size()},
+                {cen.data(), cen_d, sizeof(double) * cen.size()},      {Q.data(), Q_d, sizeof(double) * Q.size()}};
+  for (const auto& cp : copies)
+    if (cudaMemcpy(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return AMM_ERR_CUDA;
+    }
+  return amm_create(out, dim, n, gen.data(), nf, cells.data(), shift.data(), area.data(), cen.data(), box, Q.data(),
+                    gamma, opt);
+}
+
 int amm_destroy(amm_ctx* c) {
   if (!c) return AMM_OK;
   cudaStreamSynchronize(c->stream);

@@ -368,3 +368,25 @@ def test_autotune_restores_state_and_keeps_parity(amm):
     amm.amm_step(ctx, dt)
     emax, _ = errs(amm.amm_get_state(ctx), ref, fl)
     assert emax < TOL["fp32"]
+
+
+def test_create_from_device_arrays(amm):
+    """amm_create_device copies the same inputs from device memory: the
+    context steps bit-identically to one made from host arrays."""
+    import torch
+    P = ics.turbulent_3d(12, seed=6)
+    T = P.tess
+    Q = P.conserved()
+    outs = []
+    for dev in (False, True):
+        opt = amm.amm_default_options("fp64", "lagrangian")
+        if dev:
+            t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+                 (T.points, T.cells.astype(np.int32), T.shift.astype(np.int8), T.area, T.centroid, Q)]
+            ctx = amm.amm_create_device(3, T.n_cells, T.n_faces, *[x.data_ptr() for x in t[:5]], T.box,
+                                        t[5].data_ptr(), P.gamma, opt)
+        else:
+            ctx = amm.create_from_mesh(T, Q, P.gamma, precision="fp64")
+        amm.amm_advance(ctx, 0.3, 2, use_graph=False)
+        outs.append(amm.amm_get_state(ctx))
+    assert np.array_equal(outs[0], outs[1])
