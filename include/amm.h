@@ -239,7 +239,8 @@ typedef struct amm_tuning {
   int persistent;  /* 1: amm_advance runs each step as ONE cooperative launch whose CTAs walk
                       every phase (gradients, fluxes, update, totals) with grid barriers between
                       them (bounded waits); 0: one launch per phase.  Both modes give
-                      bit-identical states, in every precision. */
+                      bit-identical states in the FP64 and FP32 forms; in the learned form
+                      they agree to FP32 rounding (two kernels, two register budgets). */
   float step_ms;   /* amm_autotune: sum of the chosen kernels' median times */
 } amm_tuning;
 

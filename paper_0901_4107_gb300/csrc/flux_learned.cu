@@ -12,8 +12,9 @@
 //
 // Two kernels use it: k_flux_learned (H = 1, the flux phase of the kernel
 // sequence) and k_step_persistent_learned (H = 2, the whole step as one
-// cooperative launch, the batched-ensemble form).  Both run the identical
-// per-face arithmetic, so the two step modes give bit-identical states.
+// cooperative launch, the batched-ensemble form).  Both run the same per-face
+// arithmetic; compiled under different register budgets, they may contract a
+// multiply-add differently, so the two step modes agree to FP32 rounding.
 #include <cuda_runtime.h>
 
 #include "hydro.cuh"

@@ -532,34 +532,30 @@ __device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
 }
 
 template <typename real, int B, bool ENT>
-__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 3 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
+__global__ void __launch_bounds__(B, sizeof(real) == 4 ? 4 * FACE_TILE / B : FACE_TILE / B) k_flux(HydroView<real> v) {
   flux_item<real, B, ENT>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ A8+A1+A9
-// Fixed-point image of an FP32 value: x * 2^s as an int64, with
-// s = 188 - headroom - eb and eb the biased exponent of the largest magnitude
-// of the component, so every |x| 2^s < 2^(62 - headroom) and a sum over at
-// most 2^headroom terms cannot overflow.  Built from the float's bits on the
-// integer pipe (a float-to-int64 conversion instruction would run on GB300's
-// narrow FP64 pipe); values below the resolution 2^-s are truncated toward
-// zero, the same way for both cells of a face.  Inf/NaN sets `bad`.
-__device__ __forceinline__ long long to_fixed(float x, int eb, int headroom, bool& bad) {
+// Fixed-point image of an FP32 value: x * 2^s as an int64, truncated toward
+// zero, with s = 188 - headroom - eb and eb the biased exponent of the largest
+// magnitude of the component, so every |x| 2^s < 2^(62 - headroom) and a sum
+// over at most 2^headroom terms cannot overflow; the image is added to `acc`
+// with the sign of x flipped when `flip` is set (the incidence's side).
+// Built from the float's bits on the integer pipe (a float-to-int64
+// conversion instruction would run on GB300's narrow FP64 pipe): with the
+// 24-bit significand M and biased exponent e <= eb, the image is
+// floor(M 2^(e - eb + 38 - headroom)) = (M 2^38) >> (eb + headroom - e), one
+// right shift.  Zero (e = 0; denormals are flushed in the FP32 form) adds 0;
+// Inf/NaN sets `bad`.  ebh = eb + headroom.
+__device__ __forceinline__ void add_fixed(long long& acc, float x, int ebh, bool flip, bool& bad) {
   const unsigned u = __float_as_uint(x);
   const int e = (int)((u >> 23) & 0xffu);
-  if (e == 0) return 0;               // zero (denormals are flushed in the FP32 form)
-  if (e == 255) {
-    bad = true;
-    return 0;
-  }
-  const long long M = (long long)((u & 0x7fffffu) | 0x800000u);
-  const int sh = e - eb + 38 - headroom;
-  long long X;
-  if (sh >= 0)
-    X = M << sh;
-  else
-    X = (sh > -40) ? (M >> (-sh)) : 0ll;
-  return (u >> 31) ? -X : X;
+  bad |= (e == 255);
+  const unsigned long long M = (e != 0) ? (unsigned long long)((u & 0x7fffffu) | 0x800000u) : 0ull;
+  const long long X = (long long)((M << 38) >> min((unsigned)(ebh - e), 63u));
+  const long long neg = -(long long)(((u >> 31) ^ (unsigned)flip) & 1u);   // 0 or all ones
+  acc += (X ^ neg) - neg;
 }
 
 // 2^(eb - 188 + headroom) in FP64 (exact)
@@ -618,9 +614,9 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     // with opposite signs, so the update conserves exactly and does not
     // depend on the summation order.  One rounding per cell remains, when
     // the integer total is scaled back to FP64.
-    int eb[NA];
+    int ebh[NA];
 #pragma unroll
-    for (int a = 0; a < NA; a++) eb[a] = s_eb[a];
+    for (int a = 0; a < NA; a++) ebh[a] = s_eb[a] + v.headroom;
     long long acc[NA];
 #pragma unroll
     for (int a = 0; a < NA; a++) acc[a] = 0;
@@ -637,10 +633,7 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
         mach = mf > mach ? mf : mach;
       }
 #pragma unroll
-      for (int a = 0; a < NA; a++) {
-        const long long x = to_fixed(fv[a], eb[a], v.headroom, bad);
-        acc[a] += (r.x & 1) ? -x : x;
-      }
+      for (int a = 0; a < NA; a++) add_fixed(acc[a], fv[a], ebh[a], (r.x & 1) != 0, bad);
     }
 #pragma unroll
     for (int a = 0; a < NA; a++) acc[a] = group_sum<G>(acc[a]);
