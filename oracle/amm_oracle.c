@@ -1078,6 +1078,36 @@ void ora_totals(int dim, long n, const double* Q, double* tot) {
     for (int v = 0; v < nv; v++) tot[v] += Q[i * nv + v];
 }
 
+/* --------------------------------- Sec. 4.1: mesh-regularity correction
+ * Eq. (EqnShapeCorrVel): a generator further than a fraction eta of its
+ * cell's radius R_i = (3 V_i / 4 pi)^(1/3) (2D: (V_i / pi)^(1/2)) from the
+ * centre of mass s_i is given an extra velocity towards it,
+ *   w_i' = w_i + chi c_i (s_i - r_i)/d_i * ramp,  d_i = |s_i - r_i|,
+ *   ramp = 0 for d_i < 0.9 eta R_i, (d_i - 0.9 eta R_i)/(0.2 eta R_i) up to
+ *   1.1 eta R_i, 1 beyond; c_i = sqrt(gamma P_i / rho_i).
+ * s: [n][dim] centres of mass in the cell's own frame (as ora_geometry
+ * returns them); w, wout: [n][dim]. */
+void ora_shape_correction(int dim, long n, const double* gen, const double* s, const double* V, const double* W,
+                          const double* w, double gamma, double eta, double chi, double* wout) {
+  const int nv = dim + 2;
+  for (long i = 0; i < n; i++) {
+    double d2 = 0.0, ds[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < dim; k++) {
+      ds[k] = s[i * dim + k] - gen[i * dim + k];
+      d2 += ds[k] * ds[k];
+    }
+    const double d = sqrt(d2);
+    const double R = (dim == 3) ? cbrt(3.0 * V[i] / (4.0 * M_PI)) : sqrt(V[i] / M_PI);
+    double ramp = 0.0;
+    if (d >= 1.1 * eta * R)
+      ramp = 1.0;
+    else if (d >= 0.9 * eta * R)
+      ramp = (d - 0.9 * eta * R) / (0.2 * eta * R);
+    const double c = sqrt(gamma * W[i * nv + dim + 1] / W[i * nv]);
+    for (int k = 0; k < dim; k++) wout[i * dim + k] = w[i * dim + k] + ((ramp > 0.0) ? chi * c * ds[k] / d * ramp : 0.0);
+  }
+}
+
 /* ---------------------------------------------------- A10: generator drift
  * Sec. 3, step 8: r_i <- r_i + w_i dt, wrapped back into the box. */
 void ora_drift(int dim, long n, double* gen, const double* wmesh, const double* box, double dt) {

@@ -54,6 +54,8 @@ def lib():
         L.ora_step_entropy.restype = _I
         L.ora_step_entropy.argtypes = [_I, _L, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _P, _D, _D,
                                        _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]
+        L.ora_shape_correction.restype = None
+        L.ora_shape_correction.argtypes = [_I, _L, _P, _P, _P, _P, _P, _D, _D, _D, _P]
         L.ora_set_threads.restype = None
         L.ora_set_threads.argtypes = [_I]
         L.ora_get_threads.restype = _I
@@ -257,3 +259,13 @@ def step_entropy(mesh, Q, S, gamma, mode="lagrangian", wmesh=None, dt=0.0, cfl=0
                                 mach_thresh, alpha_s, Qn.ctypes.data, Sn.ctypes.data, kept.ctypes.data, ctypes.byref(dtu),
                                 cnt.ctypes.data)
     return Qn, Sn, kept, dtu.value, cnt, rc
+
+
+def shape_correction(mesh, W, V, s, w, gamma, eta=0.25, chi=1.0):
+    """Mesh velocity with the regularity correction of Sec. 4.1,
+    eq. (EqnShapeCorrVel); w is the uncorrected mesh velocity [n, dim]."""
+    W, V, s, w = (_c(a, np.float64) for a in (W, V, s, w))
+    out = np.empty_like(w)
+    lib().ora_shape_correction(mesh.dim, mesh.n, mesh.gen.ctypes.data, s.ctypes.data, V.ctypes.data, W.ctypes.data,
+                               w.ctypes.data, gamma, eta, chi, out.ctypes.data)
+    return out
