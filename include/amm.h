@@ -91,6 +91,14 @@ typedef struct amm_options {
                                kept its entropy.  0 (default): the plain energy update. */
   double mach_thresh;       /* shock Mach threshold of the switch (default 1.1) */
   double alpha_s;           /* cold-flow parameter (default 0.01; 0 disables that criterion) */
+  int regularize;           /* 1: mesh-regularity correction of Sec. 4.1, eq. (EqnShapeCorrVel): a
+                               generator further than eta R_i from its cell's centre of mass s_i gets
+                               the extra velocity chi c_i (s_i - r_i)/|s_i - r_i| (ramped in between
+                               0.9 and 1.1 eta R_i), in the face velocities, the Courant step and
+                               amm_drift.  Moving meshes only (AMM_ERR_INVALID_ARG with AMM_EULERIAN).
+                               0 (default): off. */
+  double eta;               /* threshold fraction of the cell radius (default 0.25) */
+  double chi;               /* strength, in units of the sound speed (default 1) */
 } amm_options;
 
 typedef struct amm_stats {

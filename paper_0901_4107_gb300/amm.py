@@ -41,7 +41,8 @@ class amm_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("riemann_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("n_boxes", ctypes.c_int64), ("box_cells", ctypes.POINTER(ctypes.c_int64)),
                 ("box_faces", ctypes.POINTER(ctypes.c_int64)), ("fp64_accumulate", ctypes.c_int),
-                ("entropy", ctypes.c_int), ("mach_thresh", ctypes.c_double), ("alpha_s", ctypes.c_double)]
+                ("entropy", ctypes.c_int), ("mach_thresh", ctypes.c_double), ("alpha_s", ctypes.c_double),
+                ("regularize", ctypes.c_int), ("eta", ctypes.c_double), ("chi", ctypes.c_double)]
 
 
 class amm_stats(ctypes.Structure):
@@ -159,7 +160,8 @@ def _arr(a, dtype):
 
 
 def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True, max_iter=64, riemann_tol=0.0,
-                        stream=None, fp64_accumulate=False, entropy=False, mach_thresh=1.1, alpha_s=0.01):
+                        stream=None, fp64_accumulate=False, entropy=False, mach_thresh=1.1, alpha_s=0.01,
+                        regularize=False, eta=0.25, chi=1.0):
     o = amm_options()
     lib().amm_default_options(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -172,6 +174,9 @@ def amm_default_options(precision="fp64", mesh_motion="lagrangian", limiter=True
     o.entropy = int(bool(entropy))
     o.mach_thresh = float(mach_thresh)
     o.alpha_s = float(alpha_s)
+    o.regularize = int(bool(regularize))
+    o.eta = float(eta)
+    o.chi = float(chi)
     return o
 
 

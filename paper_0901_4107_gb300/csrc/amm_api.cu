@@ -47,8 +47,8 @@ void free_ctx(amm_ctx* c) {
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
-                  c->ftiles, c->box_first_ctile, c->fgeo, c->igA, c->igB, c->igz, c->nbr, c->cgeo64, c->W,   c->P,       c->grad,
-                  c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
+                  c->ftiles, c->box_first_ctile, c->fgeo, c->igA, c->igB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad,
+                  c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->wcorr, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -144,6 +144,9 @@ void amm_default_options(amm_options* o) {
   o->entropy = 0;
   o->mach_thresh = 1.1;
   o->alpha_s = 0.01;
+  o->regularize = 0;
+  o->eta = 0.25;
+  o->chi = 1.0;
 }
 
 const char* amm_last_error(const amm_ctx* c) {
@@ -171,6 +174,10 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   if (opt.max_iter < 1 || opt.max_iter > 10000) return AMM_ERR_INVALID_ARG;
   if (opt.n_boxes < 1 || opt.n_boxes > (1 << 20)) return AMM_ERR_INVALID_ARG;
   if (opt.entropy != 0 && opt.entropy != 1) return AMM_ERR_INVALID_ARG;
+  if (opt.regularize != 0 && opt.regularize != 1) return AMM_ERR_INVALID_ARG;
+  if (opt.regularize && (opt.mesh_motion == AMM_EULERIAN || !(opt.eta > 0.0) || !(opt.chi >= 0.0) ||
+                         !std::isfinite(opt.eta) || !std::isfinite(opt.chi)))
+    return AMM_ERR_INVALID_ARG;
   if (opt.entropy && (!(opt.mach_thresh >= 0.0) || !(opt.alpha_s >= 0.0) || !std::isfinite(opt.alpha_s)))
     return AMM_ERR_INVALID_ARG;
   if (!(opt.riemann_tol > 0.0)) opt.riemann_tol = (opt.precision == AMM_FP64) ? 1e-12 : 1e-6;
@@ -398,8 +405,7 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   CUB(dalloc(&c->cgeo64, (size_t)n));
   CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
   CUB(cudaMalloc(&c->crad, rs * (size_t)n));
-  CUB(cudaMalloc(&c->W, rs * 4 * (size_t)n));
-  CUB(cudaMalloc(&c->P, rs * (size_t)n));
+  CUB(cudaMalloc(&c->cw, rs * 8 * (size_t)n));
   CUB(cudaMalloc(&c->grad, rs * 16 * (size_t)n));
   if (opt.mesh_motion == AMM_EXPLICIT_W) {
     CUB(cudaMalloc(&c->wmesh, rs * 4 * (size_t)n));
@@ -408,6 +414,10 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
 
   CUB(cudaMalloc(&c->flux, rs * 4 * (size_t)nf));
   CUB(cudaMalloc(&c->fluxE, rs * (size_t)nf));
+  if (opt.regularize) {
+    CUB(cudaMalloc(&c->wcorr, rs * 4 * (size_t)n));
+    CUB(cudaMemsetAsync(c->wcorr, 0, rs * 4 * (size_t)n, c->stream));
+  }
   if (opt.entropy) {
     CUB(dalloc(&c->S, (size_t)n));
     CUB(cudaMalloc(&c->Aw, rs * (size_t)n));

@@ -4,7 +4,8 @@
 // Device layout (structure of arrays; "real" is double for the FP64 form and
 // float for the FP32 forms; vectors are always 3-component, z = 0 in 2D):
 //   per cell   Q      double, 5 planes of n: m, px, py, pz, E
-//              W      R4<real> {rho, vx, vy, vz}       P  real
+//              cw     2 x R4<real>: {rho, vx, vy, vz}, {P, s - r}: one
+//                     32-byte (FP32) record, so a gathered neighbour costs one sector
 //              grad   4 x R4<real>: {d rho (xyz), dP/dx}, {d vx, dP/dy},
 //                                   {d vy, dP/dz}, {d vz, 0}
 //              cgeo   R4<real> {1/V, s - r}   crad real R_i   cgeo64 R4<double> {V, s - r}
@@ -115,8 +116,7 @@ struct HydroView {
   double* dt_used;
   unsigned long long* cour_bits;
   double* Q;                  // 5 planes of n
-  R4<real>* W;
-  real* P;
+  R4<real>* cw;                // [n][2] {rho, v}, {P, s - r}
   R4<real>* grad;
   const R4<real>* wmesh;
   const R4<real>* cgeo;        // {1/V, s - r}
@@ -141,6 +141,10 @@ struct HydroView {
   const int* box_first_ctile; // [nboxes+1]
   DeviceStats* stats;
   unsigned* box_status;        // [nboxes] StatusBits of each box
+  // mesh-regularity correction (Sec. 4.1)
+  int regularize;
+  real eta_r, chi_r;
+  R4<real>* wcorr;             // [n] corrected generator velocities of the step
   // entropy switch (Sec. 3.5)
   int entropy;
   double mach_thresh, alpha_s;
@@ -193,14 +197,14 @@ struct amm_ctx {
   void* cgeo = nullptr;            // [n] R4<real> {1/V, s - r}
   void* crad = nullptr;            // [n] real, effective radius
   amm::R4<double>* cgeo64 = nullptr;
-  void* W = nullptr;
-  void* P = nullptr;
+  void* cw = nullptr;              // [n][2] R4<real> cell records
   void* grad = nullptr;
   void* wmesh = nullptr;
   void* flux = nullptr;
   void* fluxE = nullptr;
   unsigned long long* cour_bits = nullptr;
   unsigned* fmax_bits = nullptr;   // [nboxes][FMAX_STRIDE]
+  void* wcorr = nullptr;           // regularity correction: [n] R4<real>
   double* S = nullptr;             // entropy switch: [n] total entropy
   void* Aw = nullptr;              // [n] real
   void* gradA = nullptr;           // [n] R4<real>

@@ -90,7 +90,7 @@ __global__ void k_cast4(const R4<double>* in, R4<real>* out, size_t count) {
 // per-cell constants of the bulk type: 1/V, s - r and the effective radius
 // R = (3V/4pi)^(1/3) in 3D, (V/pi)^(1/2) in 2D (eq. EqnTiStep)
 template <typename real>
-__global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad, int n, int dim) {
+__global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad, R4<real>* cw, int n, int dim) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const R4<double> a = cg64[i];
@@ -100,6 +100,9 @@ __global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad,
   b.z = (real)a.z;
   b.w = (real)a.w;
   cg[i] = b;
+  // s - r in the second half of the cell record (P is written with the state)
+  b.x = (real)0;
+  cw[2 * (size_t)i + 1] = b;
   crad[i] = (real)((dim == 3) ? cbrt(3.0 * a.x / (4.0 * M_PI)) : sqrt(a.x / M_PI));
 }
 
@@ -141,14 +144,23 @@ __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr,
   }
 }
 
-// A10: r_i <- r_i + w_i dt, wrapped into the box; w from the mesh mode
+// A10: r_i <- r_i + w_i dt, wrapped into the box; w from the mesh mode, or
+// the regularity-corrected velocities of the last step (Sec. 4.1)
 __global__ void k_drift(const Tile* ctiles, int mode, int precision, double* gen, const double* box,
-                        const double* Q, int n, const void* wmesh, double dt) {
+                        const double* Q, int n, const void* wmesh, const void* wcorr, double dt) {
   const Tile t = ctiles[blockIdx.x];
   const int i = t.begin + (int)threadIdx.x;
   if (i >= t.end || mode == AMM_EULERIAN) return;
   double w[3];
-  if (mode == AMM_LAGRANGIAN) {
+  if (wcorr) {
+    if (precision == AMM_FP64) {
+      const R4<double> q = ((const R4<double>*)wcorr)[i];
+      w[0] = q.x; w[1] = q.y; w[2] = q.z;
+    } else {
+      const R4<float> q = ((const R4<float>*)wcorr)[i];
+      w[0] = q.x; w[1] = q.y; w[2] = q.z;
+    }
+  } else if (mode == AMM_LAGRANGIAN) {
     const double m = Q[i];
     for (int a = 0; a < 3; a++) w[a] = Q[(size_t)(a + 1) * n + i] / m;
   } else if (precision == AMM_FP64) {
@@ -189,15 +201,15 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
   const size_t nfg = 2 * (size_t)c->nf;
   const unsigned nbc = (unsigned)((c->n + 255) / 256);
   if (c->is_fp64()) {
-    k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad, (int)c->n,
-                                                       c->dim);
+    k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad,
+                                                       (R4<double>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<double><<<nbc, 256, 0, c->stream>>>(
         (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igA,
         (R4<double>*)c->igB, (double*)c->igz, c->nbr);
   } else {
     k_cast4<float><<<(unsigned)((nfg + 255) / 256), 256, 0, c->stream>>>(fg64, (R4<float>*)c->fgeo, nfg);
-    k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad, (int)c->n,
-                                                      c->dim);
+    k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad,
+                                                      (R4<float>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<float><<<nbc, 256, 0, c->stream>>>(
         (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igA,
         (R4<float>*)c->igB, (float*)c->igz, c->nbr);
@@ -213,7 +225,7 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
 
 cudaError_t launch_drift(amm_ctx* c, double dt) {
   k_drift<<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(c->ctiles, c->opt.mesh_motion, c->opt.precision, c->gen, c->box,
-                                                     c->Q, (int)c->n, c->wmesh, dt);
+                                                     c->Q, (int)c->n, c->wmesh, c->wcorr, dt);
   return cudaGetLastError();
 }
 

@@ -53,8 +53,8 @@ __device__ __forceinline__ real prims_from_Q(const HydroView<real>& v, int i, do
     P = v.gas.gm1 * ((float)(E - kin) * iV);
     w.x = mf * iV; w.y = (float)px * im; w.z = (float)py * im; w.w = (float)pz * im;
   }
-  v.W[i] = w;
-  v.P[i] = P;
+  v.cw[2 * (size_t)i] = w;
+  reinterpret_cast<real*>(v.cw + 2 * (size_t)i + 1)[0] = P;   // .x; s - r stays in .yzw
   return P;
 }
 
@@ -125,9 +125,9 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
   const bool valid = i < t.end;
   const int ii = valid ? i : t.begin;
-  const R4<real> Wi = v.W[ii];
+  const R4<real> Wi = v.cw[2 * (size_t)ii];
   real phi_i[NV];
-  phi_i[0] = Wi.x; phi_i[1] = Wi.y; phi_i[2] = Wi.z; phi_i[3] = Wi.w; phi_i[4] = v.P[ii];
+  phi_i[0] = Wi.x; phi_i[1] = Wi.y; phi_i[2] = Wi.z; phi_i[3] = Wi.w; phi_i[4] = v.cw[2 * (size_t)ii + 1].x;
   if constexpr (ENT) phi_i[5] = v.Aw[ii];
   const R4<real> cg = v.cgeo[ii];
   const int q0 = valid ? v.csr_off[ii] : 0;
@@ -160,9 +160,11 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
     if (q + G < q1) jn = v.nbr[q + G];
     const R4<real> a4 = v.igA[q];
     const R4<real> b4 = v.igB[q];
-    const R4<real> Wj = v.W[j];
+    // the neighbour's record: both halves lie in one 32-byte sector
+    const R4<real> Wj = v.cw[2 * (size_t)j];
+    const real Pj = v.cw[2 * (size_t)j + 1].x;
     real phi_j[NV];
-    phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = v.P[j];
+    phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = Pj;
     if constexpr (ENT) phi_j[5] = v.Aw[j];
     if (cold) {
       const real dx = Wj.y - wi3[0], dy = Wj.z - wi3[1], dz = Wj.w - wi3[2];
@@ -244,9 +246,25 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   if (valid && lane == 0) {
     real w3[3];
     mesh_velocity(v, i, Wi, w3);
-    const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
     const real cs = xsqrt(v.gas.g * phi_i[4] / Wi.x);
-    tc = v.crad[i] / (cs + xsqrt(dx * dx + dy * dy + dz * dz));
+    const real Ri = v.crad[i];
+    if (v.regularize) {
+      // Sec. 4.1, eq. (EqnShapeCorrVel): towards the centre of mass at the
+      // sound speed once the generator is off it by more than eta R_i
+      const real sx = cg.y, sy = cg.z, sz = cg.w;   // s - r
+      const real d = xsqrt(sx * sx + sy * sy + sz * sz);
+      const real er = v.eta_r * Ri;
+      const real ramp = d >= (real)1.1 * er ? (real)1 : (d >= (real)0.9 * er ? (d - (real)0.9 * er) / ((real)0.2 * er) : (real)0);
+      if (ramp > (real)0) {
+        const real f = v.chi_r * cs * ramp / d;
+        w3[0] += f * sx; w3[1] += f * sy; w3[2] += f * sz;
+      }
+      R4<real> wc;
+      wc.x = w3[0]; wc.y = w3[1]; wc.z = w3[2]; wc.w = (real)0;
+      v.wcorr[i] = wc;
+    }
+    const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
+    tc = Ri / (cs + xsqrt(dx * dx + dy * dy + dz * dz));
   }
   // block minimum, then one integer atomic per CTA (positive doubles order
   // like their bit patterns; min is order independent, so this is exact)
@@ -278,11 +296,11 @@ template <typename real, bool ENT>
 __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real hsgn, const real* n, real sep,
                                            const real* c, const real* w, real hdt, real* Wp, real* Wpp,
                                            real& Aface) {
-  const R4<real> Wi = v.W[i];
-  const real P = v.P[i];
+  const R4<real> Wi = v.cw[2 * (size_t)i];
+  const R4<real> cg = v.cw[2 * (size_t)i + 1];   // {P, s - r}
+  const real P = cg.x;
   const R4<real>* gp = v.grad + 4 * (size_t)i;
   const R4<real> g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3];
-  const R4<real> cg = v.cgeo[i];
   // f - s_i
   const real fx = hsgn * sep * n[0] + c[0] - cg.y;
   const real fy = hsgn * sep * n[1] + c[1] - cg.z;
@@ -343,8 +361,14 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
   real w[3] = {(real)0, (real)0, (real)0};
   if (v.mode != AMM_EULERIAN) {
     real wl[3], wr[3];
-    if (v.mode == AMM_LAGRANGIAN) {
-      const R4<real> a = v.W[lr.x], b = v.W[lr.y];
+    if (v.regularize) {
+      // the generators' velocities with the regularity correction, from the
+      // gradient kernel
+      const R4<real> a = v.wcorr[lr.x], b = v.wcorr[lr.y];
+      wl[0] = a.x; wl[1] = a.y; wl[2] = a.z;
+      wr[0] = b.x; wr[1] = b.y; wr[2] = b.z;
+    } else if (v.mode == AMM_LAGRANGIAN) {
+      const R4<real> a = v.cw[2 * (size_t)lr.x], b = v.cw[2 * (size_t)lr.y];
       wl[0] = a.y; wl[1] = a.z; wl[2] = a.w;
       wr[0] = b.y; wr[1] = b.z; wr[2] = b.w;
     } else {
@@ -846,13 +870,13 @@ __global__ void k_get_prims(HydroView<real> v, double* Wa, int dim) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   const int nv = dim + 2;
-  const R4<real> w = v.W[i];
+  const R4<real> w = v.cw[2 * (size_t)i];
   double* o = Wa + (size_t)v.cell_perm[i] * nv;
   o[0] = w.x;
   o[1] = w.y;
   o[2] = w.z;
   if (dim == 3) o[3] = w.w;
-  o[dim + 1] = v.P[i];
+  o[dim + 1] = v.cw[2 * (size_t)i + 1].x;
 }
 
 template <typename real>
@@ -926,8 +950,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.dt_used = c->dt_used;
   v.cour_bits = c->cour_bits;
   v.Q = c->Q;
-  v.W = (R4<real>*)c->W;
-  v.P = (real*)c->P;
+  v.cw = (R4<real>*)c->cw;
   v.grad = (R4<real>*)c->grad;
   v.wmesh = (const R4<real>*)c->wmesh;
   v.cgeo = (const R4<real>*)c->cgeo;
@@ -953,6 +976,10 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.box_first_ctile = c->box_first_ctile;
   v.stats = c->stats;
   v.box_status = c->box_status;
+  v.regularize = c->opt.regularize;
+  v.eta_r = (real)c->opt.eta;
+  v.chi_r = (real)c->opt.chi;
+  v.wcorr = (R4<real>*)c->wcorr;
   v.entropy = c->opt.entropy;
   v.mach_thresh = c->opt.mach_thresh;
   v.alpha_s = c->opt.alpha_s;
