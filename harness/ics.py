@@ -148,6 +148,36 @@ def lognormal_3d(n=192, jitter=0.2, seed=3, sigma=1.0, mach=3.0, gamma=5.0 / 3.0
                    dict(dims=dims, jitter=jitter, seed=seed, sigma=sigma, mach=mach))
 
 
+def gresho_profile(r):
+    """Azimuthal velocity and pressure of the triangle vortex (Sec. 8.5) at
+    radius r: v_phi = 5r, 2 - 5r, 0 on r < 0.2, 0.2 <= r < 0.4, r >= 0.4, and
+    P = 5 + 25/2 r^2, 9 + 25/2 r^2 - 20r + 4 ln(r/0.2), 3 + 4 ln 2 there, so
+    that dP/dr = rho v_phi^2 / r with rho = 1."""
+    r = np.asarray(r, np.float64)
+    vphi = np.where(r < 0.2, 5 * r, np.where(r < 0.4, 2 - 5 * r, 0.0))
+    mid = 9 + 12.5 * r * r - 20 * r + 4 * np.log(np.clip(r, 0.2, 0.4) / 0.2)
+    pres = np.where(r < 0.2, 5 + 12.5 * r * r, np.where(r < 0.4, mid, 3 + 4 * np.log(2.0)))
+    return vphi, pres
+
+
+def gresho_2d(n=40, jitter=0.0, seed=11, v_vortex=0.0, gamma=5.0 / 3.0, nthreads=0):
+    """Gresho's triangle vortex (Sec. 8.5): unit periodic box, rho = 1, the
+    profile of gresho_profile about (0.5, 0.5) sampled at the generators, plus
+    a uniform v_vortex along x; n x n generators (a Cartesian lattice unless
+    jittered)."""
+    rng = np.random.default_rng(seed)
+    box = np.array([1.0, 1.0])
+    pts = jittered_lattice((n, n), box, jitter, rng)
+    T = tessellate(pts, box, nthreads)
+    dx, dy = pts[:, 0] - 0.5, pts[:, 1] - 0.5
+    r = np.hypot(dx, dy)
+    vphi, pres = gresho_profile(r)
+    rs = np.where(r > 0, r, 1.0)
+    vel = np.column_stack([-vphi * dy / rs + v_vortex, vphi * dx / rs])
+    rho = np.ones(len(pts))
+    return Problem("gresho_2d", 2, gamma, T, rho, vel, pres, dict(n=n, jitter=jitter, seed=seed, v_vortex=v_vortex))
+
+
 def contact_3d(n=12, jitter=0.2, seed=7, v=(1.0, 0.5, -0.25), gamma=5.0 / 3.0):
     """Uniform velocity and pressure P=3/5, density 1 | 2 across x=0.5 (moving contact)."""
     rng = np.random.default_rng(seed)
