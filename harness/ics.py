@@ -178,6 +178,30 @@ def gresho_2d(n=40, jitter=0.0, seed=11, v_vortex=0.0, gamma=5.0 / 3.0, nthreads
     return Problem("gresho_2d", 2, gamma, T, rho, vel, pres, dict(n=n, jitter=jitter, seed=seed, v_vortex=v_vortex))
 
 
+def sedov(dim=3, n=64, jitter=0.0, seed=13, E=1.0, rho0=1.0, p0=1e-4, gamma=5.0 / 3.0, nthreads=0):
+    """Point explosion (Sec. 8.4): a cold uniform gas (rho0, p0) in the
+    periodic unit box, n^dim generators, with the energy E put into the one
+    cell whose generator lies nearest to the box centre; that generator is
+    the explosion centre (meta['centre'])."""
+    rng = np.random.default_rng(seed)
+    box = np.ones(dim)
+    pts = jittered_lattice((n,) * dim, box, jitter, rng)
+    T = tessellate(pts, box, nthreads)
+    c = int(np.argmin(np.sum((pts - 0.5) ** 2, axis=1)))
+    rho = np.full(len(pts), rho0)
+    vel = np.zeros((len(pts), dim))
+    pres = np.full(len(pts), p0)
+    pres[c] += (gamma - 1.0) * E / T.volume[c]
+    return Problem("sedov_%dd" % dim, dim, gamma, T, rho, vel, pres,
+                   dict(n=n, jitter=jitter, seed=seed, E=E, rho0=rho0, p0=p0, centre=pts[c].copy(), cell=c))
+
+
+def sedov_radius(t, E=1.0, rho0=1.0, beta=1.15):
+    """Shock radius of the self-similar blast wave, beta (E t^2 / rho0)^(1/5)
+    (3D; beta = 1.15 for gamma = 5/3, Sec. 8.4)."""
+    return beta * (E * t * t / rho0) ** 0.2
+
+
 def contact_3d(n=12, jitter=0.2, seed=7, v=(1.0, 0.5, -0.25), gamma=5.0 / 3.0):
     """Uniform velocity and pressure P=3/5, density 1 | 2 across x=0.5 (moving contact)."""
     rng = np.random.default_rng(seed)
