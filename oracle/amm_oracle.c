@@ -704,6 +704,8 @@ typedef struct {
   double* MF;  /* largest shock Mach number of the face's Riemann problem, or NULL */
   const double* Acell;  /* entropic function A = S/M per cell (with FS) */
   const double* gA;     /* its limited gradient [n][dim] (with FS) */
+  const long* list;     /* if set: the loop index selects face list[index] */
+  const double* hside;  /* if set: [nf][2] time of each side's prediction (else dt/2) */
 } flux_args;
 
 static void flux_face(const void* a, long k, int64_t* counters);
@@ -716,15 +718,17 @@ int ora_fluxes(int dim, long n, const double* W, const double* grad, const doubl
   (void)area;
   double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
   ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
-  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F, NULL, NULL, NULL, NULL};
+  const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F, NULL, NULL, NULL,
+                       NULL, NULL, NULL};
   const int64_t fails_before = counters[3];
   par_for(nf, flux_face, &A, counters);
   free(wface);
   return counters[3] > fails_before ? -1 : 0;
 }
 
-static void flux_face(const void* a, long k, int64_t* counters) {
+static void flux_face(const void* a, long idx, int64_t* counters) {
   const flux_args* A = (const flux_args*)a;
+  const long k = A->list ? A->list[idx] : idx;
   const int dim = A->dim;
   const double *W = A->W, *grad = A->grad, *gen = A->gen, *s = A->s, *wface = A->wface;
   const int32_t* cells = A->cells;
@@ -766,7 +770,9 @@ static void flux_face(const void* a, long k, int64_t* counters) {
         for (int d = 0; d < dim; d++) dv += gi[v * dim + d] * fs[d];
         Wpp[side][v] = Wp[side][v] + dv;
       }
-      /* 2b. half-step time prediction with A(W') at the cell centre */
+      /* 2b. half-step time prediction with A(W') at the cell centre (over
+       * hs = dt/2, or the side's own interval with individual steps) */
+      const double hs = A->hside ? A->hside[2 * k + side] : 0.5 * dt;
       const double rho = Wp[side][0], P = Wp[side][dim + 1];
       const double* vp = &Wp[side][1];
       double divv = 0.0, vgrad_rho = 0.0, vgrad_P = 0.0;
@@ -777,13 +783,13 @@ static void flux_face(const void* a, long k, int64_t* counters) {
       }
       const double drho_dt = -(vgrad_rho + rho * divv);
       const double dP_dt = -(gamma * P * divv + vgrad_P);
-      Wpp[side][0] += 0.5 * dt * drho_dt;
-      Wpp[side][dim + 1] += 0.5 * dt * dP_dt;
+      Wpp[side][0] += hs * drho_dt;
+      Wpp[side][dim + 1] += hs * dP_dt;
       for (int a = 0; a < dim; a++) {
         double adv = 0.0;
         for (int d = 0; d < dim; d++) adv += vp[d] * gi[(1 + a) * dim + d];
         const double dva_dt = -adv - gi[(dim + 1) * dim + a] / rho;
-        Wpp[side][1 + a] += 0.5 * dt * dva_dt;
+        Wpp[side][1 + a] += hs * dva_dt;
       }
       if (A->FS) {
         /* A reconstructed like the other primitives; it is advected,
@@ -794,7 +800,7 @@ static void flux_face(const void* a, long k, int64_t* counters) {
           dA += ga[d] * fs[d];
           vgrad_A += vp[d] * ga[d];
         }
-        App[side] = A->Acell[i] + dA + 0.5 * dt * (-vgrad_A);
+        App[side] = A->Acell[i] + dA + hs * (-vgrad_A);
         if (!(App[side] > 0.0)) App[side] = A->Acell[i];
       }
     }
@@ -870,7 +876,7 @@ int ora_fluxes_entropy(int dim, long n, const double* W, const double* grad, con
   double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
   ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wmesh, wface);
   const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, dt, tol, maxit, F, FS, MF,
-                       Acell, gA};
+                       Acell, gA, NULL, NULL};
   const int64_t fails_before = counters[3];
   par_for(nf, flux_face, &A, counters);
   free(wface);
@@ -1151,5 +1157,219 @@ int ora_step(int dim, long n, const double* gen, long nf, const int32_t* cells, 
   free(grad);
   free(wm);
   free(F);
+  return rc;
+}
+
+/* ------------------------- Sec. 7.1: the signal-speed time step criterion
+ * Eq. (EqnTiStepIndividual):
+ *   dt_i = C min(tau_i, R_i / (c_i + |v_i|)),
+ *   tau_i = min_{j != i} r_ij / (c_i + c_j - v_ij . r_ij / r_ij),
+ * on a static mesh (w = 0), with r_ij = r_i - r_j to the nearest periodic
+ * image of j (a component of exactly half the box keeps its sign),
+ * v_ij = v_i - v_j, and the pairs whose signal speed is not positive (they
+ * recede faster than sound can cross) left out.  The minimum is taken over
+ * all cells by brute force.  signal = 0 drops tau (eq. EqnTiStep alone).
+ * dt: [n]. */
+typedef struct {
+  int dim;
+  long n;
+  const double *gen, *box, *W, *V, *c;
+  double cfl;
+  int signal;
+  double* dt;
+} sig_args;
+
+static void sig_cell(const void* a, long i, int64_t* counters) {
+  (void)counters;
+  const sig_args* A = (const sig_args*)a;
+  const int dim = A->dim, nv = dim + 2;
+  const double* W = A->W;
+  const double R = (dim == 3) ? cbrt(3.0 * A->V[i] / (4.0 * M_PI)) : sqrt(A->V[i] / M_PI);
+  double v2 = 0.0;
+  for (int d = 0; d < dim; d++) v2 += W[i * nv + 1 + d] * W[i * nv + 1 + d];
+  const double tloc = R / (A->c[i] + sqrt(v2));
+  double tau = INFINITY;
+  if (A->signal) {
+    for (long j = 0; j < A->n; j++) {
+      if (j == i) continue;
+      double dx[3], r2 = 0.0, vr = 0.0;
+      for (int d = 0; d < dim; d++) {
+        const double L = A->box[d];
+        dx[d] = A->gen[i * dim + d] - A->gen[j * dim + d];
+        if (dx[d] > 0.5 * L)
+          dx[d] -= L;
+        else if (dx[d] < -0.5 * L)
+          dx[d] += L;
+        r2 += dx[d] * dx[d];
+      }
+      for (int d = 0; d < dim; d++) vr += (W[i * nv + 1 + d] - W[j * nv + 1 + d]) * dx[d];
+      const double r = sqrt(r2);
+      const double sig = A->c[i] + A->c[j] - vr / r;
+      if (sig > 0.0) {
+        const double t = r / sig;
+        if (t < tau) tau = t;
+      }
+    }
+  }
+  A->dt[i] = A->cfl * (tau < tloc ? tau : tloc);
+}
+
+void ora_signal_timestep(int dim, long n, const double* gen, const double* box, const double* W, const double* V,
+                         double gamma, double cfl, int signal, double* dt) {
+  const int nv = dim + 2;
+  double* c = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  for (long i = 0; i < n; i++) c[i] = sqrt(gamma * W[i * nv + dim + 1] / W[i * nv]);
+  const sig_args A = {dim, n, gen, box, W, V, c, cfl, signal, dt};
+  par_for(n, sig_cell, &A, NULL);
+  free(c);
+}
+
+/* --------------------------------- Sec. 7.2: individual time steps
+ * One cycle of length dt_max on a static mesh.  Cell time steps are
+ * dt_max / 2^b (bin b = 0..max_depth): the largest such step not above the
+ * cell's criterion dt_i.  Time runs in integer ticks of dt_max / 2^max_depth;
+ * a cell is active at tick t when its step divides t, i.e. a step of its
+ * starts there; every cell is active at t = 0.  At each tick with active
+ * cells:
+ *  1. active cells take their primitives from their conserved quantities,
+ *     then their limited gradients (neighbours that are not active enter
+ *     with the primitives of their own last activation) and their criterion
+ *     (signal-speed form if `signal`, with the other cells' current
+ *     primitives), and pick a bin: a smaller step is always allowed, a larger
+ *     one only where the larger step also starts at this tick;
+ *  2. every face with an active cell is integrated over the smaller step of
+ *     its two cells, from this tick; each side is predicted to the middle of
+ *     that interval from the primitives and gradients of its own last
+ *     activation (the half-step prediction over the time since then);
+ *  3. both cells of such a face exchange dt_f A F (pairwise, conservative);
+ *  4. time moves to the next tick at which a step starts, the next multiple
+ *     of the smallest step in use.
+ * On return every cell has completed its last step at dt_max.
+ * bins: [n] the bins in use at the end.  counters: [0..3] as in ora_fluxes,
+ * [4] sub-steps, [5] face flux evaluations, [6] cell activations.
+ * Returns 0, -1 if a Newton solve failed, -2 if a cell's criterion is below
+ * dt_max / 2^max_depth (1 <= max_depth <= 40). */
+static int64_t step_ticks(int max_depth, int b) { return (int64_t)1 << (max_depth - b); }
+
+int ora_advance_individual(int dim, long n, const double* gen, long nf, const int32_t* cells,
+                           const int8_t* shift, const double* area, const double* cen, const double* box,
+                           const double* V, const double* s, const double* Q, double gamma, double cfl,
+                           double dt_max, int max_depth, int signal, int limit, double tol, int maxit,
+                           double* Qnew, int32_t* bins, int64_t* counters) {
+  if (max_depth < 1 || max_depth > 40 || !(dt_max > 0.0)) return -2;
+  const int nv = dim + 2;
+  const int64_t T = (int64_t)1 << max_depth;
+  const double dtick = dt_max / (double)T;
+  double* W = (double*)calloc((size_t)(n * nv + 1), sizeof(double));
+  double* Wt = (double*)malloc(sizeof(double) * (size_t)(n * nv + 1));
+  double* grad = (double*)calloc((size_t)(n * nv * dim + 1), sizeof(double));
+  double* gt = (double*)malloc(sizeof(double) * (size_t)(n * nv * dim + 1));
+  double* dtc = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* F = (double*)malloc(sizeof(double) * (size_t)(nf * nv + 1));
+  double* hside = (double*)malloc(sizeof(double) * (size_t)(2 * nf + 1));
+  double* dtf = (double*)malloc(sizeof(double) * (size_t)(nf + 1));
+  double* wzero = (double*)calloc((size_t)(n * dim + 1), sizeof(double));
+  long* list = (long*)malloc(sizeof(long) * (size_t)(nf + 1));
+  char* act = (char*)malloc((size_t)(n + 1));
+  char* fact = (char*)malloc((size_t)(nf + 1));
+  double* wface = (double*)malloc(sizeof(double) * (size_t)(nf * dim + 1));
+  incidence I = build_incidence(n, nf, cells);
+  for (int c = 0; c < 7; c++) counters[c] = 0;
+  memcpy(Qnew, Q, sizeof(double) * (size_t)(n * nv));
+  for (long i = 0; i < n; i++) bins[i] = 0;
+  ora_face_velocities(dim, nf, cells, shift, gen, cen, box, wzero, wface); /* static mesh: all zero */
+  int rc = 0;
+  int64_t tick = 0;
+  while (tick < T && rc == 0) {
+    /* 1. activation */
+    for (long i = 0; i < n; i++) act[i] = (tick % step_ticks(max_depth, bins[i]) == 0);
+    ora_primitives(dim, n, Qnew, V, gamma, Wt);
+    for (long i = 0; i < n; i++)
+      if (act[i]) memcpy(W + i * nv, Wt + i * nv, sizeof(double) * (size_t)nv);
+    ora_gradients(dim, n, W, gen, V, s, nf, cells, shift, area, cen, box, limit, gt);
+    for (long i = 0; i < n; i++)
+      if (act[i]) memcpy(grad + i * nv * dim, gt + i * nv * dim, sizeof(double) * (size_t)(nv * dim));
+    ora_signal_timestep(dim, n, gen, box, W, V, gamma, cfl, signal, dtc);
+    for (long i = 0; i < n && rc == 0; i++) {
+      if (!act[i]) continue;
+      counters[6]++;
+      int b = 0;
+      double st = dt_max;
+      while (st > dtc[i]) {
+        st *= 0.5;
+        b++;
+      }
+      if (b > max_depth) {
+        rc = -2;
+        break;
+      }
+      if (tick == 0 || b >= bins[i]) {
+        bins[i] = b;
+      } else {
+        int nb = bins[i];
+        while (nb > b && tick % step_ticks(max_depth, nb - 1) == 0) nb--;
+        bins[i] = nb;
+      }
+    }
+    if (rc != 0) break;
+    /* 2. the faces of this tick */
+    long na = 0;
+    for (long k = 0; k < nf; k++) {
+      const long L = cells[2 * k], R = cells[2 * k + 1];
+      fact[k] = act[L] || act[R];
+      if (!fact[k]) continue;
+      const int64_t sL = step_ticks(max_depth, bins[L]), sR = step_ticks(max_depth, bins[R]);
+      const int64_t sf = sL < sR ? sL : sR;
+      dtf[k] = (double)sf * dtick;
+      /* middle of [tick, tick + sf] minus each side's last activation, in
+       * half ticks (integers, exact) */
+      const int64_t startL = tick - tick % sL, startR = tick - tick % sR;
+      hside[2 * k] = (double)(2 * tick + sf - 2 * startL) * (0.5 * dtick);
+      hside[2 * k + 1] = (double)(2 * tick + sf - 2 * startR) * (0.5 * dtick);
+      list[na++] = k;
+    }
+    const flux_args A = {dim, W, grad, gen, s, wface, cells, shift, cen, box, gamma, 0.0, tol, maxit, F,
+                         NULL, NULL, NULL, NULL, list, hside};
+    const int64_t fails_before = counters[3];
+    par_for(na, flux_face, &A, counters);
+    if (counters[3] > fails_before) rc = -1;
+    /* 3. pairwise exchange over the active faces */
+    for (long i = 0; i < n; i++) {
+      double sum[NV_MAX] = {0, 0, 0, 0, 0, 0};
+      int touched = 0;
+      for (long q = I.off[i]; q < I.off[i + 1]; q++) {
+        const long k = I.face[q];
+        if (!fact[k]) continue;
+        touched = 1;
+        const double sgn = (I.side[q] == 0) ? 1.0 : -1.0;
+        for (int v = 0; v < nv; v++) sum[v] += sgn * dtf[k] * area[k] * F[k * nv + v];
+      }
+      if (touched)
+        for (int v = 0; v < nv; v++) Qnew[i * nv + v] -= sum[v];
+    }
+    counters[4]++;
+    counters[5] += na;
+    /* 4. the next tick */
+    int64_t smin = T;
+    for (long i = 0; i < n; i++) {
+      const int64_t si = step_ticks(max_depth, bins[i]);
+      if (si < smin) smin = si;
+    }
+    tick = (tick / smin + 1) * smin;
+  }
+  free_incidence(&I);
+  free(W);
+  free(Wt);
+  free(grad);
+  free(gt);
+  free(dtc);
+  free(F);
+  free(hside);
+  free(dtf);
+  free(wzero);
+  free(list);
+  free(act);
+  free(fact);
+  free(wface);
   return rc;
 }

@@ -56,6 +56,11 @@ def lib():
                                        _I, _D, _I, _D, _D, _P, _P, _P, _P, _P]
         L.ora_shape_correction.restype = None
         L.ora_shape_correction.argtypes = [_I, _L, _P, _P, _P, _P, _P, _D, _D, _D, _P]
+        L.ora_signal_timestep.restype = None
+        L.ora_signal_timestep.argtypes = [_I, _L, _P, _P, _P, _P, _D, _D, _I, _P]
+        L.ora_advance_individual.restype = _I
+        L.ora_advance_individual.argtypes = [_I, _L, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _I, _I,
+                                             _I, _D, _I, _P, _P, _P]
         L.ora_set_threads.restype = None
         L.ora_set_threads.argtypes = [_I]
         L.ora_get_threads.restype = _I
@@ -269,3 +274,31 @@ def shape_correction(mesh, W, V, s, w, gamma, eta=0.25, chi=1.0):
     lib().ora_shape_correction(mesh.dim, mesh.n, mesh.gen.ctypes.data, s.ctypes.data, V.ctypes.data, W.ctypes.data,
                                w.ctypes.data, gamma, eta, chi, out.ctypes.data)
     return out
+
+
+def signal_timestep(mesh, W, V, gamma, cfl, signal=True):
+    """Per-cell time-step criterion of eq. (EqnTiStepIndividual) on a static
+    mesh (signal=False: eq. EqnTiStep alone).  [n]"""
+    W = _c(W, np.float64)
+    dt = np.empty(mesh.n)
+    lib().ora_signal_timestep(mesh.dim, mesh.n, mesh.gen.ctypes.data, mesh.box.ctypes.data, W.ctypes.data,
+                              _c(V, np.float64).ctypes.data, gamma, cfl, int(bool(signal)), dt.ctypes.data)
+    return dt
+
+
+def advance_individual(mesh, Q, gamma, cfl, dt_max, max_depth=30, signal=True, limit=True, tol=1e-12, maxit=64,
+                       geom=None):
+    """One cycle of individual power-of-two time steps of length dt_max on the
+    static mesh (Sec. 7.2).  Returns (Qnew, bins, counters[7], rc); counters:
+    fallback faces, vacuum faces, Newton iterations, Newton failures,
+    sub-steps, face flux evaluations, cell activations."""
+    V, s = geometry(mesh) if geom is None else geom
+    Q = _c(Q, np.float64)
+    Qn = np.empty_like(Q)
+    bins = np.zeros(mesh.n, np.int32)
+    cnt = np.zeros(7, np.int64)
+    rc = lib().ora_advance_individual(mesh.dim, mesh.n, mesh.gen.ctypes.data, mesh.nf, *mesh.args(), V.ctypes.data,
+                                      s.ctypes.data, Q.ctypes.data, gamma, cfl, dt_max, int(max_depth),
+                                      int(bool(signal)), int(bool(limit)), tol, maxit, Qn.ctypes.data,
+                                      bins.ctypes.data, cnt.ctypes.data)
+    return Qn, bins, cnt, rc

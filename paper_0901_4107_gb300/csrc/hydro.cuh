@@ -111,25 +111,24 @@ __device__ __forceinline__ void mesh_velocity(const HydroView<real>& v, int i, c
   }
 }
 
-// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads).
+// The limited gradient of cell i (valid) by the G lanes of its group: lane
+// `lane` takes the incidences lane, lane+G, ...; the results are stored.
+// ii is a valid cell index for the lanes of an invalid group (their loads
+// stay in bounds; nothing is stored).  Returns the cell's record through
+// Wi (rho, v) and Pi, and its geometry {1/V, s - r} through cg.
 // ENT: the entropy switch is on, so the entropic function A is a sixth
 // limited variable and the largest kinetic energy around the cell is kept
 // for the cold-flow criterion.
 template <typename real, int G, bool ENT = false>
-__device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
-  constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
+__device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int ii, bool valid, int lane, R4<real>& Wi,
+                                          real& Pi, R4<real>& cg) {
   constexpr int UNR = 1;                               // incidences in flight per lane
   constexpr int NV = ENT ? 6 : 5;
-  const Tile t = v.ctiles[wi / G];
-  const int lane = (int)threadIdx.x % G;
-  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
-  const bool valid = i < t.end;
-  const int ii = valid ? i : t.begin;
-  const R4<real> Wi = v.cw[2 * (size_t)ii];
+  Wi = v.cw[2 * (size_t)ii];
   real phi_i[NV];
   phi_i[0] = Wi.x; phi_i[1] = Wi.y; phi_i[2] = Wi.z; phi_i[3] = Wi.w; phi_i[4] = v.cw[2 * (size_t)ii + 1].x;
   if constexpr (ENT) phi_i[5] = v.Aw[ii];
-  const R4<real> cg = v.cgeo[ii];
+  cg = v.cgeo[ii];
   const int q0 = valid ? v.csr_off[ii] : 0;
   const int q1 = valid ? v.csr_off[ii + 1] : 0;
   real g[NV][3];
@@ -241,12 +240,28 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
     ekm = group_max<G>(ekm);
     if (valid && lane == 0) v.ekmax[i] = ekm;
   }
+  Pi = phi_i[4];
+}
+
+// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads):
+// gradients, limiter and the per-box Courant minimum
+template <typename real, int G, bool ENT = false>
+__device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
+  constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
+  const Tile t = v.ctiles[wi / G];
+  const int lane = (int)threadIdx.x % G;
+  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
+  const bool valid = i < t.end;
+  const int ii = valid ? i : t.begin;
+  R4<real> Wi, cg;
+  real Pi;
+  grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg);
   // Courant time R_i / (c_i + |v_i - w_i|), one lane per cell
   real tc = (real)3.0e38;
   if (valid && lane == 0) {
     real w3[3];
     mesh_velocity(v, i, Wi, w3);
-    const real cs = xsqrt(v.gas.g * phi_i[4] / Wi.x);
+    const real cs = xsqrt(v.gas.g * Pi / Wi.x);
     const real Ri = v.crad[i];
     if (v.regularize) {
       // Sec. 4.1, eq. (EqnShapeCorrVel): towards the centre of mass at the
