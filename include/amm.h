@@ -111,7 +111,8 @@ typedef struct amm_stats {
   int64_t guard_faces;       /* FP32 forms: faces whose Newton solve finished in FP64 */
   int64_t nonpositive_cells; /* cells left with m <= 0 or P <= 0 by an update */
   int32_t newton_max;        /* largest iteration count on one face */
-  uint32_t status;           /* bit 0 Newton cap, bit 1 non-positive cell, bit 2 wait timeout */
+  uint32_t status;           /* bit 0 Newton cap, bit 1 non-positive cell, bit 2 wait timeout,
+                                bit 3 time bin deeper than max_depth (amm_advance_individual) */
   int64_t newton_hist[16];   /* faces by Newton iteration count 0..14, 15 and more */
   int64_t entropy_kept;      /* cell updates that kept the advected entropy (amm_options.entropy) */
 } amm_stats;
@@ -200,6 +201,40 @@ int amm_step_boxes(amm_ctx* ctx, const double* dt);
  * fluxes, update), the time step staying on the device; replayed from a
  * captured CUDA graph when use_graph != 0.  Does not synchronise. */
 int amm_advance(amm_ctx* ctx, double cfl, int64_t nsteps, int use_graph);
+
+/* Counters of one cycle of individual time steps. */
+typedef struct amm_cycle_stats {
+  int64_t substeps;     /* ticks at which steps started */
+  int64_t face_fluxes;  /* face flux evaluations (a global step costs n_faces) */
+  int64_t activations;  /* cell steps begun */
+  int32_t deepest_bin;  /* largest bin in use during the cycle */
+  int32_t reserved;
+} amm_cycle_stats;
+
+/* Sec. 7.2: one cycle of individual power-of-two time steps of total length
+ * dt_max, on the static mesh (AMM_EULERIAN, one box, entropy switch off;
+ * otherwise AMM_ERR_INVALID_ARG).  Cell i steps by dt_max / 2^b_i, the largest
+ * such step not above its criterion dt_i = cfl min(tau_i, R_i/(c_i + |v_i|))
+ * of eq. (EqnTiStepIndividual) (signal_speed != 0; tau_i, the shortest
+ * signal travel time to any other cell, through the nearest periodic image,
+ * is found by a pruned walk over a uniform-grid pyramid of the box) or of
+ * eq. (EqnTiStep) alone (signal_speed == 0).  Time runs in ticks of
+ * dt_max / 2^max_depth (1 <= max_depth <= 40); at each tick where steps
+ * start, the starting cells take new primitives, limited gradients (the
+ * other cells enter with the primitives of their own last start) and bins (a
+ * shorter step is always allowed, a longer one is at most twice the current
+ * step and only where that step also starts at this tick); every face with a starting cell is integrated over the shorter
+ * step of its two cells, each side predicted from its own last start to the
+ * middle of that step, and both cells exchange dt_f A F.  Every cell ends the
+ * cycle synchronised, with fresh primitives.  stats may be NULL.
+ * AMM_ERR_NUMERIC if a criterion fell below dt_max / 2^max_depth (status bit
+ * 3) or a Newton solve or cell failed.  Synchronises once per tick. */
+int amm_advance_individual(amm_ctx* ctx, double cfl, double dt_max, int max_depth, int signal_speed,
+                           amm_cycle_stats* stats);
+
+/* The bins b_i in use at the end of the last cycle (step dt_max / 2^b_i),
+ * host [n_cells]. */
+int amm_get_bins(amm_ctx* ctx, int32_t* bins);
 
 /* A10 (Sec. 3, step 8): moves the stored generators by w_i * dt (wrapped into
  * the box) for the caller's next tessellation. */

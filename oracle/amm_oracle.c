@@ -1235,8 +1235,9 @@ void ora_signal_timestep(int dim, long n, const double* gen, const double* box, 
  *     then their limited gradients (neighbours that are not active enter
  *     with the primitives of their own last activation) and their criterion
  *     (signal-speed form if `signal`, with the other cells' current
- *     primitives), and pick a bin: a smaller step is always allowed, a larger
- *     one only where the larger step also starts at this tick;
+ *     primitives), and pick a bin: a smaller step is always allowed; a larger
+ *     one is at most twice the current step, and only where that step also
+ *     starts at this tick;
  *  2. every face with an active cell is integrated over the smaller step of
  *     its two cells, from this tick; each side is predicted to the middle of
  *     that interval from the primitives and gradients of its own last
@@ -1303,13 +1304,10 @@ int ora_advance_individual(int dim, long n, const double* gen, long nf, const in
         rc = -2;
         break;
       }
-      if (tick == 0 || b >= bins[i]) {
+      if (tick == 0 || b >= bins[i])
         bins[i] = b;
-      } else {
-        int nb = bins[i];
-        while (nb > b && tick % step_ticks(max_depth, nb - 1) == 0) nb--;
-        bins[i] = nb;
-      }
+      else if (tick % step_ticks(max_depth, bins[i] - 1) == 0)
+        bins[i] = bins[i] - 1; /* twice the step, where that step starts now */
     }
     if (rc != 0) break;
     /* 2. the faces of this tick */

@@ -53,6 +53,11 @@ class amm_stats(ctypes.Structure):
                 ("newton_hist", ctypes.c_int64 * 16), ("entropy_kept", ctypes.c_int64)]
 
 
+class amm_cycle_stats(ctypes.Structure):
+    _fields_ = [("substeps", ctypes.c_int64), ("face_fluxes", ctypes.c_int64), ("activations", ctypes.c_int64),
+                ("deepest_bin", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -73,6 +78,8 @@ _SIGS = {
     "amm_step": (_I, [_P, _D]),
     "amm_step_boxes": (_I, [_P, _P]),
     "amm_advance": (_I, [_P, _D, _I64, _I]),
+    "amm_advance_individual": (_I, [_P, _D, _D, _I, _I, _P]),
+    "amm_get_bins": (_I, [_P, _P]),
     "amm_drift": (_I, [_P, _D]),
     "amm_sync": (_I, [_P]),
     "amm_get_state": (_I, [_P, _P]),
@@ -274,6 +281,21 @@ def amm_step_boxes(ctx, dt):
 
 def amm_advance(ctx, cfl, nsteps=1, use_graph=True):
     _check(ctx, lib().amm_advance(ctx.handle, float(cfl), int(nsteps), int(bool(use_graph))))
+
+
+def amm_advance_individual(ctx, cfl, dt_max, max_depth=30, signal_speed=True):
+    """One cycle of individual time steps (Sec. 7.2); returns the cycle's
+    counters as a dict."""
+    st = amm_cycle_stats()
+    _check(ctx, lib().amm_advance_individual(ctx.handle, float(cfl), float(dt_max), int(max_depth),
+                                             int(bool(signal_speed)), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
+def amm_get_bins(ctx):
+    b = np.empty(ctx.n, np.int32)
+    _check(ctx, lib().amm_get_bins(ctx.handle, b.ctypes.data))
+    return b
 
 
 def amm_drift(ctx, dt):

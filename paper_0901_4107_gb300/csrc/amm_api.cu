@@ -49,7 +49,10 @@ void free_ctx(amm_ctx* c) {
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
                   c->ftiles, c->box_first_ctile, c->fgeo, c->igA, c->igB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad,
                   c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->wcorr, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
-                  c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter};
+                  c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter,
+                  c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
+                  c->ind_fdt, c->ind_hist, c->ind_slot_cell, c->ind_cell_slot, c->ind_leaf_off, c->ind_level_off,
+                  c->ind_rec, c->ind_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 
@@ -110,6 +113,8 @@ int check_status(amm_ctx* c) {
   cudaError_t e = cudaMemcpy(&s, c->stats, sizeof(s), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "read status");
   if (s.status & amm::ST_TIMEOUT) return fail(c, AMM_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (s.status & amm::ST_DEPTH)
+    return fail(c, AMM_ERR_NUMERIC, "a cell's time-step criterion fell below dt_max / 2^max_depth");
   if (s.status & (amm::ST_NEWTON_CAP | amm::ST_NONPOS)) {
     char buf[256];
     snprintf(buf, sizeof buf, "numeric failure: %llu Newton solves hit the cap, %llu cells non-positive",
@@ -691,6 +696,161 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
   c->grads_fresh = false;
   c->totals_fresh = true;
   c->have_step = true;
+  return AMM_OK;
+}
+
+// Buffers and the leaf-bucket order of the cells for individual time steps,
+// once per context (the mesh is static): a uniform grid of 2^L buckets per
+// axis over the box with L = floor(log2(n^(1/dim) / 2)) (about 2^dim cells per
+// bucket on a lattice), at least 1 and at most 7 (3D) or 9 (2D) levels below
+// the root.
+static int individual_setup(amm_ctx* c) {
+  const int64_t n = c->n, nf = c->nf;
+  const int dim = c->dim;
+  int L = (int)std::floor(std::log2(std::pow((double)n, 1.0 / dim) / 2.0));
+  L = std::max(1, std::min(L, dim == 3 ? 7 : 9));
+  c->ind_levels = L + 1;
+  c->ind_level_off_h.assign(c->ind_levels + 1, 0);
+  for (int l = 0; l < c->ind_levels; l++)
+    c->ind_level_off_h[l + 1] = c->ind_level_off_h[l] + (1 << (dim * l));
+  const int leaves = 1 << (dim * L);
+  const int side = 1 << L;
+  std::vector<double> g((size_t)n * 3);
+  CU(cudaMemcpy(g.data(), c->gen, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+  std::vector<int> bucket((size_t)n), off((size_t)leaves + 1, 0), slot_cell((size_t)n), cell_slot((size_t)n);
+  for (int64_t i = 0; i < n; i++) {
+    int ib[3] = {0, 0, 0};
+    for (int a = 0; a < dim; a++) {
+      const double L_a = c->box_h[a];
+      int q = (int)std::floor(g[3 * i + a] / L_a * side);
+      ib[a] = std::max(0, std::min(side - 1, q));
+    }
+    bucket[i] = (dim == 3) ? (ib[0] * side + ib[1]) * side + ib[2] : ib[0] * side + ib[1];
+    off[bucket[i] + 1]++;
+  }
+  for (int b = 0; b < leaves; b++) off[b + 1] += off[b];
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (int64_t i = 0; i < n; i++) {
+    const int s = fill[bucket[i]]++;
+    slot_cell[s] = (int)i;
+    cell_slot[i] = s;
+  }
+  CU(dalloc(&c->ind_bin, n));
+  CU(dalloc(&c->ind_act, n));
+  CU(dalloc(&c->ind_list, n));
+  CU(dalloc(&c->ind_flist, nf));
+  CU(dalloc(&c->ind_count, 4));
+  CU(dalloc(&c->ind_fstamp, nf));
+  CU(dalloc(&c->ind_cstamp, n));
+  CU(dalloc(&c->ind_fdt, nf));
+  CU(dalloc(&c->ind_hist, 64));
+  CU(dalloc(&c->ind_slot_cell, n));
+  CU(dalloc(&c->ind_cell_slot, n));
+  CU(dalloc(&c->ind_leaf_off, (size_t)leaves + 1));
+  CU(dalloc(&c->ind_level_off, (size_t)c->ind_levels + 1));
+  CU(dalloc((double4**)&c->ind_rec, 2 * (size_t)n));
+  CU(dalloc((double2**)&c->ind_node, (size_t)c->ind_level_off_h[c->ind_levels]));
+  CU(cudaMemcpy(c->ind_slot_cell, slot_cell.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->ind_cell_slot, cell_slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->ind_leaf_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->ind_level_off, c->ind_level_off_h.data(), sizeof(int) * c->ind_level_off_h.size(),
+                cudaMemcpyHostToDevice));
+  CU(cudaMemset(c->ind_fstamp, 0xff, sizeof(int) * nf));
+  CU(cudaMemset(c->ind_cstamp, 0xff, sizeof(int) * n));
+  c->ind_stamp = 0;
+  c->ind_ready = true;
+  return AMM_OK;
+}
+
+int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth, int signal_speed,
+                           amm_cycle_stats* stats) {
+  if (!c || !(cfl > 0.0) || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_depth < 1 || max_depth > 40)
+    return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
+  if (c->opt.mesh_motion != AMM_EULERIAN || c->nboxes != 1 || c->opt.entropy ||
+      c->opt.precision == AMM_FP32_LEARNED)
+    return fail(c, AMM_ERR_INVALID_ARG,
+                "individual time steps need a static mesh (AMM_EULERIAN), one box, no entropy switch and the "
+                "FP64 or FP32 form");
+  if (!c->ind_ready) {
+    const int rc = individual_setup(c);
+    if (rc != AMM_OK) return rc;
+  }
+  const int64_t n = c->n;
+  std::vector<unsigned> hist(64, 0u);
+  hist[0] = (unsigned)n;
+  CU(cudaMemsetAsync(c->ind_bin, 0, n, c->stream));
+  CU(cudaMemcpyAsync(c->ind_hist, hist.data(), sizeof(unsigned) * 64, cudaMemcpyHostToDevice, c->stream));
+  amm::IndView d;
+  d.n = (int)n;
+  d.nf = (int)c->nf;
+  d.dim = c->dim;
+  d.depth = max_depth;
+  d.levels = c->ind_levels;
+  d.signal = signal_speed ? 1 : 0;
+  d.cfl = cfl;
+  d.dtick = dt_max / (double)(1ll << max_depth);
+  d.gamma = c->gamma;
+  for (int a = 0; a < 3; a++) d.box[a] = c->box_h[a];
+  d.gen = c->gen;
+  d.bin = c->ind_bin;
+  d.act = c->ind_act;
+  d.list = c->ind_list;
+  d.flist = c->ind_flist;
+  d.count = c->ind_count;
+  d.fstamp = c->ind_fstamp;
+  d.cstamp = c->ind_cstamp;
+  d.fdt = c->ind_fdt;
+  d.hist = c->ind_hist;
+  d.slot_cell = c->ind_slot_cell;
+  d.cell_slot = c->ind_cell_slot;
+  d.leaf_off = c->ind_leaf_off;
+  d.rec = (double4*)c->ind_rec;
+  d.node = (double2*)c->ind_node;
+  d.level_off = c->ind_level_off;
+  amm_cycle_stats st;
+  std::memset(&st, 0, sizeof st);
+  const long long T = 1ll << max_depth;
+  long long tick = 0;
+  int counts[2];
+  while (tick < T) {
+    d.tick = tick;
+    d.stamp = ++c->ind_stamp;
+    CU(cudaMemsetAsync(c->ind_count, 0, sizeof(int) * 4, c->stream));
+    CU(dispatch(c, [&] { return amm::launch_individual_tick<double>(c, d); },
+                [&] { return amm::launch_individual_tick<float>(c, d); }));
+    CU(cudaMemcpyAsync(hist.data(), c->ind_hist, sizeof(unsigned) * 64, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(counts, c->ind_count, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    st.substeps++;
+    st.activations += counts[0];
+    st.face_fluxes += counts[1];
+    int deepest = 0;
+    for (int b = 0; b <= max_depth; b++)
+      if (hist[b]) deepest = b;
+    st.deepest_bin = std::max(st.deepest_bin, deepest);
+    const int rc = check_status(c);
+    if (rc != AMM_OK) return rc;
+    const long long smin = 1ll << (max_depth - deepest);
+    tick = (tick / smin + 1) * smin;
+  }
+  // every cell has finished its last step: fresh primitives of the new state
+  CU(dispatch(c, [&] { return amm::launch_primitives<double>(c); },
+              [&] { return amm::launch_primitives<float>(c); }));
+  c->grads_fresh = false;
+  c->totals_fresh = false;
+  c->have_step = true;
+  if (stats) *stats = st;
+  CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_get_bins(amm_ctx* c, int32_t* bins) {
+  if (!c || !bins) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
+  if (!c->ind_ready) return fail(c, AMM_ERR_NOT_READY, "no cycle of individual time steps yet");
+  std::vector<signed char> b((size_t)c->n);
+  CU(cudaMemcpyAsync(b.data(), c->ind_bin, c->n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < c->n; i++) bins[c->perm_h[i]] = b[i];
   return AMM_OK;
 }
 

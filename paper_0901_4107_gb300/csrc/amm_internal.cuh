@@ -51,7 +51,7 @@ struct Tile {
   int pad;
 };
 
-enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u };
+enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u, ST_DEPTH = 8u };
 
 // per-box largest |A F| slots: m, p (3), E, and the entropy flux
 constexpr int FMAX_STRIDE = 6;
@@ -160,6 +160,34 @@ struct HydroView {
   float* harvest;              // if set, the flux kernel records each face's Riemann inputs [nf][6]
 };
 
+// Device state of the individual-step integrator (amm_ctx::ind).
+struct IndView {
+  int n, nf, dim, depth;            // depth: max_depth D (ticks per cycle 2^D)
+  int levels;                       // pyramid levels 0..levels-1 (leaf = levels-1)
+  int signal;                       // 1: signal-speed criterion, 0: eq. (EqnTiStep) alone
+  double cfl, dtick, gamma;
+  double box[3];
+  const double* gen;                // [n][3] generators
+  long long tick;
+  int stamp;
+  signed char* bin;                 // [n]
+  unsigned char* act;               // [n] active at this tick
+  int* list;                        // [n] active cells
+  int* flist;                       // [nf] active faces
+  int* count;                       // [0] active cells, [1] active faces
+  int* fstamp;                      // [nf] stamp of the tick a face was last active
+  int* cstamp;                      // [n]  stamp of the tick a cell was last touched
+  double* fdt;                      // [nf] the active face's step
+  unsigned* hist;                   // [64] cells per bin
+  // pyramid: cells in leaf-bucket order
+  const int* slot_cell;             // [n] slot -> cell
+  const int* cell_slot;             // [n] cell -> slot
+  const int* leaf_off;              // [leaf buckets + 1]
+  double4* rec;                     // [n][2] by slot: {x, y, z, c}, {vx, vy, vz, |v|}
+  double2* node;                    // per level, per bucket: {max c, max |v|}
+  const int* level_off;             // [levels] first node of each level
+};
+
 }  // namespace amm
 
 struct amm_ctx {
@@ -240,6 +268,26 @@ struct amm_ctx {
   double graph_cfl = -1.0;
   bool graph_profiled = false;
   bool graph_persistent = false;
+  // individual time steps (allocated by the first amm_advance_individual)
+  bool ind_ready = false;
+  int ind_levels = 0;
+  int ind_stamp = 0;
+  std::vector<int> ind_level_off_h;
+  signed char* ind_bin = nullptr;
+  unsigned char* ind_act = nullptr;
+  int* ind_list = nullptr;
+  int* ind_flist = nullptr;
+  int* ind_count = nullptr;
+  int* ind_fstamp = nullptr;
+  int* ind_cstamp = nullptr;
+  double* ind_fdt = nullptr;
+  unsigned* ind_hist = nullptr;
+  int* ind_slot_cell = nullptr;
+  int* ind_cell_slot = nullptr;
+  int* ind_leaf_off = nullptr;
+  int* ind_level_off = nullptr;
+  void* ind_rec = nullptr;         // double4 [n][2]
+  void* ind_node = nullptr;        // double2 per pyramid node
   // per-kernel timing: events recorded between the kernels of a step
   bool profiling = false;
   cudaEvent_t prof_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -285,6 +333,10 @@ cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
 cudaError_t launch_step_persistent_learned(amm_ctx* c, double cfl);
 cudaError_t prepare_flux_learned();
+
+// hydro_f64.cu / hydro_f32.cu: one tick of individual time steps (Sec. 7.2)
+template <typename real>
+cudaError_t launch_individual_tick(amm_ctx* c, const IndView& d);
 
 // persistent_f32.cu / persistent_f64.cu: the whole step as one cooperative launch
 template <typename real>

@@ -101,7 +101,7 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
   __syncthreads();
   tc::fence_after_sync();
   FaceWork<float> f;
-  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, f);
+  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, s.hdt, f);
   // does this face's Riemann problem take the proposal?  Only strong
   // compression: the linearised estimate above PROPOSAL_GATE times the larger
   // pressure (which also places it in the two-shock branch of the guess)

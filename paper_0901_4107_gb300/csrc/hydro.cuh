@@ -359,8 +359,12 @@ struct FaceWork {
   int fallback;
 };
 
+// hdtL, hdtR: the time over which each side is predicted (half the step; with
+// individual time steps, the time from the side's last activation to the
+// middle of the face's step)
 template <typename real, bool ENT>
-__device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdt, FaceWork<real>& f) {
+__device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdtL, real hdtR,
+                                             FaceWork<real>& f) {
   f.k = k;
   f.valid = valid;
   const int2 lr = v.lr[k];
@@ -397,8 +401,8 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
   }
   real WpL[5], WpR[5];
   f.AL = f.AR = (real)0;
-  side_state<real, ENT>(v, lr.x, (real)0.5, n, sep, c, w, hdt, WpL, f.WppL, f.AL);
-  side_state<real, ENT>(v, lr.y, (real)-0.5, n, sep, c, w, hdt, WpR, f.WppR, f.AR);
+  side_state<real, ENT>(v, lr.x, (real)0.5, n, sep, c, w, hdtL, WpL, f.WppL, f.AL);
+  side_state<real, ENT>(v, lr.y, (real)-0.5, n, sep, c, w, hdtR, WpR, f.WppR, f.AR);
   f.fallback = 0;
   if (!(f.WppL[0] > (real)0) || !(f.WppL[4] > (real)0) || !(f.WppR[0] > (real)0) || !(f.WppR[4] > (real)0)) {
 #pragma unroll
@@ -566,7 +570,7 @@ __device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
   if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
   __syncthreads();
   FaceWork<real> f;
-  face_prepare<real, ENT>(v, valid ? k0 : t.begin, valid, s_hdt, f);
+  face_prepare<real, ENT>(v, valid ? k0 : t.begin, valid, s_hdt, s_hdt, f);
   face_finish<real, B, ENT>(v, f, t.box, min(B, t.end - first), false, (real)0);
 }
 
