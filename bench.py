@@ -23,6 +23,9 @@ Other workloads (--workload), each printed as one line of the same shape:
                 20 steps on the fixed tessellation, oracle on one step
   learned192    the turbulent field at 192^3 (Lagrangian): FP32 learned
                 proposal vs the standard starting value, Newton iterations
+  sedov64       the point explosion at 64^3 to t = 0.06: global steps vs
+                individual power-of-two time steps, FP32 and FP64 forms,
+                times to solution and face-flux counts
   ensemble      64 independent periodic boxes of 16^3..96^3 cells (log-
                 uniform), Mach 0.5..4, Eulerian, per-box Courant step, 50
                 steps, one persistent launch per step inside a CUDA graph
@@ -63,6 +66,9 @@ WORKLOADS = {
                  "(seed 5), each the config-2 field at rms Mach U[0.5,4], gamma=5/3, stationary mesh, per-box "
                  "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, one persistent "
                  "cooperative launch per step replayed from a CUDA graph"),
+    "sedov64": ("point explosion of Sec. 8.4: 64^3 Cartesian lattice in a periodic unit box, rho=1, P=1e-4, E=1 in "
+                "the cell nearest the centre, gamma=5/3, static mesh, to t=0.06; global Courant steps vs one cycle "
+                "of individual power-of-two time steps (Sec. 7.2, signal-speed criterion) per 0.01"),
 }
 
 
@@ -646,6 +652,105 @@ def bench_box(args, g, world, rank, local):
     return line
 
 
+def bench_sedov(args, g, world, rank, local):
+    """The point explosion to t = 0.06: global steps against individual time
+    steps, FP32 and FP64 forms; value = face fluxes per second of the FP32
+    individual-step run, with the times to solution beside it."""
+    import numpy as np
+    from harness import ics
+    amm, torch = g.amm, g.torch
+    n = args.n or 64
+    t_end, cycles = 0.06, 6
+    P = ics.sedov(3, n)
+    Q0 = P.conserved()
+    nf = P.n_faces
+
+    def radius_err(Q):
+        rho = Q[:, 0] / P.tess.volume
+        d = P.tess.points - P.meta["centre"]
+        d -= np.round(d)
+        r = np.linalg.norm(d, axis=1)
+        edges = np.arange(0.0, 0.8, 0.5 / n)
+        idx = np.digitize(r, edges)
+        prof = np.array([rho[idx == i].mean() if np.any(idx == i) else 0.0 for i in range(1, len(edges))])
+        i = int(np.argmax(prof))
+        return 0.5 * (edges[i] + edges[i + 1]) / ics.sedov_radius(t_end) - 1.0
+
+    def run_global(ctx):
+        amm.amm_set_state(ctx, Q0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, k = 0.0, 0
+        while t < t_end * (1 - 1e-14):
+            dt = min(float(amm.amm_timestep(ctx, CFL)[0]), t_end - t)
+            amm.amm_step(ctx, dt)
+            t += dt
+            k += 1
+        amm.amm_sync(ctx)
+        return time.perf_counter() - t0, {"steps": k, "face_fluxes": k * nf}
+
+    def run_individual(ctx):
+        amm.amm_set_state(ctx, Q0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = {"substeps": 0, "face_fluxes": 0, "activations": 0, "deepest_bin": 0}
+        for _ in range(cycles):
+            st = amm.amm_advance_individual(ctx, CFL, t_end / cycles, 30, True)
+            for key in ("substeps", "face_fluxes", "activations"):
+                tot[key] += st[key]
+            tot["deepest_bin"] = max(tot["deepest_bin"], st["deepest_bin"])
+        amm.amm_sync(ctx)
+        return time.perf_counter() - t0, tot
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    res = {}
+    for prec in ("fp32", "fp64"):
+        ctx = amm.create_from_mesh(P.tess, Q0, P.gamma, precision=prec, mesh_motion="eulerian",
+                                   stream=g.stream.cuda_stream)
+        amm.amm_advance_individual(ctx, CFL, t_end / cycles, 30, True)   # warm-up (setup, first launches)
+        res[prec] = {}
+        for name, fn in (("global", run_global), ("individual", run_individual)):
+            wall, cnt = fn(ctx)
+            cnt.update({"wall_s": wall, "radius_rel_err": radius_err(amm.amm_get_state(ctx))})
+            res[prec][name] = cnt
+        res[prec]["speedup"] = res[prec]["global"]["wall_s"] / res[prec]["individual"]["wall_s"]
+        res[prec]["flux_ratio"] = res[prec]["global"]["face_fluxes"] / res[prec]["individual"]["face_fluxes"]
+        amm.amm_destroy(ctx)
+    clocks = sampler.stop()
+    ind = res["fp32"]["individual"]
+    value = ind["face_fluxes"] / ind["wall_s"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": cycles, "warmup": 1,
+        "ms_per_step": 1e3 * ind["wall_s"] / cycles, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["sedov64"], "cells": P.n_cells, "faces": nf,
+                   "step": "one cycle of individual time steps of length 0.01 (host loop, one sync per tick)",
+                   "l2": "inputs and working set exceed L2 only in part: whole runs timed, not single steps"},
+        "time_to_solution": res,
+        "gpu_launches": 8 * ind["substeps"],
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        from oracle import oracle as O
+        cores = host_threads()
+        O.set_threads(cores)
+        M = O.Mesh(P.tess)
+        V, s_ = O.geometry(M)
+        t0 = time.perf_counter()
+        Q, k = Q0, 0
+        while k < 2:
+            W = O.primitives(M, Q, V, P.gamma)
+            dt = O.timestep(M, W, V, None, P.gamma, CFL)[0]
+            Q, _, _, rc = O.step(M, Q, P.gamma, "eulerian", dt=dt, geom=(V, s_))
+            k += 1
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k * nf / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "cpu": cpu_model(),
+                                "sample": "2 global oracle steps of the 64^3 explosion, %d host threads" % cores}
+    return line
+
+
 def reduce_replicas(torch, step_ms, faces, world, device):
     """N replicas, one per rank: the job's step time is the slowest rank's and
     its work the sum of the ranks' faces (weak scaling).  Returns (step_ms,
@@ -870,6 +975,8 @@ def main():
         line = bench_ensemble(args, g, world, rank, local)
     elif args.workload == "training":
         line = bench_train_workload(args, g, world, rank, local)
+    elif args.workload == "sedov64":
+        line = bench_sedov(args, g, world, rank, local)
     else:
         line = bench_box(args, g, world, rank, local)
     if rank == 0:

@@ -52,7 +52,7 @@ void free_ctx(amm_ctx* c) {
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
                   c->ind_fdt, c->ind_hist, c->ind_slot_cell, c->ind_cell_slot, c->ind_leaf_off, c->ind_level_off,
-                  c->ind_rec, c->ind_node};
+                  c->ind_rec, c->ind_rec32, c->ind_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 
@@ -749,6 +749,7 @@ static int individual_setup(amm_ctx* c) {
   CU(dalloc(&c->ind_leaf_off, (size_t)leaves + 1));
   CU(dalloc(&c->ind_level_off, (size_t)c->ind_levels + 1));
   CU(dalloc((double4**)&c->ind_rec, 2 * (size_t)n));
+  CU(dalloc((float4**)&c->ind_rec32, 2 * (size_t)n));
   CU(dalloc((double2**)&c->ind_node, (size_t)c->ind_level_off_h[c->ind_levels]));
   CU(cudaMemcpy(c->ind_slot_cell, slot_cell.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->ind_cell_slot, cell_slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
@@ -805,6 +806,7 @@ int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth,
   d.cell_slot = c->ind_cell_slot;
   d.leaf_off = c->ind_leaf_off;
   d.rec = (double4*)c->ind_rec;
+  d.rec32 = (float4*)c->ind_rec32;
   d.node = (double2*)c->ind_node;
   d.level_off = c->ind_level_off;
   amm_cycle_stats st;

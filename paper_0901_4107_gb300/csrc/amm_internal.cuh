@@ -184,7 +184,8 @@ struct IndView {
   const int* cell_slot;             // [n] cell -> slot
   const int* leaf_off;              // [leaf buckets + 1]
   double4* rec;                     // [n][2] by slot: {x, y, z, c}, {vx, vy, vz, |v|}
-  double2* node;                    // per level, per bucket: {max c, max |v|}
+  float4* rec32;                    // the same in FP32 (the walk's first screen)
+  double2* node;                    // per level, per bucket: {max (c + |v|) (-1: empty), its slot (int bits)}
   const int* level_off;             // [levels] first node of each level
 };
 
@@ -287,6 +288,7 @@ struct amm_ctx {
   int* ind_leaf_off = nullptr;
   int* ind_level_off = nullptr;
   void* ind_rec = nullptr;         // double4 [n][2]
+  void* ind_rec32 = nullptr;       // float4 [n][2]
   void* ind_node = nullptr;        // double2 per pyramid node
   // per-kernel timing: events recorded between the kernels of a step
   bool profiling = false;

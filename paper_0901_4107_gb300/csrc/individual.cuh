@@ -10,7 +10,7 @@
 //  k_ind_activate  active cells: W from Q (cw), their walk record, the
 //                  active-cell list                          (Sec. 7.2)
 //  k_ind_leaf / k_ind_up   per bucket of a uniform-grid pyramid over the
-//                  box: the largest sound speed and speed of its cells
+//                  box: the largest c + |v| of its cells and that cell
 //  k_ind_grad      active cells: limited gradients (eq. eqngrad2), the
 //                  neighbours entering with their stored W   (Sec. 3.1)
 //  k_ind_bins      active cells: dt_i = C min(tau_i, R_i/(c_i+|v_i|)) by a
@@ -83,6 +83,8 @@ __global__ void k_ind_activate(HydroView<real> v, IndView d) {
     const int s = d.cell_slot[i];
     d.rec[2 * (size_t)s] = a;
     d.rec[2 * (size_t)s + 1] = b;
+    d.rec32[2 * (size_t)s] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
+    d.rec32[2 * (size_t)s + 1] = make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
   }
 }
 
@@ -92,13 +94,19 @@ static __global__ void k_ind_leaf(IndView d) {
   const int leaves = (d.dim == 3) ? (1 << (3 * (d.levels - 1))) : (1 << (2 * (d.levels - 1)));
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= leaves) return;
-  double cm = 0.0, vm = 0.0;
+  // FP32 records, the maximum raised by 1e-5 to cover their rounding (the
+  // bounds are used in FP32 only); an empty bucket keeps -1 and a valid slot
+  float m = -1.0f;
+  int arg = d.leaf_off[b];
   for (int s = d.leaf_off[b]; s < d.leaf_off[b + 1]; s++) {
-    const double4 a = d.rec[2 * (size_t)s], c = d.rec[2 * (size_t)s + 1];
-    cm = fmax(cm, a.w);
-    vm = fmax(vm, c.w);
+    const float4 a = d.rec32[2 * (size_t)s], c = d.rec32[2 * (size_t)s + 1];
+    if (a.w + c.w > m) {
+      m = a.w + c.w;
+      arg = s;
+    }
   }
-  d.node[nb + b] = make_double2(cm, vm);
+  if (arg >= d.n) arg = d.n - 1;
+  d.node[nb + b] = make_double2(m >= 0.0f ? (double)m * (1.0 + 1e-5) : -1.0, __longlong_as_double((long long)arg));
 }
 
 // all coarser levels by one CTA, finest first
@@ -115,15 +123,14 @@ static __global__ void __launch_bounds__(1024) k_ind_up(IndView d) {
         ix = b / side; iy = b % side; iz = 0;
       }
       const int cs = side * 2;
-      double cm = 0.0, vm = 0.0;
+      double2 m = make_double2(-2.0, 0.0);
       for (int q = 0; q < ch; q++) {
         const int jx = 2 * ix + (q & 1), jy = 2 * iy + ((q >> 1) & 1), jz = 2 * iz + ((q >> 2) & 1);
         const int cb = (d.dim == 3) ? (jx * cs + jy) * cs + jz : jx * cs + jy;
         const double2 c = d.node[d.level_off[l + 1] + cb];
-        cm = fmax(cm, c.x);
-        vm = fmax(vm, c.y);
+        if (c.x > m.x) m = c;
       }
-      d.node[d.level_off[l] + b] = make_double2(cm, vm);
+      d.node[d.level_off[l] + b] = m;
     }
     __syncthreads();
   }
@@ -147,103 +154,230 @@ __global__ void __launch_bounds__(CELL_TILE) k_ind_grad(HydroView<real> v, IndVi
 
 // ------------------------------------------------------ bins of active cells
 // Periodic distance from x to the interval [lo, lo + h] on a circle of length L.
-__device__ __forceinline__ double interval_gap(double x, double lo, double h, double L) {
-  const double hi = lo + h;
-  if (x >= lo && x <= hi) return 0.0;
-  const double a = (x < lo) ? lo - x : x - hi;     // direct
-  const double b = (x < lo) ? x + L - hi : lo + L - x;  // through the periodic boundary
+__device__ __forceinline__ float interval_gap(float x, float lo, float h, float L) {
+  const float hi = lo + h;
+  if (x >= lo && x <= hi) return 0.0f;
+  const float a = (x < lo) ? lo - x : x - hi;       // direct
+  const float b = (x < lo) ? x + L - hi : lo + L - x;  // through the periodic boundary
   return a < b ? a : b;
 }
 
+// r_ij / (c_i + c_j - v_ij . r_ij / r_ij) for the cell in walk slot s, to the
+// nearest periodic image; +inf where the signal speed is not positive
+__device__ __forceinline__ double pair_tau(const IndView& d, int s, double xi, double yi, double zi, double ci,
+                                          double vx, double vy, double vz) {
+  const double4 a = d.rec[2 * (size_t)s], c = d.rec[2 * (size_t)s + 1];
+  double dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+  if (dx > 0.5 * d.box[0]) dx -= d.box[0]; else if (dx < -0.5 * d.box[0]) dx += d.box[0];
+  if (dy > 0.5 * d.box[1]) dy -= d.box[1]; else if (dy < -0.5 * d.box[1]) dy += d.box[1];
+  if (d.dim == 3) {
+    if (dz > 0.5 * d.box[2]) dz -= d.box[2]; else if (dz < -0.5 * d.box[2]) dz += d.box[2];
+  } else {
+    dz = 0.0;
+  }
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  const double vr = (vx - c.x) * dx + (vy - c.y) * dy + (vz - c.z) * dz;
+  const double sig = ci + a.w - vr / r;
+  return sig > 0.0 ? r / sig : INFINITY;
+}
+
+__device__ __forceinline__ double warp_min_d(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y < x ? y : x;
+  }
+  return x;
+}
+
+// FP32 bounds of a pair's value r / sig, from the FP32 records, with margins
+// well above the FP32 rounding of the positions (eps, absolute), of the
+// speeds (relative 1e-5) and of the direction of r_ij (|v_ij| eps / r):
+// lo <= the FP64 value <= hi; lo = 0 where the pair is too close to bound,
+// lo = hi = +inf where the signal speed cannot be positive.
+__device__ __forceinline__ void pair_tau_bounds(const IndView& d, int s, float xi, float yi, float zi, float ci,
+                                                float vx, float vy, float vz, float eps, float& lo, float& hi) {
+  const float4 a = d.rec32[2 * (size_t)s], c = d.rec32[2 * (size_t)s + 1];
+  float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+  const float bx = (float)d.box[0], by = (float)d.box[1], bz = (float)d.box[2];
+  if (dx > 0.5f * bx) dx -= bx; else if (dx < -0.5f * bx) dx += bx;
+  if (dy > 0.5f * by) dy -= by; else if (dy < -0.5f * by) dy += by;
+  if (d.dim == 3) {
+    if (dz > 0.5f * bz) dz -= bz; else if (dz < -0.5f * bz) dz += bz;
+  } else {
+    dz = 0.0f;
+  }
+  const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float rlo = r - 4.0f * eps, rhi = r + 4.0f * eps;
+  lo = 0.0f;
+  hi = INFINITY;
+  if (!(rlo > 0.0f)) return;
+  const float ux = vx - c.x, uy = vy - c.y, uz = vz - c.z;
+  const float du = sqrtf(ux * ux + uy * uy + uz * uz);
+  const float sig = ci + a.w - (ux * dx + uy * dy + uz * dz) / r;
+  const float m = 1e-5f * (ci + a.w + du) + 2.0f * du * (4.0f * eps) / rlo;
+  const float sig_hi = sig + m, sig_lo = sig - m;
+  if (!(sig_hi > 0.0f)) {
+    lo = INFINITY;
+    return;
+  }
+  lo = rlo / sig_hi * (1.0f - 1e-5f);
+  if (sig_lo > 0.0f) hi = rhi / sig_lo * (1.0f + 1e-5f);
+}
+
+// One warp per active cell: dt_i = C min(tau_i, R_i / (c_i + |v_i|)) of
+// eq. (EqnTiStepIndividual), then the cell's bin.
+//
+// tau_i = min_j r_ij / (c_i + c_j - v_ij . r_ij / r_ij) by a walk of the
+// pyramid.  A bucket cannot hold a pair below gap / (c_i + |v_i| + max_j
+// (c_j + |v_j|)) (r >= gap, signal speed <= c_i + c_j + |v_i - v_j|); the walk
+// skips buckets whose bound is not below the current minimum and opens the
+// others smallest bound first (the children of a bucket are pushed in order).
+// The bounds and a first screen of the pairs run in FP32 with conservative
+// margins; every pair that passes the screen is evaluated exactly in FP64, so
+// the minimum is the FP64 minimum over all pairs.  It starts from the pairs
+// with the fastest cell of every bucket of a coarse level (any pair value
+// bounds the minimum).  The lanes split a bucket's children, a leaf's cells
+// and the seeds; the stack is per warp in shared memory.
+constexpr int BINS_WARPS = 4;
+
 template <typename real>
-__global__ void k_ind_bins(HydroView<real> v, IndView d) {
+__global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v, IndView d) {
+  __shared__ unsigned s_node[BINS_WARPS][64];
+  __shared__ float s_lb[BINS_WARPS][64];
+  const int lane = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
   const int count = d.count[0];
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+  const float eps = 1e-6f * (float)fmax(d.box[0], fmax(d.box[1], d.box[2]));
+  for (int idx = blockIdx.x * BINS_WARPS + w; idx < count; idx += gridDim.x * BINS_WARPS) {
     const int i = d.list[idx];
-    const R4<real> w = v.cw[2 * (size_t)i];
-    const double rho = (double)w.x, P = (double)v.cw[2 * (size_t)i + 1].x;
-    const double vx = (double)w.y, vy = (double)w.z, vz = (double)w.w;
+    const R4<real> wi = v.cw[2 * (size_t)i];
+    const double rho = (double)wi.x, P = (double)v.cw[2 * (size_t)i + 1].x;
+    const double vx = (double)wi.y, vy = (double)wi.z, vz = (double)wi.w;
     const double ci = sqrt(d.gamma * P / rho);
     const double si = sqrt(vx * vx + vy * vy + vz * vz);
     double cur = (double)v.crad[i] / (ci + si);           // R_i / (c_i + |v_i|)
     if (d.signal) {
-      // tau_i = min_j r_ij / (c_i + c_j - v_ij . r_ij / r_ij): a depth-first
-      // walk of the pyramid that skips a bucket when even its closest point,
-      // its largest sound speed and speed cannot beat the current minimum
-      // (r >= gap, signal speed <= c_i + c_max + |v_i| + v_max); the skip test
-      // keeps a relative margin of 1e-12, so rounding never drops a pair
-      // that would lower the minimum
       const double* gi = d.gen + 3 * (size_t)i;
       const double xi = gi[0], yi = gi[1], zi = gi[2];
-      unsigned stack[64];
-      int sp = 0;
-      stack[sp++] = 0u;                                    // level 0, bucket 0
+      const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
+      const float cf = (float)ci, vxf = (float)vx, vyf = (float)vy, vzf = (float)vz;
+      const float minef = (float)(ci + si);
+      const float bx = (float)d.box[0], by = (float)d.box[1], bz = (float)d.box[2];
+      // the pruning bound curf >= the FP64 minimum: the local term, and upper
+      // bounds of the pairs with the fastest cell of each coarse bucket
+      float curf = (float)cur * (1.0f + 1e-5f);
+      {
+        const int ls = d.levels - 1 < 2 ? d.levels - 1 : 2;
+        float t = INFINITY;
+        for (int b = d.level_off[ls] + lane; b < d.level_off[ls + 1]; b += 32) {
+          const int s = (int)__double_as_longlong(d.node[b].y);
+          if (d.slot_cell[s] != i) {
+            float lo, hi;
+            pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
+            t = hi < t ? hi : t;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
+        curf = t < curf ? t : curf;
+      }
       const int leaf = d.levels - 1;
+      const int nch = (d.dim == 3) ? 8 : 4;
+      int sp = 1;
+      if (lane == 0) {
+        s_node[w][0] = 0u;                                 // level 0, bucket 0
+        s_lb[w][0] = 0.0f;
+      }
+      __syncwarp();
       while (sp > 0) {
-        const unsigned e = stack[--sp];
+        sp--;
+        const unsigned e = s_node[w][sp];
+        const float lbe = s_lb[w][sp];
+        __syncwarp();
+        if (!(lbe < curf)) continue;
         const int l = (int)(e >> 27);
         const int ix = (int)((e >> 18) & 511u), iy = (int)((e >> 9) & 511u), iz = (int)(e & 511u);
         const int side = 1 << l;
-        const int b = (d.dim == 3) ? (ix * side + iy) * side + iz : ix * side + iy;
-        if (l > 0) {
-          const double hx = d.box[0] / side, hy = d.box[1] / side, hz = d.box[2] / side;
-          const double gx = interval_gap(xi, ix * hx, hx, d.box[0]);
-          const double gy = interval_gap(yi, iy * hy, hy, d.box[1]);
-          const double gz = (d.dim == 3) ? interval_gap(zi, iz * hz, hz, d.box[2]) : 0.0;
-          const double2 nd = d.node[d.level_off[l] + b];
-          const double bound = ci + nd.x + si + nd.y;
-          if (!(sqrt(gx * gx + gy * gy + gz * gz) < cur * bound * (1.0 + 1e-12))) continue;
-        }
         if (l == leaf) {
-          for (int s = d.leaf_off[b]; s < d.leaf_off[b + 1]; s++) {
+          const int b = (d.dim == 3) ? (ix * side + iy) * side + iz : ix * side + iy;
+          double t = INFINITY;
+          for (int s = d.leaf_off[b] + lane; s < d.leaf_off[b + 1]; s += 32) {
             if (d.slot_cell[s] == i) continue;
-            const double4 a = d.rec[2 * (size_t)s], c = d.rec[2 * (size_t)s + 1];
-            double dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
-            if (dx > 0.5 * d.box[0]) dx -= d.box[0]; else if (dx < -0.5 * d.box[0]) dx += d.box[0];
-            if (dy > 0.5 * d.box[1]) dy -= d.box[1]; else if (dy < -0.5 * d.box[1]) dy += d.box[1];
-            if (d.dim == 3) {
-              if (dz > 0.5 * d.box[2]) dz -= d.box[2]; else if (dz < -0.5 * d.box[2]) dz += d.box[2];
-            } else {
-              dz = 0.0;
-            }
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            const double vr = (vx - c.x) * dx + (vy - c.y) * dy + (vz - c.z) * dz;
-            const double sig = ci + a.w - vr / r;
-            if (sig > 0.0) {
-              const double t = r / sig;
-              cur = t < cur ? t : cur;
+            float lo, hi;
+            pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
+            if (lo < curf) {
+              const double ts = pair_tau(d, s, xi, yi, zi, ci, vx, vy, vz);
+              t = ts < t ? ts : t;
             }
           }
-        } else {
-          const int nch = (d.dim == 3) ? 8 : 4;
-          for (int q = 0; q < nch && sp < 64; q++) {
-            const unsigned jx = 2u * ix + (q & 1), jy = 2u * iy + ((q >> 1) & 1), jz = 2u * iz + ((q >> 2) & 1);
-            stack[sp++] = ((unsigned)(l + 1) << 27) | (jx << 18) | (jy << 9) | jz;
+          t = warp_min_d(t);
+          if (t < cur) {
+            cur = t;
+            const float cu = (float)cur * (1.0f + 1e-5f);
+            curf = cu < curf ? cu : curf;
+          }
+          continue;
+        }
+        // lane q < nch takes child q: its bound, then its rank among the
+        // surviving children (larger bound deeper in the stack)
+        const int cside = side * 2;
+        bool ok = false;
+        float lb = 0.0f;
+        unsigned ce = 0u;
+        if (lane < nch) {
+          const unsigned jx = 2u * ix + (lane & 1), jy = 2u * iy + ((lane >> 1) & 1), jz = 2u * iz + ((lane >> 2) & 1);
+          const int cb = (d.dim == 3) ? ((int)jx * cside + (int)jy) * cside + (int)jz : (int)jx * cside + (int)jy;
+          const double fast = d.node[d.level_off[l + 1] + cb].x;
+          if (fast >= 0.0) {
+            const float hx = bx / (float)cside, hy = by / (float)cside, hz = bz / (float)cside;
+            const float gx = interval_gap(xf, (float)jx * hx, hx, bx);
+            const float gy = interval_gap(yf, (float)jy * hy, hy, by);
+            const float gz = (d.dim == 3) ? interval_gap(zf, (float)jz * hz, hz, bz) : 0.0f;
+            const float gap = fmaxf(sqrtf(gx * gx + gy * gy + gz * gz) - eps, 0.0f);
+            lb = gap / ((minef + (float)fast) * (1.0f + 1e-5f));
+            ok = lb < curf;
+            ce = ((unsigned)(l + 1) << 27) | (jx << 18) | (jy << 9) | jz;
           }
         }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        int rank = 0;
+        for (int q = 0; q < nch; q++) {
+          const float lq = __shfl_sync(0xffffffffu, lb, q);
+          if (((okm >> q) & 1u) && (lq > lb || (lq == lb && q < lane))) rank++;
+        }
+        const int nok = __popc(okm);
+        if (ok && sp + rank < 64) {
+          s_node[w][sp + rank] = ce;
+          s_lb[w][sp + rank] = lb;
+        }
+        __syncwarp();
+        sp = sp + nok < 64 ? sp + nok : 64;
       }
     }
-    const double dti = d.cfl * cur;
-    // the largest step dt_max 2^-b not above dt_i
-    int b = 0;
-    double st = d.dtick * (double)(1ll << d.depth);
-    while (st > dti && b <= d.depth) {
-      st *= 0.5;
-      b++;
+    if (lane == 0) {
+      const double dti = d.cfl * cur;
+      // the largest step dt_max 2^-b not above dt_i
+      int b = 0;
+      double st = d.dtick * (double)(1ll << d.depth);
+      while (st > dti && b <= d.depth) {
+        st *= 0.5;
+        b++;
+      }
+      if (b > d.depth) {
+        atomicOr(&v.stats->status, (unsigned)ST_DEPTH);
+        b = d.depth;
+      }
+      const int old = d.bin[i];
+      int nb = b;
+      if (d.tick != 0 && b < old)   // at most twice the step, where that step starts now
+        nb = ((d.tick & (step_ticks(d.depth, old - 1) - 1)) == 0) ? old - 1 : old;
+      if (nb != old) {
+        atomicSub(d.hist + old, 1u);
+        atomicAdd(d.hist + nb, 1u);
+        d.bin[i] = (signed char)nb;
+      }
     }
-    if (b > d.depth) {
-      atomicOr(&v.stats->status, (unsigned)ST_DEPTH);
-      b = d.depth;
-    }
-    const int old = d.bin[i];
-    int nb = b;
-    if (d.tick != 0 && b < old)   // at most twice the step, where that step starts now
-      nb = ((d.tick & (step_ticks(d.depth, old - 1) - 1)) == 0) ? old - 1 : old;
-    if (nb != old) {
-      atomicSub(d.hist + old, 1u);
-      atomicAdd(d.hist + nb, 1u);
-      d.bin[i] = (signed char)nb;
-    }
+    __syncwarp();
   }
 }
 
@@ -325,9 +459,9 @@ cudaError_t launch_individual_tick(amm_ctx* c, const IndView& d) {
   // list kernels: a fixed grid strides over the list, whose length only the
   // device knows
   const int sms = 152;
-  const int g_grad = nblk(c->n, CELL_TILE / 4), g_bins = nblk(c->n, 128), g_flux = nblk(c->nf, 128);
+  const int g_grad = nblk(c->n, CELL_TILE / 4), g_bins = nblk(c->n, BINS_WARPS), g_flux = nblk(c->nf, 128);
   k_ind_grad<real, 4><<<g_grad < sms * 8 ? g_grad : sms * 8, CELL_TILE, 0, c->stream>>>(v, d);
-  k_ind_bins<real><<<g_bins < sms * 8 ? g_bins : sms * 8, 128, 0, c->stream>>>(v, d);
+  k_ind_bins<real><<<g_bins < sms * 16 ? g_bins : sms * 16, 32 * BINS_WARPS, 0, c->stream>>>(v, d);
   k_ind_faces<real><<<nblk(c->nf, 256), 256, 0, c->stream>>>(v, d);
   k_ind_flux<real, 128><<<g_flux < sms * 8 ? g_flux : sms * 8, 128, 0, c->stream>>>(v, d);
   k_ind_update<real><<<grid_c, 256, 0, c->stream>>>(v, d);
