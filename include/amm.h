@@ -112,7 +112,8 @@ typedef struct amm_stats {
   int64_t nonpositive_cells; /* cells left with m <= 0 or P <= 0 by an update */
   int32_t newton_max;        /* largest iteration count on one face */
   uint32_t status;           /* bit 0 Newton cap, bit 1 non-positive cell, bit 2 wait timeout,
-                                bit 3 time bin deeper than max_depth (amm_advance_individual) */
+                                bit 3 time bin deeper than max_depth, bit 4 more than 2^20 ticks in
+                                one cycle (amm_advance_individual) */
   int64_t newton_hist[16];   /* faces by Newton iteration count 0..14, 15 and more */
   int64_t entropy_kept;      /* cell updates that kept the advected entropy (amm_options.entropy) */
 } amm_stats;
@@ -226,11 +227,21 @@ typedef struct amm_cycle_stats {
  * step and only where that step also starts at this tick); every face with a starting cell is integrated over the shorter
  * step of its two cells, each side predicted from its own last start to the
  * middle of that step, and both cells exchange dt_f A F.  Every cell ends the
- * cycle synchronised, with fresh primitives.  stats may be NULL.
- * AMM_ERR_NUMERIC if a criterion fell below dt_max / 2^max_depth (status bit
- * 3) or a Newton solve or cell failed.  Synchronises once per tick. */
+ * cycle synchronised, with fresh primitives.  The cycle runs on the device
+ * as one CUDA graph (a while loop over the ticks; captured again when cfl,
+ * dt_max, max_depth or signal_speed change) and synchronises once, at its
+ * end.  stats may be NULL.  AMM_ERR_NUMERIC if a criterion fell below
+ * dt_max / 2^max_depth (status bit 3), the cycle needed more than 2^20 ticks
+ * (bit 4) or a Newton solve or cell failed; the loop stops at the first
+ * failing tick. */
 int amm_advance_individual(amm_ctx* ctx, double cfl, double dt_max, int max_depth, int signal_speed,
                            amm_cycle_stats* stats);
+
+/* enable != 0: amm_advance_individual launches each tick from the host and
+ * synchronises once per tick instead of running the cycle as one graph (the
+ * same kernels and results; for profilers that cannot look inside graphs
+ * with conditional nodes).  Default 0. */
+int amm_individual_host_loop(amm_ctx* ctx, int enable);
 
 /* The bins b_i in use at the end of the last cycle (step dt_max / 2^b_i),
  * host [n_cells]. */

@@ -80,6 +80,7 @@ _SIGS = {
     "amm_advance": (_I, [_P, _D, _I64, _I]),
     "amm_advance_individual": (_I, [_P, _D, _D, _I, _I, _P]),
     "amm_get_bins": (_I, [_P, _P]),
+    "amm_individual_host_loop": (_I, [_P, _I]),
     "amm_drift": (_I, [_P, _D]),
     "amm_sync": (_I, [_P]),
     "amm_get_state": (_I, [_P, _P]),
@@ -290,6 +291,10 @@ def amm_advance_individual(ctx, cfl, dt_max, max_depth=30, signal_speed=True):
     _check(ctx, lib().amm_advance_individual(ctx.handle, float(cfl), float(dt_max), int(max_depth),
                                              int(bool(signal_speed)), ctypes.byref(st)))
     return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
+def amm_individual_host_loop(ctx, enable=True):
+    _check(ctx, lib().amm_individual_host_loop(ctx.handle, int(bool(enable))))
 
 
 def amm_get_bins(ctx):

@@ -44,6 +44,8 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_ctx(amm_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->ind_exec) cudaGraphExecDestroy(c->ind_exec);
+  if (c->ind_graph) cudaGraphDestroy(c->ind_graph);
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
@@ -52,7 +54,7 @@ void free_ctx(amm_ctx* c) {
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
                   c->ind_fdt, c->ind_hist, c->ind_slot_cell, c->ind_cell_slot, c->ind_leaf_off, c->ind_level_off,
-                  c->ind_rec, c->ind_rec32, c->ind_node};
+                  c->ind_rec, c->ind_rec32, c->ind_node, c->ind_loop};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 
@@ -115,6 +117,8 @@ int check_status(amm_ctx* c) {
   if (s.status & amm::ST_TIMEOUT) return fail(c, AMM_ERR_TIMEOUT, "a bounded device wait timed out");
   if (s.status & amm::ST_DEPTH)
     return fail(c, AMM_ERR_NUMERIC, "a cell's time-step criterion fell below dt_max / 2^max_depth");
+  if (s.status & amm::ST_SUBSTEPS)
+    return fail(c, AMM_ERR_NUMERIC, "a cycle of individual time steps exceeded 2^20 sub-steps");
   if (s.status & (amm::ST_NEWTON_CAP | amm::ST_NONPOS)) {
     char buf[256];
     snprintf(buf, sizeof buf, "numeric failure: %llu Newton solves hit the cap, %llu cells non-positive",
@@ -750,7 +754,8 @@ static int individual_setup(amm_ctx* c) {
   CU(dalloc(&c->ind_level_off, (size_t)c->ind_levels + 1));
   CU(dalloc((double4**)&c->ind_rec, 2 * (size_t)n));
   CU(dalloc((float4**)&c->ind_rec32, 2 * (size_t)n));
-  CU(dalloc((double2**)&c->ind_node, (size_t)c->ind_level_off_h[c->ind_levels]));
+  CU(dalloc(&c->ind_loop, 1));
+  CU(dalloc((float2**)&c->ind_node, (size_t)c->ind_level_off_h[c->ind_levels]));
   CU(cudaMemcpy(c->ind_slot_cell, slot_cell.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->ind_cell_slot, cell_slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->ind_leaf_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
@@ -780,7 +785,14 @@ int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth,
   std::vector<unsigned> hist(64, 0u);
   hist[0] = (unsigned)n;
   CU(cudaMemsetAsync(c->ind_bin, 0, n, c->stream));
+  CU(cudaMemsetAsync(c->ind_count, 0, sizeof(int) * 4, c->stream));
   CU(cudaMemcpyAsync(c->ind_hist, hist.data(), sizeof(unsigned) * 64, cudaMemcpyHostToDevice, c->stream));
+  amm::IndLoop L0;
+  std::memset(&L0, 0, sizeof L0);
+  L0.T = 1ll << max_depth;
+  L0.stamp = ++c->ind_stamp;
+  L0.max_substeps = 1ull << 20;
+  CU(cudaMemcpyAsync(c->ind_loop, &L0, sizeof L0, cudaMemcpyHostToDevice, c->stream));
   amm::IndView d;
   d.n = (int)n;
   d.nf = (int)c->nf;
@@ -793,6 +805,9 @@ int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth,
   d.gamma = c->gamma;
   for (int a = 0; a < 3; a++) d.box[a] = c->box_h[a];
   d.gen = c->gen;
+  d.loop = c->ind_loop;
+  d.handle = 0;
+  d.in_graph = 0;
   d.bin = c->ind_bin;
   d.act = c->ind_act;
   d.list = c->ind_list;
@@ -805,36 +820,70 @@ int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth,
   d.slot_cell = c->ind_slot_cell;
   d.cell_slot = c->ind_cell_slot;
   d.leaf_off = c->ind_leaf_off;
+  d.stats = c->stats;
   d.rec = (double4*)c->ind_rec;
   d.rec32 = (float4*)c->ind_rec32;
-  d.node = (double2*)c->ind_node;
+  d.node = (float2*)c->ind_node;
   d.level_off = c->ind_level_off;
-  amm_cycle_stats st;
-  std::memset(&st, 0, sizeof st);
-  const long long T = 1ll << max_depth;
-  long long tick = 0;
-  int counts[2];
-  while (tick < T) {
-    d.tick = tick;
-    d.stamp = ++c->ind_stamp;
-    CU(cudaMemsetAsync(c->ind_count, 0, sizeof(int) * 4, c->stream));
-    CU(dispatch(c, [&] { return amm::launch_individual_tick<double>(c, d); },
-                [&] { return amm::launch_individual_tick<float>(c, d); }));
-    CU(cudaMemcpyAsync(hist.data(), c->ind_hist, sizeof(unsigned) * 64, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(counts, c->ind_count, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+  auto one_tick = [&]() -> cudaError_t {
+    cudaError_t e = dispatch(c, [&] { return amm::launch_individual_tick<double>(c, d); },
+                             [&] { return amm::launch_individual_tick<float>(c, d); });
+    return e == cudaSuccess ? amm::launch_individual_next(c, d) : e;
+  };
+  amm::IndLoop L;
+  if (c->ind_host_loop) {
+    // one launch sequence and one synchronisation per tick
+    do {
+      CU(one_tick());
+      CU(cudaMemcpyAsync(&L, c->ind_loop, sizeof L, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    } while (L.go);
+  } else {
+    const double key[4] = {cfl, dt_max, (double)max_depth, signal_speed ? 1.0 : 0.0};
+    if (!c->ind_exec || std::memcmp(key, c->ind_key, sizeof key) != 0) {
+      // the cycle as one graph: a while node whose body is one tick, the
+      // last kernel of which sets the condition
+      if (c->ind_exec) cudaGraphExecDestroy(c->ind_exec);
+      if (c->ind_graph) cudaGraphDestroy(c->ind_graph);
+      c->ind_exec = nullptr;
+      c->ind_graph = nullptr;
+      CU(cudaGraphCreate(&c->ind_graph, 0));
+      cudaGraphConditionalHandle h;
+      CU(cudaGraphConditionalHandleCreate(&h, c->ind_graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CU(cudaGraphAddNode(&node, c->ind_graph, nullptr, nullptr, 0, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      d.handle = h;
+      d.in_graph = 1;
+      CU(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      const cudaError_t e = one_tick();
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
+      if (e != cudaSuccess) return cuda_fail(c, e, "capture of one tick");
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+      CU(cudaGraphInstantiate(&c->ind_exec, c->ind_graph, 0));
+      std::memcpy(c->ind_key, key, sizeof key);
+    }
+    CU(cudaGraphLaunch(c->ind_exec, c->stream));
+    CU(cudaMemcpyAsync(&L, c->ind_loop, sizeof L, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    st.substeps++;
-    st.activations += counts[0];
-    st.face_fluxes += counts[1];
-    int deepest = 0;
-    for (int b = 0; b <= max_depth; b++)
-      if (hist[b]) deepest = b;
-    st.deepest_bin = std::max(st.deepest_bin, deepest);
+  }
+  c->ind_stamp = L.stamp;
+  {
     const int rc = check_status(c);
     if (rc != AMM_OK) return rc;
-    const long long smin = 1ll << (max_depth - deepest);
-    tick = (tick / smin + 1) * smin;
   }
+  amm_cycle_stats st;
+  std::memset(&st, 0, sizeof st);
+  st.substeps = (int64_t)L.substeps;
+  st.face_fluxes = (int64_t)L.face_fluxes;
+  st.activations = (int64_t)L.activations;
+  st.deepest_bin = L.deepest;
   // every cell has finished its last step: fresh primitives of the new state
   CU(dispatch(c, [&] { return amm::launch_primitives<double>(c); },
               [&] { return amm::launch_primitives<float>(c); }));
@@ -843,6 +892,12 @@ int amm_advance_individual(amm_ctx* c, double cfl, double dt_max, int max_depth,
   c->have_step = true;
   if (stats) *stats = st;
   CU(cudaStreamSynchronize(c->stream));
+  return AMM_OK;
+}
+
+int amm_individual_host_loop(amm_ctx* c, int enable) {
+  if (!c) return AMM_ERR_INVALID_ARG;
+  c->ind_host_loop = enable != 0;
   return AMM_OK;
 }
 

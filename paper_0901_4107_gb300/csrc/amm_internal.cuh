@@ -51,7 +51,7 @@ struct Tile {
   int pad;
 };
 
-enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u, ST_DEPTH = 8u };
+enum StatusBits : unsigned { ST_NEWTON_CAP = 1u, ST_NONPOS = 2u, ST_TIMEOUT = 4u, ST_DEPTH = 8u, ST_SUBSTEPS = 16u };
 
 // per-box largest |A F| slots: m, p (3), E, and the entropy flux
 constexpr int FMAX_STRIDE = 6;
@@ -160,6 +160,19 @@ struct HydroView {
   float* harvest;              // if set, the flux kernel records each face's Riemann inputs [nf][6]
 };
 
+// Loop state of a cycle of individual time steps, in device memory: the
+// cycle runs as a while loop inside one CUDA graph, and k_ind_next advances it.
+struct IndLoop {
+  long long tick;                   // current tick
+  long long T;                      // ticks per cycle, 2^depth
+  int stamp;                        // stamp of the current tick
+  int deepest;                      // largest bin in use during the cycle
+  int go;                           // 1 while the cycle continues
+  int pad;
+  unsigned long long substeps, face_fluxes, activations;
+  unsigned long long max_substeps;  // the loop stops (ST_SUBSTEPS) beyond this
+};
+
 // Device state of the individual-step integrator (amm_ctx::ind).
 struct IndView {
   int n, nf, dim, depth;            // depth: max_depth D (ticks per cycle 2^D)
@@ -168,8 +181,9 @@ struct IndView {
   double cfl, dtick, gamma;
   double box[3];
   const double* gen;                // [n][3] generators
-  long long tick;
-  int stamp;
+  IndLoop* loop;                    // tick, stamp and counters
+  cudaGraphConditionalHandle handle;  // the cycle's while condition
+  int in_graph;                     // 1: k_ind_next sets the condition; 0: the host loops
   signed char* bin;                 // [n]
   unsigned char* act;               // [n] active at this tick
   int* list;                        // [n] active cells
@@ -183,9 +197,10 @@ struct IndView {
   const int* slot_cell;             // [n] slot -> cell
   const int* cell_slot;             // [n] cell -> slot
   const int* leaf_off;              // [leaf buckets + 1]
+  DeviceStats* stats;               // status bits (the loop stops on a failure)
   double4* rec;                     // [n][2] by slot: {x, y, z, c}, {vx, vy, vz, |v|}
   float4* rec32;                    // the same in FP32 (the walk's first screen)
-  double2* node;                    // per level, per bucket: {max (c + |v|) (-1: empty), its slot (int bits)}
+  float2* node;                     // per level, per bucket: {max (c + |v|) (-1: empty), its slot (int bits)}
   const int* level_off;             // [levels] first node of each level
 };
 
@@ -289,7 +304,12 @@ struct amm_ctx {
   int* ind_level_off = nullptr;
   void* ind_rec = nullptr;         // double4 [n][2]
   void* ind_rec32 = nullptr;       // float4 [n][2]
-  void* ind_node = nullptr;        // double2 per pyramid node
+  void* ind_node = nullptr;        // float2 per pyramid node
+  amm::IndLoop* ind_loop = nullptr;
+  cudaGraph_t ind_graph = nullptr;  // the cycle as one graph (while loop over ticks)
+  cudaGraphExec_t ind_exec = nullptr;
+  double ind_key[4] = {0, 0, 0, 0}; // cfl, dt_max, max_depth, signal of the captured graph
+  bool ind_host_loop = false;       // ticks launched by the host (for profilers)
   // per-kernel timing: events recorded between the kernels of a step
   bool profiling = false;
   cudaEvent_t prof_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -339,6 +359,7 @@ cudaError_t prepare_flux_learned();
 // hydro_f64.cu / hydro_f32.cu: one tick of individual time steps (Sec. 7.2)
 template <typename real>
 cudaError_t launch_individual_tick(amm_ctx* c, const IndView& d);
+cudaError_t launch_individual_next(amm_ctx* c, const IndView& d);
 
 // persistent_f32.cu / persistent_f64.cu: the whole step as one cooperative launch
 template <typename real>

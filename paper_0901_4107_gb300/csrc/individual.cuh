@@ -54,8 +54,9 @@ template <typename real>
 __global__ void k_ind_activate(HydroView<real> v, IndView d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = i < d.n;
+  const long long tick = d.loop->tick;
   bool active = false;
-  if (in) active = (d.tick & (step_ticks(d.depth, d.bin[i]) - 1)) == 0;
+  if (in) active = (tick & (step_ticks(d.depth, d.bin[i]) - 1)) == 0;
   const int at = warp_append(d.count, active);
   if (!in) return;
   d.act[i] = active ? 1 : 0;
@@ -106,7 +107,7 @@ static __global__ void k_ind_leaf(IndView d) {
     }
   }
   if (arg >= d.n) arg = d.n - 1;
-  d.node[nb + b] = make_double2(m >= 0.0f ? (double)m * (1.0 + 1e-5) : -1.0, __longlong_as_double((long long)arg));
+  d.node[nb + b] = make_float2(m >= 0.0f ? m * (1.0f + 1e-5f) : -1.0f, __int_as_float(arg));
 }
 
 // all coarser levels by one CTA, finest first
@@ -123,11 +124,11 @@ static __global__ void __launch_bounds__(1024) k_ind_up(IndView d) {
         ix = b / side; iy = b % side; iz = 0;
       }
       const int cs = side * 2;
-      double2 m = make_double2(-2.0, 0.0);
+      float2 m = make_float2(-2.0f, 0.0f);
       for (int q = 0; q < ch; q++) {
         const int jx = 2 * ix + (q & 1), jy = 2 * iy + ((q >> 1) & 1), jz = 2 * iz + ((q >> 2) & 1);
         const int cb = (d.dim == 3) ? (jx * cs + jy) * cs + jz : jx * cs + jy;
-        const double2 c = d.node[d.level_off[l + 1] + cb];
+        const float2 c = d.node[d.level_off[l + 1] + cb];
         if (c.x > m.x) m = c;
       }
       d.node[d.level_off[l] + b] = m;
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
   __shared__ float s_lb[BINS_WARPS][64];
   const int lane = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
   const int count = d.count[0];
+  const long long tick = d.loop->tick;
   const float eps = 1e-6f * (float)fmax(d.box[0], fmax(d.box[1], d.box[2]));
   for (int idx = blockIdx.x * BINS_WARPS + w; idx < count; idx += gridDim.x * BINS_WARPS) {
     const int i = d.list[idx];
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
         const int ls = d.levels - 1 < 2 ? d.levels - 1 : 2;
         float t = INFINITY;
         for (int b = d.level_off[ls] + lane; b < d.level_off[ls + 1]; b += 32) {
-          const int s = (int)__double_as_longlong(d.node[b].y);
+          const int s = __float_as_int(d.node[b].y);
           if (d.slot_cell[s] != i) {
             float lo, hi;
             pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
@@ -283,6 +285,50 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
       }
       const int leaf = d.levels - 1;
       const int nch = (d.dim == 3) ? 8 : 4;
+      // the cell's own leaf bucket and its 3^dim - 1 neighbours first (lane q
+      // takes neighbour q), so the walk below starts from a tight bound and
+      // skips them
+      const int lside = 1 << leaf;
+      const int lx = min(lside - 1, max(0, (int)floorf(xf / bx * (float)lside)));
+      const int ly = min(lside - 1, max(0, (int)floorf(yf / by * (float)lside)));
+      const int lz = (d.dim == 3) ? min(lside - 1, max(0, (int)floorf(zf / bz * (float)lside))) : 0;
+      {
+        const int nnb = (d.dim == 3) ? 27 : 9;
+        int s0 = 0, s1 = 0;
+        if (lane < nnb) {
+          const int qx = lane % 3 - 1, qy = (lane / 3) % 3 - 1, qz = (d.dim == 3) ? lane / 9 - 1 : 0;
+          const int jx = (lx + qx + lside) % lside, jy = (ly + qy + lside) % lside, jz = (lz + qz + lside) % lside;
+          const int b = (d.dim == 3) ? (jx * lside + jy) * lside + jz : jx * lside + jy;
+          s0 = d.leaf_off[b];
+          s1 = d.leaf_off[b + 1];
+        }
+        float hmin = INFINITY;
+        for (int s = s0; s < s1; s++) {
+          if (d.slot_cell[s] == i) continue;
+          float lo, hi;
+          pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
+          hmin = hi < hmin ? hi : hmin;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+        curf = hmin < curf ? hmin : curf;
+        double t = INFINITY;
+        for (int s = s0; s < s1; s++) {
+          if (d.slot_cell[s] == i) continue;
+          float lo, hi;
+          pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
+          if (lo < curf) {
+            const double ts = pair_tau(d, s, xi, yi, zi, ci, vx, vy, vz);
+            t = ts < t ? ts : t;
+          }
+        }
+        t = warp_min_d(t);
+        if (t < cur) {
+          cur = t;
+          const float cu = (float)cur * (1.0f + 1e-5f);
+          curf = cu < curf ? cu : curf;
+        }
+      }
       int sp = 1;
       if (lane == 0) {
         s_node[w][0] = 0u;                                 // level 0, bucket 0
@@ -300,8 +346,21 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
         const int side = 1 << l;
         if (l == leaf) {
           const int b = (d.dim == 3) ? (ix * side + iy) * side + iz : ix * side + iy;
+          // first the FP32 upper bounds tighten curf, then only the pairs
+          // whose lower bound stays below it are evaluated in FP64
+          const int s0 = d.leaf_off[b], s1 = d.leaf_off[b + 1];
+          float hmin = INFINITY;
+          for (int s = s0 + lane; s < s1; s += 32) {
+            if (d.slot_cell[s] == i) continue;
+            float lo, hi;
+            pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
+            hmin = hi < hmin ? hi : hmin;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+          curf = hmin < curf ? hmin : curf;
           double t = INFINITY;
-          for (int s = d.leaf_off[b] + lane; s < d.leaf_off[b + 1]; s += 32) {
+          for (int s = s0 + lane; s < s1; s += 32) {
             if (d.slot_cell[s] == i) continue;
             float lo, hi;
             pair_tau_bounds(d, s, xf, yf, zf, cf, vxf, vyf, vzf, eps, lo, hi);
@@ -327,14 +386,20 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
         if (lane < nch) {
           const unsigned jx = 2u * ix + (lane & 1), jy = 2u * iy + ((lane >> 1) & 1), jz = 2u * iz + ((lane >> 2) & 1);
           const int cb = (d.dim == 3) ? ((int)jx * cside + (int)jy) * cside + (int)jz : (int)jx * cside + (int)jy;
-          const double fast = d.node[d.level_off[l + 1] + cb].x;
-          if (fast >= 0.0) {
+          const float fast = d.node[d.level_off[l + 1] + cb].x;
+          bool near = false;
+          if (l + 1 == leaf) {
+            // a leaf of the neighbourhood scanned above (periodic distance <= 1)
+            const int ax = abs((int)jx - lx), ay = abs((int)jy - ly), az = abs((int)jz - lz);
+            near = min(ax, lside - ax) <= 1 && min(ay, lside - ay) <= 1 && min(az, lside - az) <= 1;
+          }
+          if (fast >= 0.0f && !near) {
             const float hx = bx / (float)cside, hy = by / (float)cside, hz = bz / (float)cside;
             const float gx = interval_gap(xf, (float)jx * hx, hx, bx);
             const float gy = interval_gap(yf, (float)jy * hy, hy, by);
             const float gz = (d.dim == 3) ? interval_gap(zf, (float)jz * hz, hz, bz) : 0.0f;
             const float gap = fmaxf(sqrtf(gx * gx + gy * gy + gz * gz) - eps, 0.0f);
-            lb = gap / ((minef + (float)fast) * (1.0f + 1e-5f));
+            lb = gap / ((minef + fast) * (1.0f + 1e-5f));
             ok = lb < curf;
             ce = ((unsigned)(l + 1) << 27) | (jx << 18) | (jy << 9) | jz;
           }
@@ -356,12 +421,16 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
     }
     if (lane == 0) {
       const double dti = d.cfl * cur;
-      // the largest step dt_max 2^-b not above dt_i
+      // the largest step dt_max 2^-b not above dt_i, from the exponents and
+      // significands (dt_max 2^-b is exact): with dt_max = m1 2^e1 and
+      // dt_i = m2 2^e2, b = e1 - e2, plus one if m1 > m2
+      const double dtm = d.dtick * (double)(1ll << d.depth);
       int b = 0;
-      double st = d.dtick * (double)(1ll << d.depth);
-      while (st > dti && b <= d.depth) {
-        st *= 0.5;
-        b++;
+      if (dti < dtm) {
+        const long long u1 = __double_as_longlong(dtm), u2 = __double_as_longlong(dti);
+        const int e1 = (int)((u1 >> 52) & 0x7ff), e2 = (int)((u2 >> 52) & 0x7ff);
+        const long long m1 = u1 & 0xfffffffffffffll, m2 = u2 & 0xfffffffffffffll;
+        b = (e2 == 0) ? d.depth + 1 : e1 - e2 + (m1 > m2 ? 1 : 0);   // zero or subnormal: below every bin
       }
       if (b > d.depth) {
         atomicOr(&v.stats->status, (unsigned)ST_DEPTH);
@@ -369,8 +438,8 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
       }
       const int old = d.bin[i];
       int nb = b;
-      if (d.tick != 0 && b < old)   // at most twice the step, where that step starts now
-        nb = ((d.tick & (step_ticks(d.depth, old - 1) - 1)) == 0) ? old - 1 : old;
+      if (tick != 0 && b < old)   // at most twice the step, where that step starts now
+        nb = ((tick & (step_ticks(d.depth, old - 1) - 1)) == 0) ? old - 1 : old;
       if (nb != old) {
         atomicSub(d.hist + old, 1u);
         atomicAdd(d.hist + nb, 1u);
@@ -394,10 +463,11 @@ __global__ void k_ind_faces(HydroView<real> v, IndView d) {
   }
   const int at = warp_append(d.count + 1, active);
   if (!active) return;
+  const int stamp = d.loop->stamp;
   d.flist[at] = k;
-  d.fstamp[k] = d.stamp;
-  d.cstamp[e.x] = d.stamp;   // both writers store the same value
-  d.cstamp[e.y] = d.stamp;
+  d.fstamp[k] = stamp;
+  d.cstamp[e.x] = stamp;   // both writers store the same value
+  d.cstamp[e.y] = stamp;
   const long long sL = step_ticks(d.depth, d.bin[e.x]), sR = step_ticks(d.depth, d.bin[e.y]);
   d.fdt[k] = (double)(sL < sR ? sL : sR) * d.dtick;
 }
@@ -406,6 +476,7 @@ __global__ void k_ind_faces(HydroView<real> v, IndView d) {
 template <typename real, int B>
 __global__ void __launch_bounds__(B) k_ind_flux(HydroView<real> v, IndView d) {
   const int count = d.count[1];
+  const long long tick = d.loop->tick;
   for (int blk = blockIdx.x; blk * B < count; blk += gridDim.x) {
     const int idx = blk * B + (int)threadIdx.x;
     const bool valid = idx < count;
@@ -413,9 +484,9 @@ __global__ void __launch_bounds__(B) k_ind_flux(HydroView<real> v, IndView d) {
     const int2 e = v.lr[k];
     const long long sL = step_ticks(d.depth, d.bin[e.x]), sR = step_ticks(d.depth, d.bin[e.y]);
     const long long sf = sL < sR ? sL : sR;
-    const long long t2 = 2 * d.tick + sf;                 // twice the middle of the face's step
-    const double hL = (double)(t2 - 2 * (d.tick - (d.tick & (sL - 1)))) * (0.5 * d.dtick);
-    const double hR = (double)(t2 - 2 * (d.tick - (d.tick & (sR - 1)))) * (0.5 * d.dtick);
+    const long long t2 = 2 * tick + sf;                   // twice the middle of the face's step
+    const double hL = (double)(t2 - 2 * (tick - (tick & (sL - 1)))) * (0.5 * d.dtick);
+    const double hR = (double)(t2 - 2 * (tick - (tick & (sR - 1)))) * (0.5 * d.dtick);
     FaceWork<real> f;
     face_prepare<real, false>(v, k, valid, (real)hL, (real)hR, f);
     face_finish<real, B, false>(v, f, 0, min(B, count - blk * B), false, (real)0);
@@ -426,12 +497,14 @@ __global__ void __launch_bounds__(B) k_ind_flux(HydroView<real> v, IndView d) {
 template <typename real>
 __global__ void k_ind_update(HydroView<real> v, IndView d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n || d.cstamp[i] != d.stamp) return;
+  if (i >= d.n) return;
+  const int stamp = d.loop->stamp;
+  if (d.cstamp[i] != stamp) return;
   double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int q = v.csr_off[i]; q < v.csr_off[i + 1]; q++) {
     const int2 e = v.csr[q];
     const int k = e.x >> 1;
-    if (d.fstamp[k] != d.stamp) continue;
+    if (d.fstamp[k] != stamp) continue;
     const double w = (e.x & 1) ? -d.fdt[k] : d.fdt[k];
     const R4<real> f = v.flux[k];
     s[0] += w * (double)f.x;
@@ -442,6 +515,36 @@ __global__ void k_ind_update(HydroView<real> v, IndView d) {
   }
   const size_t n = (size_t)d.n;
   for (int a = 0; a < 5; a++) v.Q[a * n + i] -= s[a];
+}
+
+// ----------------------------------------------------------- the next tick
+// One warp: the deepest bin in use (from the histogram), the counters, the
+// next tick (the next multiple of the shortest step), a fresh stamp and
+// cleared list counters; the cycle's while condition stays set while ticks
+// remain, no cell has failed and the sub-step cap is not reached.
+static __global__ void k_ind_next(IndView d) {
+  const int lane = (int)threadIdx.x;
+  const unsigned h0 = lane <= d.depth ? d.hist[lane] : 0u;
+  const unsigned h1 = lane + 32 <= d.depth ? d.hist[lane + 32] : 0u;
+  const unsigned m0 = __ballot_sync(0xffffffffu, h0 != 0u), m1 = __ballot_sync(0xffffffffu, h1 != 0u);
+  if (lane != 0) return;
+  const int deepest = m1 ? 32 + 31 - __clz(m1) : (m0 ? 31 - __clz(m0) : 0);
+  IndLoop* L = d.loop;
+  L->substeps++;
+  L->activations += (unsigned long long)d.count[0];
+  L->face_fluxes += (unsigned long long)d.count[1];
+  L->deepest = deepest > L->deepest ? deepest : L->deepest;
+  const long long smin = 1ll << (d.depth - deepest);
+  L->tick = (L->tick / smin + 1) * smin;
+  L->stamp++;
+  d.count[0] = 0;
+  d.count[1] = 0;
+  const DeviceStats* S = d.stats;
+  const bool failed = (S->status & (ST_NEWTON_CAP | ST_NONPOS | ST_DEPTH)) != 0u;
+  const bool capped = L->substeps >= L->max_substeps;
+  if (capped && L->tick < L->T) atomicOr(&d.stats->status, (unsigned)ST_SUBSTEPS);
+  L->go = (L->tick < L->T && !failed && !capped) ? 1 : 0;
+  if (d.in_graph) cudaGraphSetConditional(d.handle, (unsigned)L->go);
 }
 
 // ---------------------------------------------------------------- launchers

@@ -152,3 +152,18 @@ def test_sedov_64_radius_and_savings(amm, prec):
     tot0 = np.array([math.fsum(c) for c in Q0.T])
     tot = np.array([math.fsum(c) for c in Q.T])
     np.testing.assert_allclose(tot[[0, 4]], tot0[[0, 4]], rtol=1e-12)
+
+
+def test_host_loop_gives_the_same_cycle(amm):
+    P = ics.sedov(3, 16)
+    Q0 = P.conserved()
+    out = {}
+    for host in (False, True):
+        ctx = amm.create_from_mesh(P.tess, Q0, P.gamma, precision="fp32", mesh_motion="eulerian")
+        amm.amm_individual_host_loop(ctx, host)
+        st = [amm.amm_advance_individual(ctx, 0.3, 0.01, 30, True) for _ in range(2)]
+        out[host] = (amm.amm_get_state(ctx), amm.amm_get_bins(ctx), st)
+        amm.amm_destroy(ctx)
+    assert np.array_equal(out[False][0], out[True][0])
+    assert np.array_equal(out[False][1], out[True][1])
+    assert out[False][2] == out[True][2]
