@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle legs")
     ap.add_argument("--no-extras", action="store_true", help="headline form only (profiling runs)")
     ap.add_argument("--proposal-epochs", type=int, default=4, help="training epochs of the learned p* proposal")
+    ap.add_argument("--individual-host-loop", action="store_true",
+                    help="sedov64: launch each tick of the individual time steps from the host (for profilers "
+                         "that cannot look inside graphs with conditional nodes)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes grad_lanes,update_lanes,flux_block,persistent instead of autotuning")
     a = ap.parse_args()
@@ -708,6 +711,8 @@ def bench_sedov(args, g, world, rank, local):
     for prec in ("fp32", "fp64"):
         ctx = amm.create_from_mesh(P.tess, Q0, P.gamma, precision=prec, mesh_motion="eulerian",
                                    stream=g.stream.cuda_stream)
+        if args.individual_host_loop:
+            amm.amm_individual_host_loop(ctx, True)
         amm.amm_advance_individual(ctx, CFL, t_end / cycles, 30, True)   # warm-up (setup, first launches)
         res[prec] = {}
         for name, fn in (("global", run_global), ("individual", run_individual)):
@@ -725,7 +730,9 @@ def bench_sedov(args, g, world, rank, local):
         "ms_per_step": 1e3 * ind["wall_s"] / cycles, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["sedov64"], "cells": P.n_cells, "faces": nf,
-                   "step": "one cycle of individual time steps of length 0.01 (host loop, one sync per tick)",
+                   "step": "one cycle of individual time steps of length 0.01: one CUDA graph whose while node "
+                           "runs the ticks on the device" + (" (here: ticks launched from the host)"
+                                                             if args.individual_host_loop else ""),
                    "l2": "inputs and working set exceed L2 only in part: whole runs timed, not single steps"},
         "time_to_solution": res,
         "gpu_launches": 8 * ind["substeps"],
