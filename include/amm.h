@@ -203,6 +203,42 @@ int amm_step_boxes(amm_ctx* ctx, const double* dt);
  * captured CUDA graph when use_graph != 0.  Does not synchronise. */
 int amm_advance(amm_ctx* ctx, double cfl, int64_t nsteps, int use_graph);
 
+/* ---------------------------------------------------------------------------
+ * Voronoi tessellation on the GPU (Sec. 2): the face list consumed by
+ * amm_create / amm_create_device, built from device-resident generators.
+ * Each cell is the intersection of the half-spaces bounded by the bisectors to
+ * nearby generators and their periodic images; candidates are searched in
+ * shells of a uniform grid until the completeness radius is reached (twice
+ * the largest vertex distance, Sec. 2.4).  Faces of zero area (below 1e-12
+ * h^(dim-1), h the mean spacing) are dropped.  A face is listed once, by the
+ * cell with the smaller index (by the side with a positive image shift for a
+ * face with its own image), with the right cell's periodic image in box
+ * lengths and the centroid in the left cell's frame -- the layout amm_create
+ * takes.  3D: one warp per cell, at most 48 faces per cell; 2D: 32.
+ * --------------------------------------------------------------------------- */
+typedef struct amm_tess amm_tess;
+
+/* gen_device: [n][dim] device array, every coordinate in [0, box[d]);
+ * box: host [dim]; stream: cudaStream_t or NULL.  Synchronises.  Errors:
+ * AMM_ERR_INVALID_ARG (bad sizes, a generator outside the box),
+ * AMM_ERR_NUMERIC (a cell over capacity, vanished -- duplicate generators --,
+ * not closed, or incomplete; amm_tess_last_error says which), AMM_ERR_CUDA. */
+int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_device, const double* box, void* stream);
+const char* amm_tess_last_error(void);
+int64_t amm_tess_num_faces(const amm_tess* t);
+/* Device arrays owned by t: cells [F][2] (left, right), shift [F][dim],
+ * area [F], centroid [F][dim] (absolute, left cell's frame). */
+int amm_tess_faces(const amm_tess* t, const int32_t** cells, const int8_t** shift, const double** area,
+                   const double** centroid);
+/* Device arrays owned by t: cell volume [n] and centre of mass [n][dim]
+ * (absolute), integrated from the cell's faces as pyramids about its
+ * generator; half-faces per cell [n] (before the listing rule). */
+int amm_tess_cells(const amm_tess* t, const double** volume, const double** com, const int32_t** faces_per_cell);
+/* Listed faces whose mirror the neighbour did not find, and the largest
+ * relative area mismatch between the two sides of a face. */
+int amm_tess_check(const amm_tess* t, int64_t* asymmetric, double* max_rel);
+int amm_tess_destroy(amm_tess* t);
+
 /* Counters of one cycle of individual time steps. */
 typedef struct amm_cycle_stats {
   int64_t substeps;     /* ticks at which steps started */

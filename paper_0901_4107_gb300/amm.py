@@ -78,6 +78,13 @@ _SIGS = {
     "amm_step": (_I, [_P, _D]),
     "amm_step_boxes": (_I, [_P, _P]),
     "amm_advance": (_I, [_P, _D, _I64, _I]),
+    "amm_tess_build": (_I, [ctypes.POINTER(_P), _I, _I64, _P, _P, _P]),
+    "amm_tess_last_error": (ctypes.c_char_p, []),
+    "amm_tess_num_faces": (_I64, [_P]),
+    "amm_tess_faces": (_I, [_P, _P, _P, _P, _P]),
+    "amm_tess_cells": (_I, [_P, _P, _P, _P]),
+    "amm_tess_check": (_I, [_P, _P, _P]),
+    "amm_tess_destroy": (_I, [_P]),
     "amm_advance_individual": (_I, [_P, _D, _D, _I, _I, _P]),
     "amm_get_bins": (_I, [_P, _P]),
     "amm_individual_host_loop": (_I, [_P, _I]),
@@ -282,6 +289,77 @@ def amm_step_boxes(ctx, dt):
 
 def amm_advance(ctx, cfl, nsteps=1, use_graph=True):
     _check(ctx, lib().amm_advance(ctx.handle, float(cfl), int(nsteps), int(bool(use_graph))))
+
+
+class Tess:
+    """A GPU tessellation (amm_tess*): device face and cell arrays owned by
+    the library, freed with the object."""
+
+    def __init__(self, handle, dim, n):
+        self.handle, self.dim, self.n = handle, dim, n
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().amm_tess_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    @property
+    def n_faces(self):
+        return int(lib().amm_tess_num_faces(self.handle))
+
+    def device_faces(self):
+        """Device pointers (cells, shift, area, centroid)."""
+        p = [_P() for _ in range(4)]
+        rc = lib().amm_tess_faces(self.handle, *[ctypes.byref(x) for x in p])
+        if rc != 0:
+            raise AmmError(rc, "amm_tess_faces")
+        return tuple(x.value for x in p)
+
+    def device_cells(self):
+        """Device pointers (volume, centre of mass, half-faces per cell)."""
+        p = [_P() for _ in range(3)]
+        rc = lib().amm_tess_cells(self.handle, *[ctypes.byref(x) for x in p])
+        if rc != 0:
+            raise AmmError(rc, "amm_tess_cells")
+        return tuple(x.value for x in p)
+
+    def to_host(self):
+        """Copies of the face and cell arrays (numpy): cells [F, 2], shift
+        [F, dim], area [F], centroid [F, dim], volume [n], com [n, dim]."""
+        import torch
+        F, d, n = self.n_faces, self.dim, self.n
+        c, s, a, cen = self.device_faces()
+        v, m, _ = self.device_cells()
+
+        def host(ptr, shape, typestr):
+            class _View:
+                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), False),
+                                            "version": 2}
+            return torch.as_tensor(_View(), device="cuda").cpu().numpy().copy()
+
+        return (host(c, (F, 2), "<i4"), host(s, (F, d), "|i1"), host(a, (F,), "<f8"), host(cen, (F, d), "<f8"),
+                host(v, (n,), "<f8"), host(m, (n, d), "<f8"))
+
+    def check(self):
+        a = ctypes.c_int64(0)
+        r = ctypes.c_double(0.0)
+        lib().amm_tess_check(self.handle, ctypes.byref(a), ctypes.byref(r))
+        return a.value, r.value
+
+
+def amm_tess_build(dim, n, gen_ptr, box, stream=None):
+    """Voronoi tessellation of device generators gen_ptr [n][dim] in the
+    periodic box (host sequence of dim lengths)."""
+    h = _P()
+    b = _arr(box, np.float64)
+    rc = lib().amm_tess_build(ctypes.byref(h), int(dim), int(n), ctypes.c_void_p(int(gen_ptr)), b.ctypes.data,
+                              stream)
+    if rc != 0:
+        raise AmmError(rc, "amm_tess_build: " + lib().amm_tess_last_error().decode())
+    return Tess(h.value, dim, n)
 
 
 def amm_advance_individual(ctx, cfl, dt_max, max_depth=30, signal_speed=True):

@@ -102,3 +102,26 @@ def test_vortex_error_independent_of_bulk_velocity(amm, prec, tol):
         l1[v] = moving.gresho_l1(T, Q, t, v)
     assert l1[0.0] > 1e-3
     assert abs(l1[3.0] - l1[0.0]) < tol * l1[0.0], (prec, l1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gresho_fixed_mesh_converges(amm, prec):
+    """Sec. 8.5: at t = 3 the azimuthal-velocity L1 error on Cartesian meshes
+    converges roughly as N^-1.4 (the vorticity jumps at r = 0.2 and 0.4 keep it
+    below second order); checked as an overall slope in [1, 2] from 20^2 to
+    80^2, with the error at 40^2 near the paper's 40 x 40 default well below
+    the vortex's peak speed."""
+    l1 = {}
+    for n in (20, 40, 80):
+        P = ics.gresho_2d(n)
+        ctx = amm.create_from_mesh(P.tess, P.conserved(), P.gamma, precision=prec, mesh_motion="eulerian")
+        t = 0.0
+        while t < 3.0 * (1 - 1e-14):
+            dt = min(float(amm.amm_timestep(ctx, 0.3)[0]), 3.0 - t)
+            amm.amm_step(ctx, dt)
+            t += dt
+        l1[n] = moving.gresho_l1(P.tess, amm.amm_get_state(ctx), t)
+        amm.amm_destroy(ctx)
+    slope = np.log(l1[20] / l1[80]) / np.log(4.0)
+    assert 1.0 < slope < 2.0, (prec, l1, slope)
+    assert l1[40] < 0.1, l1
