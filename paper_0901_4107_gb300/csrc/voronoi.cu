@@ -42,7 +42,7 @@ namespace vor {
 constexpr int WARPS = 4;      // cells per CTA (3D)
 constexpr int MAXP = 64;      // planes per cell: 6 of the box + the cutting bisectors
 constexpr int MAXT = 192;     // vertex slots (dual triangles), dead ones included
-constexpr int MAXC = 128;     // candidates gathered per pass
+constexpr int MAXC = 192;     // candidates gathered per pass
 constexpr int MAXFV = 32;     // vertices of one face
 constexpr int MAXHF = 48;     // output half-faces per cell (3D); 2D uses 32
 
@@ -131,15 +131,19 @@ __global__ void k_bin_sort(const int* bin_start, int* bin_pts, int m) {
 
 // ------------------------------------------------------------- 3D, a warp per cell
 struct Cell3 {
-  double pn[MAXP][4];          // unit normal and offset h: the plane n.x = h (x relative to the generator)
+  double pn[MAXP][4];          // the plane n.x = h (x relative to the generator): for a bisector n is the
+                               // vector to the neighbour's image and h = |n|^2 / 2; for the box, unit n
   int pj[MAXP];                // neighbour (-1: a face of the initial box)
   signed char ps[MAXP][4];     // its periodic image
   unsigned char tri[MAXT][4];  // a vertex: planes a, b, c, and [3] = 1 while it exists
   double tv[MAXT][3];          // its position
+  float tvf[MAXT][4];          // the position in FP32 (first screen of a cut)
   double cx[MAXC][3];          // candidates: image position relative to the generator
   double cd2[MAXC];
+  float cd2f[MAXC];
   int cj[MAXC];
   signed char cs[MAXC][4];
+  short ord[MAXC];             // candidates by distance
   int mk[MAXT];                // the vertices a cut removes
   int np, nt, nc, nm;
 };
@@ -160,8 +164,17 @@ __device__ __forceinline__ void vertex3(const Cell3& C, int a, int b, int c, dou
   cross3(nb, nc, bc);
   cross3(nc, na, ca);
   cross3(na, nb, ab);
-  const double det = dot3(na, bc);
-  for (int d = 0; d < 3; d++) v[d] = (na[3] * bc[d] + nb[3] * ca[d] + nc[3] * ab[d]) / det;
+  const double inv = 1.0 / dot3(na, bc);
+  for (int d = 0; d < 3; d++) v[d] = (na[3] * bc[d] + nb[3] * ca[d] + nc[3] * ab[d]) * inv;
+}
+
+// the FP32 copy of vertex t: position and |v|
+__device__ __forceinline__ void set_f32(Cell3& C, int t) {
+  const double* v = C.tv[t];
+  C.tvf[t][0] = (float)v[0];
+  C.tvf[t][1] = (float)v[1];
+  C.tvf[t][2] = (float)v[2];
+  C.tvf[t][3] = sqrtf(C.tvf[t][0] * C.tvf[t][0] + C.tvf[t][1] * C.tvf[t][1] + C.tvf[t][2] * C.tvf[t][2]);
 }
 
 __device__ __forceinline__ bool has_edge(const unsigned char* t, int u, int w) {
@@ -176,9 +189,11 @@ __device__ void compact3(Cell3& C, int lane) {
     const bool live = t < C.nt && C.tri[t][3];
     unsigned char tr[4] = {0, 0, 0, 0};
     double v[3] = {0, 0, 0};
+    float vf[4] = {0, 0, 0, 0};
     if (live) {
       for (int k = 0; k < 4; k++) tr[k] = C.tri[t][k];
       for (int d = 0; d < 3; d++) v[d] = C.tv[t][d];
+      for (int d = 0; d < 4; d++) vf[d] = C.tvf[t][d];
     }
     const unsigned m = __ballot_sync(0xffffffffu, live);
     __syncwarp();
@@ -186,6 +201,7 @@ __device__ void compact3(Cell3& C, int lane) {
       const int dst = w + __popc(m & ((1u << lane) - 1u));
       for (int k = 0; k < 4; k++) C.tri[dst][k] = tr[k];
       for (int d = 0; d < 3; d++) C.tv[dst][d] = v[d];
+      for (int d = 0; d < 4; d++) C.tvf[dst][d] = vf[d];
     }
     w += __popc(m);
     __syncwarp();
@@ -194,17 +210,31 @@ __device__ void compact3(Cell3& C, int lane) {
   __syncwarp();
 }
 
+// Is vertex t outside {x : n.x <= h} by more than eps (eps scaled with |n|)?
+// An FP32 screen decides the clear cases (its error, a few 1e-7 of
+// |n||v| + |h|, is far below its margin); the rest in FP64.
+__device__ __forceinline__ bool outside(const Cell3& C, int t, const double* n, double h, const float* nf,
+                                        double eps) {
+  const float* v = C.tvf[t];
+  const float d = nf[0] * v[0] + nf[1] * v[1] + nf[2] * v[2] - nf[3];
+  const float tol = 1e-5f * (sqrtf(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]) * v[3] + fabsf(nf[3]));
+  if (d > tol) return true;
+  if (d < -tol) return false;
+  return dot3(C.tv[t], n) - h > eps;
+}
+
 // Cut the cell by {x : n.x <= h}.  Returns 0 if the plane misses the cell
 // (within eps), 1 after a cut, a negative code on overflow or if the cell
 // vanished.  R2 (the largest squared vertex distance) is updated.
 __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const signed char* s, double eps,
-                    double& R2) {
+                    float& R2) {
+  const float nf[4] = {(float)n[0], (float)n[1], (float)n[2], (float)h};
   // vertices outside the plane
   int nm = 0;
   for (int base = 0; base < C.nt; base += 32) {
     const int t = base + lane;
     bool out = false;
-    if (t < C.nt && C.tri[t][3]) out = dot3(C.tv[t], n) - h > eps;
+    if (t < C.nt && C.tri[t][3]) out = outside(C, t, n, h, nf, eps);
     const unsigned m = __ballot_sync(0xffffffffu, out);
     if (out) C.mk[nm + __popc(m & ((1u << lane) - 1u))] = t;
     nm += __popc(m);
@@ -219,7 +249,7 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
     for (int base = 0; base < C.nt; base += 32) {
       const int t = base + lane;
       bool out = false;
-      if (t < C.nt) out = dot3(C.tv[t], n) - h > eps;
+      if (t < C.nt) out = outside(C, t, n, h, nf, eps);
       const unsigned m = __ballot_sync(0xffffffffu, out);
       if (out) C.mk[nm + __popc(m & ((1u << lane) - 1u))] = t;
       nm += __popc(m);
@@ -272,6 +302,7 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
         C.tri[slot][2] = (unsigned char)q;
         C.tri[slot][3] = 1;
         vertex3(C, e[k][0], e[k][1], q, C.tv[slot]);
+        set_f32(C, slot);
         slot++;
       }
     }
@@ -281,19 +312,19 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
   for (int m = lane; m < nm; m += 32) C.tri[C.mk[m]][3] = 0;
   if (lane == 0) C.nt = nt;
   __syncwarp();
-  double r2 = 0.0;
+  float r = 0.0f;
   int live = 0;
   for (int t = lane; t < nt; t += 32)
     if (C.tri[t][3]) {
-      r2 = fmax(r2, dot3(C.tv[t], C.tv[t]));
+      r = fmaxf(r, C.tvf[t][3]);
       live++;
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
     live += __shfl_xor_sync(0xffffffffu, live, o);
   }
-  R2 = r2;
+  R2 = r * r * (1.0f + 1e-5f);           // an upper bound of the largest squared vertex distance
   return live >= 4 ? 1 : E_VANISHED;
 }
 
@@ -341,6 +372,7 @@ __device__ int gather3(const Grid& G, Cell3& C, int lane, int i, const double* r
       d2 += x * x;
     }
     C.cd2[slot] = self ? -1.0 : d2;     // -1: the generator itself, skipped
+    C.cd2f[slot] = self ? -1.0f : (float)d2;
     C.cj[slot] = j;
     for (int d = 0; d < 3; d++) C.cs[slot][d] = (signed char)sh[d];
     C.cs[slot][3] = 0;
@@ -350,14 +382,27 @@ __device__ int gather3(const Grid& G, Cell3& C, int lane, int i, const double* r
   return at + total;
 }
 
-// cuts by the buffered candidates, in buffer order; returns 0 or an error
-__device__ int cut_buffer3(Cell3& C, int lane, int nc, double eps, double& R2) {
-  for (int k = 0; k < nc; k++) {
-    const double d2 = C.cd2[k];
-    if (d2 < 0.0 || 0.25 * d2 >= R2) continue;   // the bisector lies beyond every vertex
-    const double r = sqrt(d2);
-    const double n[3] = {C.cx[k][0] / r, C.cx[k][1] / r, C.cx[k][2] / r};
-    const int rc = cut3(C, lane, n, 0.5 * r, C.cj[k], C.cs[k], eps, R2);
+// cuts by the buffered candidates, nearest first (the near bisectors shrink
+// the cell, after which most far ones miss it and are skipped unexamined);
+// ties in FP32 distance keep buffer order; returns 0 or an error
+__device__ int cut_buffer3(Cell3& C, int lane, int nc, double eps, float& R2) {
+  for (int k = lane; k < nc; k += 32) {
+    const float dk = C.cd2f[k];
+    int r = 0;
+    for (int u = 0; u < nc; u++) {
+      const float du = C.cd2f[u];
+      r += (du < dk || (du == dk && u < k)) ? 1 : 0;
+    }
+    C.ord[r] = (short)k;
+  }
+  __syncwarp();
+  for (int z = 0; z < nc; z++) {
+    const int k = C.ord[z];
+    const float d2f = C.cd2f[k];
+    // the bisector lies beyond every vertex (R2 is an FP32 upper bound)
+    if (d2f < 0.0f || 0.25f * d2f >= R2 * (1.0f + 1e-5f)) continue;
+    const double n[3] = {C.cx[k][0], C.cx[k][1], C.cx[k][2]};
+    const int rc = cut3(C, lane, n, 0.5 * C.cd2[k], C.cj[k], C.cs[k], eps * sqrtf(d2f), R2);
     if (rc < 0) return rc;
   }
   return 0;
@@ -392,19 +437,22 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
       C.tv[lane][0] = sx * 0.5 * G.box[0];
       C.tv[lane][1] = sy * 0.5 * G.box[1];
       C.tv[lane][2] = sz * 0.5 * G.box[2];
+      set_f32(C, lane);
     }
     if (lane == 0) {
       C.np = 6;
       C.nt = 8;
     }
     __syncwarp();
-    double R2 = 0.25 * (G.box[0] * G.box[0] + G.box[1] * G.box[1] + G.box[2] * G.box[2]);
+    float R2 = 0.25f * (float)(G.box[0] * G.box[0] + G.box[1] * G.box[1] + G.box[2] * G.box[2]) * (1.0f + 1e-5f);
     int b[3];
     for (int d = 0; d < 3; d++) b[d] = bin_coord(ri[d], G.bs[d], G.nb[d]);
     const int smax = max(G.nb[0], max(G.nb[1], G.nb[2])) + 2;
     int rc = E_INCOMPLETE;
-    for (int s = 1; s <= smax && rc == E_INCOMPLETE; s++) {
-      const int s0 = (s == 1) ? 0 : s;
+    // the first pass takes the whole 5^3 cube of bins (shells 1 and 2), so
+    // the nearest candidates come first; then one shell at a time
+    for (int s = 2; s <= smax && rc == E_INCOMPLETE; s++) {
+      const int s0 = (s == 2) ? 0 : s;
       const int side = 2 * s + 1, nq = side * side * side;
       int nc = 0;
       int bad = 0;
@@ -432,7 +480,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
         const double lo = (b[d] - s) * G.bs[d], hi = (b[d] + s + 1) * G.bs[d];
         bound = fmin(bound, fmin(ri[d] - lo, hi - ri[d]));
       }
-      if (bound * bound >= 4.0 * R2 * (1 + 1e-12)) rc = 0;
+      if (bound * bound >= 4.0 * (double)R2) rc = 0;
     }
     // a face of the initial box that survived: the cell is not closed
     if (rc == 0) {
@@ -480,7 +528,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
             }
             okc = okc && cur == 0;              // the cycle closes on its start
             if (okc) {
-              const double* nk = C.pn[k];
+              const double* pk = C.pn[k];
+              const double inv = 1.0 / sqrt(dot3(pk, pk));
+              const double nk[4] = {pk[0] * inv, pk[1] * inv, pk[2] * inv, pk[3] * inv};   // unit normal, height
               const double* v0 = C.tv[ord[0]];
               for (int z = 1; z + 1 < m; z++) {
                 const double* v1 = C.tv[ord[z]];
