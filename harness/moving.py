@@ -6,7 +6,8 @@ state, moves the generators by w dt, updates the conserved quantities on the
 current tessellation (its faces move with the velocities derived from the
 same w), and then tessellates the moved generators, which keep their cells'
 conserved quantities.  Two backends take the same steps: the library, in any
-of its forms, and the FP64 oracle (test infrastructure only)."""
+of its forms, and the FP64 oracle (test infrastructure only); run_on_device
+keeps the whole cycle on the GPU (amm_retessellate)."""
 import numpy as np
 
 from .ics import gresho_profile
@@ -67,6 +68,29 @@ class OracleBackend:
         if rc != 0:
             raise RuntimeError("oracle step failed")
         return Qn, gen, dt
+
+
+def run_on_device(amm, problem, precision="fp64", mesh_motion="lagrangian", t_end=None, steps=None, cfl=0.3,
+                  **options):
+    """The same cycle with everything on the device: one context, whose mesh
+    amm_retessellate rebuilds on the GPU after every drift.  Returns
+    (generators, Q, t, steps) in the problem's cell numbering."""
+    ctx = amm.create_from_mesh(problem.tess, problem.conserved(), problem.gamma, precision=precision,
+                               mesh_motion=mesh_motion, **options)
+    try:
+        t, k = 0.0, 0
+        while (steps is None or k < steps) and (t_end is None or t < t_end * (1 - 1e-14)):
+            dt = float(amm.amm_timestep(ctx, cfl)[0])
+            if t_end is not None:
+                dt = min(dt, t_end - t)
+            amm.amm_drift(ctx, dt)
+            amm.amm_step(ctx, dt)
+            amm.amm_retessellate(ctx)
+            t += dt
+            k += 1
+        return amm.amm_get_generators(ctx), amm.amm_get_state(ctx), t, k
+    finally:
+        amm.amm_destroy(ctx)
 
 
 def run(problem, backend, t_end=None, steps=None, cfl=0.3, nthreads=0, tess=None, Q=None, t0=0.0):

@@ -239,6 +239,20 @@ int amm_tess_cells(const amm_tess* t, const double** volume, const double** com,
 int amm_tess_check(const amm_tess* t, int64_t* asymmetric, double* max_rel);
 int amm_tess_destroy(amm_tess* t);
 
+/* The mesh step of the moving-mesh cycle on the device: a new Voronoi
+ * tessellation of the context's current generators (after amm_drift) built on
+ * the GPU as amm_tess_build does, replacing the context's faces; every cell
+ * keeps its conserved quantities (and entropy), its primitives are recomputed
+ * with its new volume.  One box only (AMM_ERR_INVALID_ARG otherwise).  The
+ * face count usually changes: amm_get_num_faces and amm_get_faces give the
+ * new list (face getters follow it).  Synchronises.  Errors as
+ * amm_tess_build. */
+int amm_retessellate(amm_ctx* ctx);
+int64_t amm_get_num_faces(const amm_ctx* ctx);
+/* The current faces in the caller's cell numbering: cells [F][2] (left,
+ * right), area [F], host arrays. */
+int amm_get_faces(amm_ctx* ctx, int32_t* cells, double* area);
+
 /* Counters of one cycle of individual time steps. */
 typedef struct amm_cycle_stats {
   int64_t substeps;     /* ticks at which steps started */

@@ -85,6 +85,9 @@ _SIGS = {
     "amm_tess_cells": (_I, [_P, _P, _P, _P]),
     "amm_tess_check": (_I, [_P, _P, _P]),
     "amm_tess_destroy": (_I, [_P]),
+    "amm_retessellate": (_I, [_P]),
+    "amm_get_num_faces": (_I64, [_P]),
+    "amm_get_faces": (_I, [_P, _P, _P]),
     "amm_advance_individual": (_I, [_P, _D, _D, _I, _I, _P]),
     "amm_get_bins": (_I, [_P, _P]),
     "amm_individual_host_loop": (_I, [_P, _I]),
@@ -360,6 +363,22 @@ def amm_tess_build(dim, n, gen_ptr, box, stream=None):
     if rc != 0:
         raise AmmError(rc, "amm_tess_build: " + lib().amm_tess_last_error().decode())
     return Tess(h.value, dim, n)
+
+
+def amm_retessellate(ctx):
+    """A new GPU tessellation of the context's current generators; cells keep
+    their conserved quantities."""
+    _check(ctx, lib().amm_retessellate(ctx.handle))
+    ctx.nf = int(lib().amm_get_num_faces(ctx.handle))
+
+
+def amm_get_faces(ctx):
+    """(cells [F, 2], area [F]) of the current mesh, caller numbering."""
+    F = int(lib().amm_get_num_faces(ctx.handle))
+    cells = np.empty((F, 2), np.int32)
+    area = np.empty(F)
+    _check(ctx, lib().amm_get_faces(ctx.handle, cells.ctypes.data, area.ctypes.data))
+    return cells, area
 
 
 def amm_advance_individual(ctx, cfl, dt_max, max_depth=30, signal_speed=True):
