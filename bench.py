@@ -23,6 +23,8 @@ Other workloads (--workload), each printed as one line of the same shape:
                 20 steps on the fixed tessellation, oracle on one step
   learned192    the turbulent field at 192^3 (Lagrangian): FP32 learned
                 proposal vs the standard starting value, Newton iterations
+  moving64      the whole moving-mesh step at 64^3 (drift and a new Voronoi
+                mesh every step): on the device vs host-driven
   sedov64       the point explosion at 64^3 to t = 0.06: global steps vs
                 individual power-of-two time steps, FP32 and FP64 forms,
                 times to solution and face-flux counts
@@ -66,6 +68,10 @@ WORKLOADS = {
                  "(seed 5), each the config-2 field at rms Mach U[0.5,4], gamma=5/3, stationary mesh, per-box "
                  "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, one persistent "
                  "cooperative launch per step replayed from a CUDA graph"),
+    "moving64": ("the moving-mesh cycle of Sec. 3 (Courant step, drift, MUSCL-Hancock update, new Voronoi mesh of "
+                 "the moved generators) on the config-2 workload: 64^3 jittered lattice (+-0.2h, seed 2), rms Mach 2, "
+                 "Lagrangian; the mesh built on the GPU (amm_retessellate) against the host tessellator and a new "
+                 "context every step"),
     "sedov64": ("point explosion of Sec. 8.4: 64^3 Cartesian lattice in a periodic unit box, rho=1, P=1e-4, E=1 in "
                 "the cell nearest the centre, gamma=5/3, static mesh, to t=0.06; global Courant steps vs one cycle "
                 "of individual power-of-two time steps (Sec. 7.2, signal-speed criterion) per 0.01"),
@@ -655,6 +661,68 @@ def bench_box(args, g, world, rank, local):
     return line
 
 
+def bench_moving(args, g, world, rank, local):
+    """Whole moving-mesh steps: everything on the device (one context,
+    amm_retessellate after each drift) against the host-driven cycle (host
+    tessellator, a new context per step); value = face-flux updates per
+    second of the device cycle, whole step included."""
+    from harness import ics, moving
+    amm, torch = g.amm, g.torch
+    n = args.n or 64
+    P = ics.turbulent_3d(n, seed=2 + rank)
+    nf = P.n_faces
+    steps = max(3, min(args.steps, 20))
+    res = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for prec in ("fp32", "fp64"):
+        moving.run_on_device(amm, P, prec, "lagrangian", steps=1)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gen, Q, t, k = moving.run_on_device(amm, P, prec, "lagrangian", steps=steps)
+        torch.cuda.synchronize()
+        dev = (time.perf_counter() - t0) / steps
+        kh = 2
+        t0 = time.perf_counter()
+        moving.run(P, moving.LibraryBackend(amm, prec, "lagrangian"), steps=kh)
+        host = (time.perf_counter() - t0) / kh
+        res[prec] = {"device_s_per_step": dev, "host_driven_s_per_step": host, "speedup": host / dev,
+                     "steps": steps, "sim_time": t}
+    # the parts of one device step (FP32): mesh, step
+    ctx = amm.create_from_mesh(P.tess, P.conserved(), P.gamma, precision="fp32", mesh_motion="lagrangian")
+    dt = float(amm.amm_timestep(ctx, CFL)[0])
+    amm.amm_drift(ctx, dt)
+    amm.amm_step(ctx, dt)
+    amm.amm_sync(ctx)
+    t0 = time.perf_counter()
+    amm.amm_retessellate(ctx)
+    res["fp32"]["retessellate_s"] = time.perf_counter() - t0
+    gd = torch.from_numpy(amm.amm_get_generators(ctx)).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tess = amm.amm_tess_build(3, P.n_cells, gd.data_ptr(), P.tess.box)
+    torch.cuda.synchronize()
+    res["fp32"]["tessellation_s"] = time.perf_counter() - t0
+    del tess
+    from harness.tess import tessellate
+    t0 = time.perf_counter()
+    tessellate(amm.amm_get_generators(ctx), P.tess.box)
+    res["fp32"]["host_tessellation_s"] = time.perf_counter() - t0
+    amm.amm_destroy(ctx)
+    clocks = sampler.stop()
+    dev = res["fp32"]["device_s_per_step"]
+    return {
+        "metric": METRIC, "value": nf / dev, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": 1,
+        "ms_per_step": 1e3 * dev, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["moving64"], "cells": P.n_cells, "faces": nf,
+                   "step": "Courant step, drift, update, GPU re-tessellation (wall clock, host loop)"},
+        "cycle": res,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+
+
 def bench_sedov(args, g, world, rank, local):
     """The point explosion to t = 0.06: global steps against individual time
     steps, FP32 and FP64 forms; value = face fluxes per second of the FP32
@@ -984,6 +1052,8 @@ def main():
         line = bench_train_workload(args, g, world, rank, local)
     elif args.workload == "sedov64":
         line = bench_sedov(args, g, world, rank, local)
+    elif args.workload == "moving64":
+        line = bench_moving(args, g, world, rank, local)
     else:
         line = bench_box(args, g, world, rank, local)
     if rank == 0:

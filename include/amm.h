@@ -214,7 +214,7 @@ int amm_advance(amm_ctx* ctx, double cfl, int64_t nsteps, int use_graph);
  * cell with the smaller index (by the side with a positive image shift for a
  * face with its own image), with the right cell's periodic image in box
  * lengths and the centroid in the left cell's frame -- the layout amm_create
- * takes.  3D: one warp per cell, at most 48 faces per cell; 2D: 32.
+ * takes.  3D: one warp per cell, at most 64 faces per cell; 2D: 32.
  * --------------------------------------------------------------------------- */
 typedef struct amm_tess amm_tess;
 

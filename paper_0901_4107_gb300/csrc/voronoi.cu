@@ -39,15 +39,15 @@
 namespace amm {
 namespace vor {
 
-constexpr int WARPS = 4;      // cells per CTA (3D)
-constexpr int MAXP = 64;      // planes per cell: 6 of the box + the cutting bisectors
-constexpr int MAXT = 192;     // vertex slots (dual triangles), dead ones included
+constexpr int WARPS = 2;      // cells per CTA (3D)
+constexpr int MAXP = 128;     // planes per cell: 6 of the box + the cutting bisectors
+constexpr int MAXT = 384;     // vertex slots (dual triangles), dead ones included
 constexpr int MAXC = 192;     // candidates gathered per pass
-constexpr int MAXFV = 32;     // vertices of one face
-constexpr int MAXHF = 48;     // output half-faces per cell (3D); 2D uses 32
+constexpr int MAXFV = 48;     // vertices of one face
+constexpr int MAXHF = 64;     // output half-faces per cell (3D); 2D uses 32
 
 // error codes, as the host tessellator's
-constexpr int E_CAPACITY = -1, E_VANISHED = -2, E_INCOMPLETE = -3, E_OPEN = -4;
+constexpr int E_CAPACITY = -1, E_VANISHED = -2, E_INCOMPLETE = -3, E_OPEN = -4, E_FACES = -6, E_CANDIDATES = -7;
 
 struct Grid {
   int dim, n;
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
           nc = 0;
           if (!bad) {
             at = gather3(G, C, lane, i, ri, b, s, s0, q0, q1, 0);
-            if (at < 0) bad = E_CAPACITY;
+            if (at < 0) bad = E_CANDIDATES;
           }
         }
         if (!bad) nc = at;
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
         nf += __popc(km);
       }
       if (__any_sync(0xffffffffu, rc != 0)) rc = E_OPEN;
-      if (nf > MAXHF) rc = E_CAPACITY;
+      if (nf > MAXHF) rc = E_FACES;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -851,11 +851,13 @@ void tess_free(amm_tess* t) {
 
 const char* tess_msg(int rc) {
   switch (rc) {
-    case -1: return "capacity of a cell exceeded";
+    case -1: return "a cell has more planes or vertices than the builder holds";
     case -2: return "a cell vanished (duplicate generators)";
     case -3: return "completeness radius not reached";
     case -4: return "a cell is not closed by Voronoi faces";
     case -5: return "a generator lies outside [0, box)";
+    case -6: return "a cell has more faces than the builder lists (64 in 3D, 32 in 2D)";
+    case -7: return "too many generators in 32 bins of the search grid";
     default: return "tessellation failed";
   }
 }
