@@ -133,10 +133,11 @@ __global__ void k_bin_sort(const int* bin_start, int* bin_pts, int m) {
 struct Cell3 {
   double pn[MAXP][4];          // the plane n.x = h (x relative to the generator): for a bisector n is the
                                // vector to the neighbour's image and h = |n|^2 / 2; for the box, unit n
+  float pnf[MAXP][4];          // the same in FP32
   int pj[MAXP];                // neighbour (-1: a face of the initial box)
   signed char ps[MAXP][4];     // its periodic image
-  unsigned char tri[MAXT][4];  // a vertex: planes a, b, c, and [3] = 1 while it exists
-  double tv[MAXT][3];          // its position
+  unsigned char tri[MAXT][4];  // a vertex: planes a, b, c; [3]: bit 0 while it exists, bit 1 once tv holds it
+  double tv[MAXT][3];          // its position in FP64, computed when first needed
   float tvf[MAXT][4];          // the position in FP32 (first screen of a cut)
   double cx[MAXC][3];          // candidates: image position relative to the generator
   double cd2[MAXC];
@@ -168,7 +169,36 @@ __device__ __forceinline__ void vertex3(const Cell3& C, int a, int b, int c, dou
   for (int d = 0; d < 3; d++) v[d] = (na[3] * bc[d] + nb[3] * ca[d] + nc[3] * ab[d]) * inv;
 }
 
-// the FP32 copy of vertex t: position and |v|
+// The point on planes a, b, c in FP32, when the three are well conditioned
+// (|det| >= 0.1 |n_a||n_b||n_c|, so the FP32 position is good to a few 1e-7
+// of |v|, far inside the side tests' margin); false otherwise.
+__device__ __forceinline__ bool vertex3f(const Cell3& C, int a, int b, int c, float* v) {
+  const float* na = C.pnf[a];
+  const float* nb = C.pnf[b];
+  const float* nc = C.pnf[c];
+  const float bc[3] = {nb[1] * nc[2] - nb[2] * nc[1], nb[2] * nc[0] - nb[0] * nc[2], nb[0] * nc[1] - nb[1] * nc[0]};
+  const float ca[3] = {nc[1] * na[2] - nc[2] * na[1], nc[2] * na[0] - nc[0] * na[2], nc[0] * na[1] - nc[1] * na[0]};
+  const float ab[3] = {na[1] * nb[2] - na[2] * nb[1], na[2] * nb[0] - na[0] * nb[2], na[0] * nb[1] - na[1] * nb[0]};
+  const float det = na[0] * bc[0] + na[1] * bc[1] + na[2] * bc[2];
+  const float la = na[0] * na[0] + na[1] * na[1] + na[2] * na[2];
+  const float lb = nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2];
+  const float lc = nc[0] * nc[0] + nc[1] * nc[1] + nc[2] * nc[2];
+  if (!(det * det >= 0.01f * la * lb * lc)) return false;
+  const float inv = 1.0f / det;
+  for (int d = 0; d < 3; d++) v[d] = (na[3] * bc[d] + nb[3] * ca[d] + nc[3] * ab[d]) * inv;
+  return true;
+}
+
+// vertex t's FP64 position, computed on first use
+__device__ __forceinline__ const double* vertex64(Cell3& C, int t) {
+  if (!(C.tri[t][3] & 2)) {
+    vertex3(C, C.tri[t][0], C.tri[t][1], C.tri[t][2], C.tv[t]);
+    C.tri[t][3] |= 2;
+  }
+  return C.tv[t];
+}
+
+// the FP32 copy of vertex t from its FP64 position: position and |v|
 __device__ __forceinline__ void set_f32(Cell3& C, int t) {
   const double* v = C.tv[t];
   C.tvf[t][0] = (float)v[0];
@@ -213,14 +243,14 @@ __device__ void compact3(Cell3& C, int lane) {
 // Is vertex t outside {x : n.x <= h} by more than eps (eps scaled with |n|)?
 // An FP32 screen decides the clear cases (its error, a few 1e-7 of
 // |n||v| + |h|, is far below its margin); the rest in FP64.
-__device__ __forceinline__ bool outside(const Cell3& C, int t, const double* n, double h, const float* nf,
+__device__ __forceinline__ bool outside(Cell3& C, int t, const double* n, double h, const float* nf,
                                         double eps) {
   const float* v = C.tvf[t];
   const float d = nf[0] * v[0] + nf[1] * v[1] + nf[2] * v[2] - nf[3];
   const float tol = 1e-5f * (sqrtf(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]) * v[3] + fabsf(nf[3]));
   if (d > tol) return true;
   if (d < -tol) return false;
-  return dot3(C.tv[t], n) - h > eps;
+  return dot3(vertex64(C, t), n) - h > eps;
 }
 
 // Cut the cell by {x : n.x <= h}.  Returns 0 if the plane misses the cell
@@ -261,6 +291,7 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
   if (lane == 0) {
     for (int d = 0; d < 3; d++) C.pn[q][d] = n[d];
     C.pn[q][3] = h;
+    for (int d = 0; d < 4; d++) C.pnf[q][d] = nf[d];
     C.pj[q] = j;
     for (int d = 0; d < 4; d++) C.ps[q][d] = s[d];
     C.np = q + 1;
@@ -300,9 +331,16 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
         C.tri[slot][0] = e[k][0];
         C.tri[slot][1] = e[k][1];
         C.tri[slot][2] = (unsigned char)q;
-        C.tri[slot][3] = 1;
-        vertex3(C, e[k][0], e[k][1], q, C.tv[slot]);
-        set_f32(C, slot);
+        float vf[3];
+        if (vertex3f(C, e[k][0], e[k][1], q, vf)) {
+          C.tri[slot][3] = 1;
+          for (int d = 0; d < 3; d++) C.tvf[slot][d] = vf[d];
+          C.tvf[slot][3] = sqrtf(vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2]);
+        } else {
+          vertex3(C, e[k][0], e[k][1], q, C.tv[slot]);
+          C.tri[slot][3] = 3;
+          set_f32(C, slot);
+        }
         slot++;
       }
     }
@@ -422,6 +460,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
       const int ax = lane >> 1;
       for (int d = 0; d < 3; d++) C.pn[lane][d] = (d == ax) ? ((lane & 1) ? -1.0 : 1.0) : 0.0;
       C.pn[lane][3] = 0.5 * G.box[ax];
+      for (int d = 0; d < 4; d++) C.pnf[lane][d] = (float)C.pn[lane][d];
       C.pj[lane] = -1;
       for (int d = 0; d < 4; d++) C.ps[lane][d] = 0;
     }
@@ -433,7 +472,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
       C.tri[lane][0] = pos ? a : b;
       C.tri[lane][1] = pos ? b : a;
       C.tri[lane][2] = c;
-      C.tri[lane][3] = 1;
+      C.tri[lane][3] = 3;                  // the box corners are exact
       C.tv[lane][0] = sx * 0.5 * G.box[0];
       C.tv[lane][1] = sy * 0.5 * G.box[1];
       C.tv[lane][2] = sz * 0.5 * G.box[2];
@@ -489,7 +528,13 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
         if (C.tri[t][3] && (C.tri[t][0] < 6 || C.tri[t][1] < 6 || C.tri[t][2] < 6)) open = true;
       if (__any_sync(0xffffffffu, open)) rc = E_OPEN;
     }
+    // FP64 positions of every vertex left (lanes over vertices), then the
     // faces: lane per plane; the plane's vertices in cycle order
+    if (rc == 0) {
+      for (int t = lane; t < C.nt; t += 32)
+        if (C.tri[t][3] & 1) vertex64(C, t);
+      __syncwarp();
+    }
     int nf = 0;
     double V = 0.0, M[3] = {0.0, 0.0, 0.0};
     if (rc == 0) {
