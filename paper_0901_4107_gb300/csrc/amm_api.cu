@@ -46,6 +46,7 @@ void free_ctx(amm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->ind_exec) cudaGraphExecDestroy(c->ind_exec);
   if (c->ind_graph) cudaGraphDestroy(c->ind_graph);
+  amm::vor::work_free((amm::vor::TessWork*)c->tess_ws);
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
@@ -54,7 +55,7 @@ void free_ctx(amm_ctx* c) {
                   c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
                   c->ind_fdt, c->ind_hist, c->ind_slot_cell, c->ind_cell_slot, c->ind_leaf_off, c->ind_level_off,
-                  c->ind_rec, c->ind_rec32, c->ind_node, c->ind_loop};
+                  c->ind_rec, c->ind_rec32, c->ind_node, c->ind_loop, c->geo_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 
@@ -238,6 +239,7 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   c->opt = opt;
   c->box_cells = bc;
   c->box_faces = bf;
+  c->nf_cap = nf;
   int dev = 0;
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) {
@@ -742,11 +744,11 @@ static int individual_setup(amm_ctx* c) {
   CU(dalloc(&c->ind_bin, n));
   CU(dalloc(&c->ind_act, n));
   CU(dalloc(&c->ind_list, n));
-  CU(dalloc(&c->ind_flist, nf));
+  CU(dalloc(&c->ind_flist, c->nf_cap));
   CU(dalloc(&c->ind_count, 4));
-  CU(dalloc(&c->ind_fstamp, nf));
+  CU(dalloc(&c->ind_fstamp, c->nf_cap));
   CU(dalloc(&c->ind_cstamp, n));
-  CU(dalloc(&c->ind_fdt, nf));
+  CU(dalloc(&c->ind_fdt, c->nf_cap));
   CU(dalloc(&c->ind_hist, 64));
   CU(dalloc(&c->ind_slot_cell, n));
   CU(dalloc(&c->ind_cell_slot, n));
@@ -761,7 +763,7 @@ static int individual_setup(amm_ctx* c) {
   CU(cudaMemcpy(c->ind_leaf_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c->ind_level_off, c->ind_level_off_h.data(), sizeof(int) * c->ind_level_off_h.size(),
                 cudaMemcpyHostToDevice));
-  CU(cudaMemset(c->ind_fstamp, 0xff, sizeof(int) * nf));
+  CU(cudaMemset(c->ind_fstamp, 0xff, sizeof(int) * c->nf_cap));
   CU(cudaMemset(c->ind_cstamp, 0xff, sizeof(int) * n));
   c->ind_stamp = 0;
   c->ind_ready = true;

@@ -274,6 +274,10 @@ struct amm_ctx {
   float* harvest = nullptr;        // set only during amm_harvest
   bool mlp_loaded = false;
   double* scratch = nullptr;       // layout conversions for getters/setters
+  void* geo_ws = nullptr;          // FP64 face geometry before the FP32 cast (grown on demand)
+  size_t geo_ws_bytes = 0;
+  void* tess_ws = nullptr;         // amm_retessellate: the GPU tessellation's workspace (amm::vor::TessWork)
+  int64_t nf_cap = 0;              // faces the face-sized buffers hold
   size_t scratch_size = 0;         // in doubles
   unsigned long long* counter = nullptr;
   bool grads_fresh = false;
@@ -318,6 +322,19 @@ struct amm_ctx {
 };
 
 namespace amm {
+
+// voronoi.cu: the GPU tessellation into a reusable workspace
+namespace vor {
+struct TessWork;
+TessWork* work_new();
+void work_free(TessWork* w);
+// the last build's faces (device arrays owned by w): cells [F][2], shift [F][dim], area [F], centroid [F][dim]
+void work_faces(const TessWork* w, const int32_t** cells, const int8_t** shift, const double** area,
+                const double** cen);
+int tess_build_work(TessWork* w, int dim, int64_t n, const double* gen_d, const double* box, cudaStream_t st,
+                    bool check, int64_t* nf_out, int64_t* asym, double* max_rel);
+const char* tess_last_error();
+}  // namespace vor
 
 // geometry.cu
 cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* cen, const int8_t* shift_d3);

@@ -187,8 +187,16 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
   if (c->is_fp64()) {
     fg64 = (R4<double>*)c->fgeo;
   } else {
-    e = cudaMalloc(&fg64, sizeof(R4<double>) * 2 * (size_t)c->nf);
-    if (e != cudaSuccess) return e;
+    const size_t need = sizeof(R4<double>) * 2 * (size_t)c->nf;
+    if (need > c->geo_ws_bytes) {
+      if (c->geo_ws) cudaFree(c->geo_ws);
+      c->geo_ws = nullptr;
+      c->geo_ws_bytes = 0;
+      e = cudaMalloc(&c->geo_ws, need);
+      if (e != cudaSuccess) return e;
+      c->geo_ws_bytes = need;
+    }
+    fg64 = (R4<double>*)c->geo_ws;
   }
   k_face_geometry<<<c->n_ftiles, FACE_TILE, 0, c->stream>>>(c->ftiles, c->lr, c->gen, c->box, area, cen, shift3,
                                                              fg64);
@@ -214,13 +222,7 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
         (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igA,
         (R4<float>*)c->igB, (float*)c->igz, c->nbr);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (!c->is_fp64()) {
-    e = cudaStreamSynchronize(c->stream);
-    cudaFree(fg64);
-  }
-  return e;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_drift(amm_ctx* c, double dt) {

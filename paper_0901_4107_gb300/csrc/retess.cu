@@ -135,13 +135,6 @@ __global__ void k_csr_sort(int n, int dim, const int* off, int2* csr, const int2
 
 extern "C" {
 
-int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_d, const double* box, void* stream);
-const char* amm_tess_last_error(void);
-int64_t amm_tess_num_faces(const amm_tess* t);
-int amm_tess_faces(const amm_tess* t, const int32_t** cells, const int8_t** shift, const double** area,
-                   const double** cen);
-int amm_tess_destroy(amm_tess* t);
-
 int amm_retessellate(amm_ctx* c) {
   using namespace amm;
   if (!c) return AMM_ERR_INVALID_ARG;
@@ -157,100 +150,102 @@ int amm_retessellate(amm_ctx* c) {
     if (e != cudaSuccess && where.empty()) where = std::string(w) + ": " + cudaGetErrorString(e);
     return where.empty();
   };
-  // 1. the tessellation of the current generators, internal numbering
+  // 1. the tessellation of the current generators, internal numbering, into
+  // the context's workspace (kept between calls)
+  if (!c->tess_ws) c->tess_ws = vor::work_new();
+  vor::TessWork* w = (vor::TessWork*)c->tess_ws;
   double* g = c->gen;
-  double* packed = nullptr;
   if (dim != 3) {
-    if (!cu(cudaMalloc(&packed, sizeof(double) * n * dim), "alloc")) {
+    // [n][dim] in the workspace's volume scratch would be overwritten by the
+    // build: a buffer of its own
+    if (!cu(cudaMalloc(&g, sizeof(double) * n * dim), "alloc")) {
       c->err = where;
       return AMM_ERR_CUDA;
     }
-    k_pack_gen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)n, dim, c->gen, packed);
-    g = packed;
+    k_pack_gen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)n, dim, c->gen, g);
   }
-  amm_tess* t = nullptr;
-  const int rc = amm_tess_build(&t, dim, n, g, c->box_h.data(), st);
-  if (packed) cudaFree(packed);
+  int64_t nf = 0;
+  const int rc = vor::tess_build_work(w, dim, n, g, c->box_h.data(), st, false, &nf, nullptr, nullptr);
+  if (dim != 3) cudaFree(g);
   if (rc != AMM_OK) {
-    c->err = std::string("amm_retessellate: ") + amm_tess_last_error();
+    c->err = std::string("amm_retessellate: ") + vor::tess_last_error();
     return rc;
   }
-  const int64_t nf = amm_tess_num_faces(t);
-  const int32_t* tcells;
-  const int8_t* tshift;
-  const double* tarea;
-  const double* tcen;
-  amm_tess_faces(t, &tcells, &tshift, &tarea, &tcen);
-  // 2. face-sized buffers for the new face count
+  // 2. face-sized buffers: kept while the new face count fits, else grown
+  // with room for the next meshes of the run
   const size_t rs = c->real_size();
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  if (nf != c->nf) {
+  if (c->ind_exec) cudaGraphExecDestroy(c->ind_exec);
+  if (c->ind_graph) cudaGraphDestroy(c->ind_graph);
+  c->ind_exec = nullptr;
+  c->ind_graph = nullptr;
+  if (nf > c->nf_cap) {
+    const int64_t cap = nf + nf / 8;
     void** bufs[] = {(void**)&c->lr, (void**)&c->face_perm, (void**)&c->csr, &c->fgeo, &c->igA, &c->igB, &c->igz,
-                     (void**)&c->nbr, &c->flux, &c->fluxE, &c->fluxS, &c->machf, (void**)&c->ftiles};
+                     (void**)&c->nbr, &c->flux, &c->fluxE, &c->fluxS, &c->machf, (void**)&c->ftiles,
+                     (void**)&c->ind_flist, (void**)&c->ind_fstamp, (void**)&c->ind_fdt};
     for (void** b : bufs)
       if (*b) {
         cudaFree(*b);
         *b = nullptr;
       }
-    cu(cudaMalloc(&c->lr, sizeof(int2) * nf), "alloc");
-    cu(cudaMalloc(&c->face_perm, sizeof(int) * nf), "alloc");
-    cu(cudaMalloc(&c->csr, sizeof(int2) * 2 * nf), "alloc");
-    cu(cudaMalloc(&c->fgeo, rs * 8 * nf), "alloc");
-    cu(cudaMalloc(&c->igA, rs * 8 * nf), "alloc");
-    cu(cudaMalloc(&c->igB, rs * 8 * nf), "alloc");
-    cu(cudaMalloc(&c->igz, rs * 2 * nf), "alloc");
-    cu(cudaMalloc(&c->nbr, sizeof(int) * 2 * nf), "alloc");
-    cu(cudaMalloc(&c->flux, rs * 4 * nf), "alloc");
-    cu(cudaMalloc(&c->fluxE, rs * nf), "alloc");
+    cu(cudaMalloc(&c->lr, sizeof(int2) * cap), "alloc");
+    cu(cudaMalloc(&c->face_perm, sizeof(int) * cap), "alloc");
+    cu(cudaMalloc(&c->csr, sizeof(int2) * 2 * cap), "alloc");
+    cu(cudaMalloc(&c->fgeo, rs * 8 * cap), "alloc");
+    cu(cudaMalloc(&c->igA, rs * 8 * cap), "alloc");
+    cu(cudaMalloc(&c->igB, rs * 8 * cap), "alloc");
+    cu(cudaMalloc(&c->igz, rs * 2 * cap), "alloc");
+    cu(cudaMalloc(&c->nbr, sizeof(int) * 2 * cap), "alloc");
+    cu(cudaMalloc(&c->flux, rs * 4 * cap), "alloc");
+    cu(cudaMalloc(&c->fluxE, rs * cap), "alloc");
     if (c->opt.entropy) {
-      cu(cudaMalloc(&c->fluxS, rs * nf), "alloc");
-      cu(cudaMalloc(&c->machf, rs * nf), "alloc");
+      cu(cudaMalloc(&c->fluxS, rs * cap), "alloc");
+      cu(cudaMalloc(&c->machf, rs * cap), "alloc");
     }
+    cu(cudaMalloc(&c->ftiles, sizeof(Tile) * ((cap + FACE_TILE - 1) / FACE_TILE)), "alloc");
+    if (c->ind_ready) {
+      cu(cudaMalloc(&c->ind_flist, sizeof(int) * cap), "alloc");
+      cu(cudaMalloc(&c->ind_fstamp, sizeof(int) * cap), "alloc");
+      cu(cudaMalloc(&c->ind_fdt, sizeof(double) * cap), "alloc");
+      cu(cudaMemsetAsync(c->ind_fstamp, 0xff, sizeof(int) * cap, st), "memset");
+    }
+    if (where.empty()) c->nf_cap = cap;
+  }
+  if (nf != c->nf || c->n_ftiles == 0) {
     std::vector<Tile> ft;
     for (int64_t s = 0; s < nf; s += FACE_TILE) ft.push_back(Tile{0, (int)s, (int)std::min<int64_t>(s + FACE_TILE, nf), 0});
     c->n_ftiles = (int)ft.size();
-    cu(cudaMalloc(&c->ftiles, sizeof(Tile) * ft.size()), "alloc");
-    cu(cudaMemcpy(c->ftiles, ft.data(), sizeof(Tile) * ft.size(), cudaMemcpyHostToDevice), "copy");
+    cu(cudaMemcpyAsync(c->ftiles, ft.data(), sizeof(Tile) * ft.size(), cudaMemcpyHostToDevice, st), "copy");
+    cu(cudaStreamSynchronize(st), "sync");     // the host vector goes out of scope
     c->nf = nf;
     c->box_faces = {0, nf};
   }
-  // the individual-step cycle graph holds the old face buffers
-  if (c->ind_exec) cudaGraphExecDestroy(c->ind_exec);
-  if (c->ind_graph) cudaGraphDestroy(c->ind_graph);
-  c->ind_exec = nullptr;
-  c->ind_graph = nullptr;
-  if (c->ind_ready) {
-    void* ib[] = {c->ind_flist, c->ind_fstamp, c->ind_fdt};
-    for (void* p : ib)
-      if (p) cudaFree(p);
-    c->ind_flist = nullptr;
-    c->ind_fstamp = nullptr;
-    c->ind_fdt = nullptr;
-    cu(cudaMalloc(&c->ind_flist, sizeof(int) * nf), "alloc");
-    cu(cudaMalloc(&c->ind_fstamp, sizeof(int) * nf), "alloc");
-    cu(cudaMalloc(&c->ind_fdt, sizeof(double) * nf), "alloc");
-    cu(cudaMemsetAsync(c->ind_fstamp, 0xff, sizeof(int) * nf, st), "memset");
-  }
   // 3. faces, cell -> face lists, geometry
+  const int32_t* wcells;
+  const int8_t* wshift;
+  const double* warea;
+  const double* wcen;
+  vor::work_faces(w, &wcells, &wshift, &warea, &wcen);
   double* cen3 = nullptr;
   int8_t* sh3 = nullptr;
   int *count = nullptr, *cursor = nullptr, *maxinc = nullptr;
   const unsigned gf = (unsigned)((nf + 255) / 256), gc = (unsigned)((n + 255) / 256);
-  if (cu(cudaMalloc(&cen3, sizeof(double) * 3 * nf), "alloc") && cu(cudaMalloc(&sh3, 3 * nf), "alloc") &&
-      cu(cudaMalloc(&count, sizeof(int) * n), "alloc") && cu(cudaMalloc(&cursor, sizeof(int) * n), "alloc") &&
-      cu(cudaMalloc(&maxinc, sizeof(int)), "alloc")) {
-    cu(cudaMemcpyAsync(c->lr, tcells, sizeof(int2) * nf, cudaMemcpyDeviceToDevice, st), "copy");
-    k_pad_faces<<<gf, 256, 0, st>>>((int)nf, dim, tcen, tshift, cen3, sh3, c->face_perm);
+  if (where.empty() && cu(cudaMalloc(&cen3, sizeof(double) * 3 * nf), "alloc") &&
+      cu(cudaMalloc(&sh3, 3 * nf), "alloc") && cu(cudaMalloc(&count, sizeof(int) * n), "alloc") &&
+      cu(cudaMalloc(&cursor, sizeof(int) * n), "alloc") && cu(cudaMalloc(&maxinc, sizeof(int)), "alloc")) {
+    cu(cudaMemcpyAsync(c->lr, wcells, sizeof(int2) * nf, cudaMemcpyDeviceToDevice, st), "copy");
+    k_pad_faces<<<gf, 256, 0, st>>>((int)nf, dim, wcen, wshift, cen3, sh3, c->face_perm);
     cu(cudaMemsetAsync(count, 0, sizeof(int) * n, st), "memset");
     cu(cudaMemsetAsync(maxinc, 0, sizeof(int), st), "memset");
     k_csr_count<<<gf, 256, 0, st>>>((int)nf, c->lr, count);
     k_scan_one<<<1, 1024, 0, st>>>(count, c->csr_off, (int)n);
     cu(cudaMemcpyAsync(cursor, c->csr_off, sizeof(int) * n, cudaMemcpyDeviceToDevice, st), "copy");
     k_csr_fill<<<gf, 256, 0, st>>>((int)nf, c->lr, cursor, c->csr);
-    k_csr_sort<<<gc, 256, 0, st>>>((int)n, dim, c->csr_off, c->csr, c->lr, c->gen, sh3, c->box, tarea, maxinc);
+    k_csr_sort<<<gc, 256, 0, st>>>((int)n, dim, c->csr_off, c->csr, c->lr, c->gen, sh3, c->box, warea, maxinc);
     cu(cudaGetLastError(), "csr");
     int mi = 0;
     cu(cudaMemcpyAsync(&mi, maxinc, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
@@ -258,7 +253,7 @@ int amm_retessellate(amm_ctx* c) {
     c->headroom = 1;
     while ((1 << c->headroom) < mi + 1) c->headroom++;
     c->headroom += 1;
-    if (where.empty()) cu(launch_face_geometry(c, tarea, cen3, sh3), "geometry");
+    if (where.empty()) cu(launch_face_geometry(c, warea, cen3, sh3), "geometry");
     if (where.empty())
       cu(c->is_fp64() ? launch_primitives<double>(c) : launch_primitives<float>(c), "primitives");
     cu(cudaStreamSynchronize(st), "sync");
@@ -266,7 +261,6 @@ int amm_retessellate(amm_ctx* c) {
   void* tmp[] = {cen3, sh3, count, cursor, maxinc};
   for (void* p : tmp)
     if (p) cudaFree(p);
-  amm_tess_destroy(t);
   if (!where.empty()) {
     c->err = "amm_retessellate: " + where;
     return AMM_ERR_CUDA;

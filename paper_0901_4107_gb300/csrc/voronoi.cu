@@ -868,31 +868,46 @@ __global__ void k_check_range(Grid G, int* err) {
 }  // namespace vor
 }  // namespace amm
 
-// ------------------------------------------------------------------ C ABI
-struct amm_tess {
-  int dim = 0;
-  int64_t n = 0, nf = 0;
-  cudaStream_t stream = nullptr;
+// ------------------------------------------------------------------ driver
+namespace amm {
+namespace vor {
+
+// Device scratch and outputs of a build, grown on demand and kept between
+// builds by a caller that tessellates repeatedly (amm_retessellate).
+struct TessWork {
+  int64_t cap_n = 0, cap_bins = 0, cap_hf = 0, cap_f = 0;
+  int *binof = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *bin_pts = nullptr;
+  int *err = nullptr, *nhf = nullptr, *keep = nullptr, *off = nullptr;
+  HalfFace* hf = nullptr;
+  unsigned long long* chk = nullptr;
+  double *vol = nullptr, *com = nullptr;
   int32_t* cells = nullptr;
   int8_t* shift = nullptr;
-  double* area = nullptr;
-  double* cen = nullptr;
-  double* vol = nullptr;
-  double* com = nullptr;
-  int32_t* nface = nullptr;
-  int64_t asym = 0;
-  double max_rel = 0.0;
+  double *area = nullptr, *cen = nullptr;
 };
+
+TessWork* work_new() { return new TessWork(); }
+
+void work_faces(const TessWork* w, const int32_t** cells, const int8_t** shift, const double** area,
+                const double** cen) {
+  *cells = w->cells;
+  *shift = w->shift;
+  *area = w->area;
+  *cen = w->cen;
+}
+
+void work_free(TessWork* w) {
+  if (!w) return;
+  void* p[] = {w->binof, w->count, w->start, w->cursor, w->bin_pts, w->err, w->nhf, w->keep, w->off, w->hf,
+               w->chk,   w->vol,   w->com,   w->cells,  w->shift,   w->area, w->cen};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  delete w;
+}
 
 namespace {
 
-void tess_free(amm_tess* t) {
-  if (!t) return;
-  void* p[] = {t->cells, t->shift, t->area, t->cen, t->vol, t->com, t->nface};
-  for (void* q : p)
-    if (q) cudaFree(q);
-  delete t;
-}
+thread_local std::string g_tess_err;
 
 const char* tess_msg(int rc) {
   switch (rc) {
@@ -907,22 +922,25 @@ const char* tess_msg(int rc) {
   }
 }
 
-thread_local std::string g_tess_err;
+template <typename T>
+cudaError_t grow(T** p, int64_t& cap, int64_t need, int64_t alloc) {
+  if (need <= cap && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)std::max<int64_t>(alloc, 1));
+  if (e == cudaSuccess) cap = alloc;
+  return e;
+}
 
 }  // namespace
 
-extern "C" {
-
-const char* amm_tess_last_error(void) { return g_tess_err.c_str(); }
-
-int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_d, const double* box, void* stream) {
-  using namespace amm::vor;
-  if (!out) return AMM_ERR_INVALID_ARG;
-  *out = nullptr;
-  if ((dim != 2 && dim != 3) || n < 2 || n > ((int64_t)1 << 30) || !gen_d || !box) return AMM_ERR_INVALID_ARG;
-  for (int d = 0; d < dim; d++)
-    if (!(box[d] > 0.0)) return AMM_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+// The build: faces into w->cells/shift/area/cen (nf of them), cell volumes and
+// centres into w->vol/com, half-faces per cell in w->nhf.  check: also the
+// mirror test (asym, max_rel).  Returns an AMM status; the message in
+// tess_last_error().
+int tess_build_work(TessWork* w, int dim, int64_t n, const double* gen_d, const double* box, cudaStream_t st,
+                    bool check, int64_t* nf_out, int64_t* asym, double* max_rel) {
   Grid G;
   G.dim = dim;
   G.n = (int)n;
@@ -942,14 +960,6 @@ int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_d, cons
   }
   const int nbins = G.nb[0] * G.nb[1] * G.nb[2];
   const int slots = dim == 3 ? MAXHF : 32;
-  amm_tess* t = new amm_tess();
-  t->dim = dim;
-  t->n = n;
-  t->stream = st;
-  int *binof = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *bin_pts = nullptr, *err = nullptr;
-  int *nhf = nullptr, *keep = nullptr, *off = nullptr;
-  HalfFace* hf = nullptr;
-  unsigned long long* chk = nullptr;
   int rc = AMM_OK;
   auto cu = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess && rc == AMM_OK) {
@@ -958,84 +968,144 @@ int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_d, cons
     }
     return rc == AMM_OK;
   };
-  const int nb256 = (int)((n + 255) / 256);
-  if (cu(cudaMalloc(&binof, sizeof(int) * n), "alloc") && cu(cudaMalloc(&count, sizeof(int) * nbins), "alloc") &&
-      cu(cudaMalloc(&start, sizeof(int) * (nbins + 1)), "alloc") && cu(cudaMalloc(&cursor, sizeof(int) * nbins), "alloc") &&
-      cu(cudaMalloc(&bin_pts, sizeof(int) * n), "alloc") && cu(cudaMalloc(&err, sizeof(int)), "alloc") &&
-      cu(cudaMalloc(&nhf, sizeof(int) * n), "alloc") && cu(cudaMalloc(&keep, sizeof(int) * n), "alloc") &&
-      cu(cudaMalloc(&off, sizeof(int) * (n + 1)), "alloc") &&
-      cu(cudaMalloc(&hf, sizeof(HalfFace) * (size_t)n * slots), "alloc") &&
-      cu(cudaMalloc(&chk, sizeof(unsigned long long) * 2), "alloc") &&
-      cu(cudaMalloc(&t->vol, sizeof(double) * n), "alloc") && cu(cudaMalloc(&t->com, sizeof(double) * n * dim), "alloc")) {
-    G.pts = gen_d;
-    cu(cudaMemsetAsync(count, 0, sizeof(int) * nbins, st), "memset");
-    cu(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
-    cu(cudaMemsetAsync(chk, 0, sizeof(unsigned long long) * 2, st), "memset");
-    k_check_range<<<nb256, 256, 0, st>>>(G, err);
-    k_bin_count<<<nb256, 256, 0, st>>>(G, binof, count);
-    k_scan<<<1, 1024, 0, st>>>(count, start, nbins);
-    cu(cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, st), "copy");
-    k_bin_fill<<<nb256, 256, 0, st>>>(G, binof, cursor, bin_pts);
-    k_bin_sort<<<(nbins + 255) / 256, 256, 0, st>>>(start, bin_pts, nbins);
-    G.bin_start = start;
-    G.bin_pts = bin_pts;
-    int herr = 0;
-    cu(cudaGetLastError(), "bins");
-    cu(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
-    cu(cudaStreamSynchronize(st), "sync");
-    if (rc == AMM_OK && herr != 0) {
-      g_tess_err = tess_msg(herr);
-      rc = AMM_ERR_INVALID_ARG;
-    }
-    if (rc == AMM_OK) {
-      const double thr = 1e-12 * std::pow(hcell, dim - 1);
-      if (dim == 3) {
-        const size_t smem = sizeof(Cell3) * WARPS;
-        cu(cudaFuncSetAttribute(k_cells3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attribute");
-        const int64_t blocks = std::min<int64_t>((n + WARPS - 1) / WARPS, 152 * 16);
-        k_cells3<<<(int)blocks, 32 * WARPS, smem, st>>>(G, hf, nhf, t->vol, t->com, err, thr);
-      } else {
-        k_cells2<<<nb256, 256, 0, st>>>(G, hf, nhf, t->vol, t->com, err, thr);
-      }
-      cu(cudaGetLastError(), "cells");
-      cu(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
-      cu(cudaStreamSynchronize(st), "sync");
-      if (rc == AMM_OK && herr != 0) {
-        g_tess_err = tess_msg(herr);
-        rc = AMM_ERR_NUMERIC;
-      }
-    }
-    if (rc == AMM_OK) {
-      k_keep_count<<<nb256, 256, 0, st>>>((int)n, dim, slots, hf, nhf, keep);
-      k_scan<<<1, 1024, 0, st>>>(keep, off, (int)n);
-      int nf = 0;
-      cu(cudaMemcpyAsync(&nf, off + n, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
-      cu(cudaStreamSynchronize(st), "sync");
-      t->nf = nf;
-      if (rc == AMM_OK && nf < 1) {
-        g_tess_err = "no faces";
-        rc = AMM_ERR_NUMERIC;
-      }
-      if (rc == AMM_OK && cu(cudaMalloc(&t->cells, sizeof(int32_t) * 2 * nf), "alloc") &&
-          cu(cudaMalloc(&t->shift, (size_t)nf * dim), "alloc") && cu(cudaMalloc(&t->area, sizeof(double) * nf), "alloc") &&
-          cu(cudaMalloc(&t->cen, sizeof(double) * nf * dim), "alloc") && cu(cudaMalloc(&t->nface, sizeof(int32_t) * n), "alloc")) {
-        k_emit<<<nb256, 256, 0, st>>>((int)n, dim, slots, gen_d, hf, nhf, off, t->cells, t->shift, t->area, t->cen);
-        k_mirror<<<nb256, 256, 0, st>>>((int)n, dim, slots, hf, nhf, chk, chk + 1);
-        cu(cudaMemcpyAsync(t->nface, nhf, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st), "copy");
-        unsigned long long h[2] = {0, 0};
-        cu(cudaGetLastError(), "faces");
-        cu(cudaMemcpyAsync(h, chk, sizeof h, cudaMemcpyDeviceToHost, st), "read");
-        cu(cudaStreamSynchronize(st), "sync");
-        t->asym = (int64_t)h[0];
-        std::memcpy(&t->max_rel, &h[1], sizeof(double));
-      }
-    }
+  // per-cell and per-bin scratch (sizes fixed by n, grown only)
+  if (n > w->cap_n || !w->binof) {
+    int64_t c0 = 0;
+    const int64_t m = n;
+    void* p[] = {w->binof, w->bin_pts, w->nhf, w->keep, w->off, w->vol, w->com};
+    for (void* q : p)
+      if (q) cudaFree(q);
+    w->binof = w->bin_pts = w->nhf = w->keep = w->off = nullptr;
+    w->vol = w->com = nullptr;
+    w->cap_n = 0;
+    cu(cudaMalloc(&w->binof, sizeof(int) * m), "alloc");
+    cu(cudaMalloc(&w->bin_pts, sizeof(int) * m), "alloc");
+    cu(cudaMalloc(&w->nhf, sizeof(int) * m), "alloc");
+    cu(cudaMalloc(&w->keep, sizeof(int) * m), "alloc");
+    cu(cudaMalloc(&w->off, sizeof(int) * (m + 1)), "alloc");
+    cu(cudaMalloc(&w->vol, sizeof(double) * m), "alloc");
+    cu(cudaMalloc(&w->com, sizeof(double) * m * 3), "alloc");
+    if (rc == AMM_OK) w->cap_n = m;
+    (void)c0;
   }
-  void* tmp[] = {binof, count, start, cursor, bin_pts, err, nhf, keep, off, hf, chk};
-  for (void* q : tmp)
-    if (q) cudaFree(q);
+  if (nbins > w->cap_bins || !w->count) {
+    void* p[] = {w->count, w->start, w->cursor};
+    for (void* q : p)
+      if (q) cudaFree(q);
+    w->count = w->start = w->cursor = nullptr;
+    w->cap_bins = 0;
+    cu(cudaMalloc(&w->count, sizeof(int) * nbins), "alloc");
+    cu(cudaMalloc(&w->start, sizeof(int) * (nbins + 1)), "alloc");
+    cu(cudaMalloc(&w->cursor, sizeof(int) * nbins), "alloc");
+    if (rc == AMM_OK) w->cap_bins = nbins;
+  }
+  if (!w->err) cu(cudaMalloc(&w->err, sizeof(int)), "alloc");
+  if (!w->chk) cu(cudaMalloc(&w->chk, sizeof(unsigned long long) * 2), "alloc");
+  cu(grow(&w->hf, w->cap_hf, n * slots, n * slots), "alloc");
+  if (rc != AMM_OK) return rc;
+  const int nb256 = (int)((n + 255) / 256);
+  G.pts = gen_d;
+  cu(cudaMemsetAsync(w->count, 0, sizeof(int) * nbins, st), "memset");
+  cu(cudaMemsetAsync(w->err, 0, sizeof(int), st), "memset");
+  cu(cudaMemsetAsync(w->chk, 0, sizeof(unsigned long long) * 2, st), "memset");
+  k_check_range<<<nb256, 256, 0, st>>>(G, w->err);
+  k_bin_count<<<nb256, 256, 0, st>>>(G, w->binof, w->count);
+  k_scan<<<1, 1024, 0, st>>>(w->count, w->start, nbins);
+  cu(cudaMemcpyAsync(w->cursor, w->start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, st), "copy");
+  k_bin_fill<<<nb256, 256, 0, st>>>(G, w->binof, w->cursor, w->bin_pts);
+  k_bin_sort<<<(nbins + 255) / 256, 256, 0, st>>>(w->start, w->bin_pts, nbins);
+  G.bin_start = w->start;
+  G.bin_pts = w->bin_pts;
+  const double thr = 1e-12 * std::pow(hcell, dim - 1);
+  if (dim == 3) {
+    const size_t smem = sizeof(Cell3) * WARPS;
+    cu(cudaFuncSetAttribute(k_cells3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attribute");
+    const int64_t blocks = std::min<int64_t>((n + WARPS - 1) / WARPS, 152 * 16);
+    k_cells3<<<(int)blocks, 32 * WARPS, smem, st>>>(G, w->hf, w->nhf, w->vol, w->com, w->err, thr);
+  } else {
+    k_cells2<<<nb256, 256, 0, st>>>(G, w->hf, w->nhf, w->vol, w->com, w->err, thr);
+  }
+  k_keep_count<<<nb256, 256, 0, st>>>((int)n, dim, slots, w->hf, w->nhf, w->keep);
+  k_scan<<<1, 1024, 0, st>>>(w->keep, w->off, (int)n);
+  cu(cudaGetLastError(), "cells");
+  int herr[2] = {0, 0};
+  cu(cudaMemcpyAsync(&herr[0], w->err, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+  cu(cudaMemcpyAsync(&herr[1], w->off + n, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+  cu(cudaStreamSynchronize(st), "sync");
+  if (rc != AMM_OK) return rc;
+  if (herr[0] != 0) {
+    g_tess_err = tess_msg(herr[0]);
+    return herr[0] == -5 ? AMM_ERR_INVALID_ARG : AMM_ERR_NUMERIC;
+  }
+  const int64_t nf = herr[1];
+  if (nf < 1) {
+    g_tess_err = "no faces";
+    return AMM_ERR_NUMERIC;
+  }
+  if (nf > w->cap_f || !w->cells) {
+    const int64_t cap = nf + nf / 8;   // room for the next meshes of a moving run
+    void* p[] = {w->cells, w->shift, w->area, w->cen};
+    for (void* q : p)
+      if (q) cudaFree(q);
+    w->cells = nullptr;
+    w->shift = nullptr;
+    w->area = w->cen = nullptr;
+    w->cap_f = 0;
+    cu(cudaMalloc(&w->cells, sizeof(int32_t) * 2 * cap), "alloc");
+    cu(cudaMalloc(&w->shift, (size_t)cap * 3), "alloc");
+    cu(cudaMalloc(&w->area, sizeof(double) * cap), "alloc");
+    cu(cudaMalloc(&w->cen, sizeof(double) * cap * 3), "alloc");
+    if (rc != AMM_OK) return rc;
+    w->cap_f = cap;
+  }
+  k_emit<<<nb256, 256, 0, st>>>((int)n, dim, slots, gen_d, w->hf, w->nhf, w->off, w->cells, w->shift, w->area,
+                                w->cen);
+  if (check) k_mirror<<<nb256, 256, 0, st>>>((int)n, dim, slots, w->hf, w->nhf, w->chk, w->chk + 1);
+  cu(cudaGetLastError(), "faces");
+  unsigned long long h[2] = {0, 0};
+  if (check) cu(cudaMemcpyAsync(h, w->chk, sizeof h, cudaMemcpyDeviceToHost, st), "read");
+  cu(cudaStreamSynchronize(st), "sync");
+  if (rc != AMM_OK) return rc;
+  *nf_out = nf;
+  if (asym) *asym = (int64_t)h[0];
+  if (max_rel) std::memcpy(max_rel, &h[1], sizeof(double));
+  return AMM_OK;
+}
+
+const char* tess_last_error() { return g_tess_err.c_str(); }
+
+}  // namespace vor
+}  // namespace amm
+
+// ------------------------------------------------------------------ C ABI
+struct amm_tess {
+  int dim = 0;
+  int64_t n = 0, nf = 0;
+  cudaStream_t stream = nullptr;
+  amm::vor::TessWork* w = nullptr;   // owns every device array
+  int64_t asym = 0;
+  double max_rel = 0.0;
+};
+
+extern "C" {
+
+const char* amm_tess_last_error(void) { return amm::vor::tess_last_error(); }
+
+int amm_tess_build(amm_tess** out, int dim, int64_t n, const double* gen_d, const double* box, void* stream) {
+  if (!out) return AMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((dim != 2 && dim != 3) || n < 2 || n > ((int64_t)1 << 30) || !gen_d || !box) return AMM_ERR_INVALID_ARG;
+  for (int d = 0; d < dim; d++)
+    if (!(box[d] > 0.0)) return AMM_ERR_INVALID_ARG;
+  amm_tess* t = new amm_tess();
+  t->dim = dim;
+  t->n = n;
+  t->stream = (cudaStream_t)stream;
+  t->w = new amm::vor::TessWork();
+  const int rc = amm::vor::tess_build_work(t->w, dim, n, gen_d, box, t->stream, true, &t->nf, &t->asym, &t->max_rel);
   if (rc != AMM_OK) {
-    tess_free(t);
+    amm::vor::work_free(t->w);
+    delete t;
     return rc;
   }
   *out = t;
@@ -1047,18 +1117,18 @@ int64_t amm_tess_num_faces(const amm_tess* t) { return t ? t->nf : 0; }
 int amm_tess_faces(const amm_tess* t, const int32_t** cells, const int8_t** shift, const double** area,
                    const double** cen) {
   if (!t || !cells || !shift || !area || !cen) return AMM_ERR_INVALID_ARG;
-  *cells = t->cells;
-  *shift = t->shift;
-  *area = t->area;
-  *cen = t->cen;
+  *cells = t->w->cells;
+  *shift = t->w->shift;
+  *area = t->w->area;
+  *cen = t->w->cen;
   return AMM_OK;
 }
 
 int amm_tess_cells(const amm_tess* t, const double** vol, const double** com, const int32_t** nface) {
   if (!t || !vol || !com || !nface) return AMM_ERR_INVALID_ARG;
-  *vol = t->vol;
-  *com = t->com;
-  *nface = t->nface;
+  *vol = t->w->vol;
+  *com = t->w->com;
+  *nface = t->w->nhf;
   return AMM_OK;
 }
 
@@ -1070,8 +1140,10 @@ int amm_tess_check(const amm_tess* t, int64_t* asymmetric, double* max_rel) {
 }
 
 int amm_tess_destroy(amm_tess* t) {
-  if (t && t->stream) cudaStreamSynchronize(t->stream);
-  tess_free(t);
+  if (!t) return AMM_OK;
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  amm::vor::work_free(t->w);
+  delete t;
   return AMM_OK;
 }
 
