@@ -970,7 +970,6 @@ int tess_build_work(TessWork* w, int dim, int64_t n, const double* gen_d, const 
   };
   // per-cell and per-bin scratch (sizes fixed by n, grown only)
   if (n > w->cap_n || !w->binof) {
-    int64_t c0 = 0;
     const int64_t m = n;
     void* p[] = {w->binof, w->bin_pts, w->nhf, w->keep, w->off, w->vol, w->com};
     for (void* q : p)
@@ -986,7 +985,6 @@ int tess_build_work(TessWork* w, int dim, int64_t n, const double* gen_d, const 
     cu(cudaMalloc(&w->vol, sizeof(double) * m), "alloc");
     cu(cudaMalloc(&w->com, sizeof(double) * m * 3), "alloc");
     if (rc == AMM_OK) w->cap_n = m;
-    (void)c0;
   }
   if (nbins > w->cap_bins || !w->count) {
     void* p[] = {w->count, w->start, w->cursor};
