@@ -136,9 +136,9 @@ struct Cell3 {
   float pnf[MAXP][4];          // the same in FP32
   int pj[MAXP];                // neighbour (-1: a face of the initial box)
   signed char ps[MAXP][4];     // its periodic image
-  unsigned char tri[MAXT][4];  // a vertex: planes a, b, c; [3]: bit 0 while it exists, bit 1 once tv holds it
-  double tv[MAXT][3];          // its position in FP64, computed when first needed
-  float tvf[MAXT][4];          // the position in FP32 (first screen of a cut)
+  unsigned char tri[MAXT][4];  // a vertex: planes a, b, c; [3] = 1 while it exists
+  float tvf[MAXT][4];          // its position in FP32 and |v| (the FP64 position is recomputed from the
+                               // three planes where it is needed: close side tests, the final faces)
   double cx[MAXC][3];          // candidates: image position relative to the generator
   double cd2[MAXC];
   float cd2f[MAXC];
@@ -189,18 +189,8 @@ __device__ __forceinline__ bool vertex3f(const Cell3& C, int a, int b, int c, fl
   return true;
 }
 
-// vertex t's FP64 position, computed on first use
-__device__ __forceinline__ const double* vertex64(Cell3& C, int t) {
-  if (!(C.tri[t][3] & 2)) {
-    vertex3(C, C.tri[t][0], C.tri[t][1], C.tri[t][2], C.tv[t]);
-    C.tri[t][3] |= 2;
-  }
-  return C.tv[t];
-}
-
-// the FP32 copy of vertex t from its FP64 position: position and |v|
-__device__ __forceinline__ void set_f32(Cell3& C, int t) {
-  const double* v = C.tv[t];
+// the FP32 copy of vertex t from its FP64 position v: position and |v|
+__device__ __forceinline__ void set_f32(Cell3& C, int t, const double* v) {
   C.tvf[t][0] = (float)v[0];
   C.tvf[t][1] = (float)v[1];
   C.tvf[t][2] = (float)v[2];
@@ -218,11 +208,9 @@ __device__ void compact3(Cell3& C, int lane) {
     const int t = base + lane;
     const bool live = t < C.nt && C.tri[t][3];
     unsigned char tr[4] = {0, 0, 0, 0};
-    double v[3] = {0, 0, 0};
     float vf[4] = {0, 0, 0, 0};
     if (live) {
       for (int k = 0; k < 4; k++) tr[k] = C.tri[t][k];
-      for (int d = 0; d < 3; d++) v[d] = C.tv[t][d];
       for (int d = 0; d < 4; d++) vf[d] = C.tvf[t][d];
     }
     const unsigned m = __ballot_sync(0xffffffffu, live);
@@ -230,7 +218,6 @@ __device__ void compact3(Cell3& C, int lane) {
     if (live) {
       const int dst = w + __popc(m & ((1u << lane) - 1u));
       for (int k = 0; k < 4; k++) C.tri[dst][k] = tr[k];
-      for (int d = 0; d < 3; d++) C.tv[dst][d] = v[d];
       for (int d = 0; d < 4; d++) C.tvf[dst][d] = vf[d];
     }
     w += __popc(m);
@@ -243,14 +230,16 @@ __device__ void compact3(Cell3& C, int lane) {
 // Is vertex t outside {x : n.x <= h} by more than eps (eps scaled with |n|)?
 // An FP32 screen decides the clear cases (its error, a few 1e-7 of
 // |n||v| + |h|, is far below its margin); the rest in FP64.
-__device__ __forceinline__ bool outside(Cell3& C, int t, const double* n, double h, const float* nf,
+__device__ __forceinline__ bool outside(const Cell3& C, int t, const double* n, double h, const float* nf,
                                         double eps) {
   const float* v = C.tvf[t];
   const float d = nf[0] * v[0] + nf[1] * v[1] + nf[2] * v[2] - nf[3];
   const float tol = 1e-5f * (sqrtf(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]) * v[3] + fabsf(nf[3]));
   if (d > tol) return true;
   if (d < -tol) return false;
-  return dot3(vertex64(C, t), n) - h > eps;
+  double x[3];
+  vertex3(C, C.tri[t][0], C.tri[t][1], C.tri[t][2], x);
+  return dot3(x, n) - h > eps;
 }
 
 // Cut the cell by {x : n.x <= h}.  Returns 0 if the plane misses the cell
@@ -337,9 +326,10 @@ __device__ int cut3(Cell3& C, int lane, const double* n, double h, int j, const 
           for (int d = 0; d < 3; d++) C.tvf[slot][d] = vf[d];
           C.tvf[slot][3] = sqrtf(vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2]);
         } else {
-          vertex3(C, e[k][0], e[k][1], q, C.tv[slot]);
-          C.tri[slot][3] = 3;
-          set_f32(C, slot);
+          double v[3];
+          vertex3(C, e[k][0], e[k][1], q, v);
+          C.tri[slot][3] = 1;
+          set_f32(C, slot, v);
         }
         slot++;
       }
@@ -472,11 +462,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
       C.tri[lane][0] = pos ? a : b;
       C.tri[lane][1] = pos ? b : a;
       C.tri[lane][2] = c;
-      C.tri[lane][3] = 3;                  // the box corners are exact
-      C.tv[lane][0] = sx * 0.5 * G.box[0];
-      C.tv[lane][1] = sy * 0.5 * G.box[1];
-      C.tv[lane][2] = sz * 0.5 * G.box[2];
-      set_f32(C, lane);
+      C.tri[lane][3] = 1;
+      const double v[3] = {sx * 0.5 * G.box[0], sy * 0.5 * G.box[1], sz * 0.5 * G.box[2]};
+      set_f32(C, lane, v);
     }
     if (lane == 0) {
       C.np = 6;
@@ -528,13 +516,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
         if (C.tri[t][3] && (C.tri[t][0] < 6 || C.tri[t][1] < 6 || C.tri[t][2] < 6)) open = true;
       if (__any_sync(0xffffffffu, open)) rc = E_OPEN;
     }
-    // FP64 positions of every vertex left (lanes over vertices), then the
-    // faces: lane per plane; the plane's vertices in cycle order
-    if (rc == 0) {
-      for (int t = lane; t < C.nt; t += 32)
-        if (C.tri[t][3] & 1) vertex64(C, t);
-      __syncwarp();
-    }
+    // faces: lane per plane; the plane's vertices in cycle order, their FP64
+    // positions from their three planes
     int nf = 0;
     double V = 0.0, M[3] = {0.0, 0.0, 0.0};
     if (rc == 0) {
@@ -576,10 +559,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_cells3(Grid G, HalfFace* hf, int
               const double* pk = C.pn[k];
               const double inv = 1.0 / sqrt(dot3(pk, pk));
               const double nk[4] = {pk[0] * inv, pk[1] * inv, pk[2] * inv, pk[3] * inv};   // unit normal, height
-              const double* v0 = C.tv[ord[0]];
+              double v0[3], v1[3], v2[3];
+              vertex3(C, C.tri[ord[0]][0], C.tri[ord[0]][1], C.tri[ord[0]][2], v0);
+              vertex3(C, C.tri[ord[1]][0], C.tri[ord[1]][1], C.tri[ord[1]][2], v2);
               for (int z = 1; z + 1 < m; z++) {
-                const double* v1 = C.tv[ord[z]];
-                const double* v2 = C.tv[ord[z + 1]];
+                for (int d = 0; d < 3; d++) v1[d] = v2[d];
+                vertex3(C, C.tri[ord[z + 1]][0], C.tri[ord[z + 1]][1], C.tri[ord[z + 1]][2], v2);
                 const double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
                 const double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
                 double cr[3];
