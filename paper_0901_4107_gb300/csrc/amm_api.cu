@@ -711,7 +711,7 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
 // bucket on a lattice), at least 1 and at most 7 (3D) or 9 (2D) levels below
 // the root.
 static int individual_setup(amm_ctx* c) {
-  const int64_t n = c->n, nf = c->nf;
+  const int64_t n = c->n;
   const int dim = c->dim;
   int L = (int)std::floor(std::log2(std::pow((double)n, 1.0 / dim) / 2.0));
   L = std::max(1, std::min(L, dim == 3 ? 7 : 9));
