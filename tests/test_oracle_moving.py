@@ -73,3 +73,27 @@ def test_moving_mesh_conserves_across_retessellation():
     # the neighbourhoods changed: faces came and went
     pairs = lambda tess: {(min(a, b), max(a, b)) for a, b in tess.cells.tolist()}
     assert len(pairs(T) ^ pairs(P.tess)) > 10
+
+
+def test_gresho_l1_converges_on_the_fixed_mesh():
+    """Sec. 8.5: the azimuthal-velocity error converges below second order
+    (the paper fits N^-1.4 at t = 3; the vorticity jumps at r = 0.2 and 0.4
+    limit it); here at t = 1 from 16^2 to 64^2 the overall slope lies in
+    [1, 2], and the error at 32^2 is a few per cent of the peak speed."""
+    O.set_threads(8)
+    l1 = {}
+    for n in (16, 32, 64):
+        P = ics.gresho_2d(n)
+        M = O.Mesh(P.tess)
+        V, s = O.geometry(M)
+        Q, t = P.conserved(), 0.0
+        while t < 1.0 * (1 - 1e-14):
+            W = O.primitives(M, Q, V, P.gamma)
+            dt = min(O.timestep(M, W, V, None, P.gamma, 0.3)[0], 1.0 - t)
+            Q, _, _, rc = O.step(M, Q, P.gamma, "eulerian", dt=dt, geom=(V, s))
+            assert rc == 0
+            t += dt
+        l1[n] = moving.gresho_l1(P.tess, Q, t)
+    slope = np.log(l1[16] / l1[64]) / np.log(4.0)
+    assert 1.0 < slope < 2.0, l1
+    assert l1[32] < 0.05, l1
