@@ -72,3 +72,12 @@ def test_reference_arm_other_ranks_exit_quietly():
     out = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"],
                env={"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert out.strip() == ""
+
+
+@pytest.mark.parametrize("workload", ["sedov64", "moving64"])
+def test_reference_arm_other_workloads(workload):
+    out = _run(["--impl", "reference", "--workload", workload, "--steps", "1", "--warmup", "0", "--n", "12"])
+    d = json.loads([l for l in out.splitlines() if l.startswith("{")][0])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["config"]["workload"].startswith(("point explosion", "the moving-mesh cycle"))
+    assert d["cpu_baseline"]["kind"] == "oracle" and str(d["config"]["sample_lattice"]) in d["cpu_baseline"]["sample"]
