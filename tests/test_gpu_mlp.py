@@ -93,16 +93,79 @@ def _blocks(g):
     return amm.unpack_params(g)
 
 
-@pytest.mark.parametrize("n", [1000, 300])
+def backward_bf16(p, x, t):
+    """FP64 evaluation of the backward with the kernel's rounding points: BF16
+    copies of the weights and of every tensor-core operand (x, h1, dZ2, dZ1),
+    everything else unrounded.  Returns the gradients and, per entry, the
+    sum of the magnitudes of the terms it adds up (the scale of its rounding
+    error)."""
+    xb, W1b, W2b, W3b = bf16(x), bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"])
+    B = x.shape[0]
+    z1 = xb @ W1b.T + p["b1"]
+    h1b = bf16(M.silu(z1))
+    z2 = h1b @ W2b.T + p["b2"]
+    h2 = M.silu(z2)
+    y = (h2 @ W3b.T)[:, 0] + p["b3"][0]
+    dy = (2.0 / B) * (y - t)
+    dz2 = dy[:, None] * W3b * M.dsilu(z2)
+    dz2b = bf16(dz2)
+    dz1 = (dz2b @ W2b) * M.dsilu(z1)
+    dz1b = bf16(dz1)
+    g = {"W3": dy[None, :] @ h2, "b3": np.array([dy.sum()]), "W2": dz2b.T @ h1b, "b2": dz2.sum(0),
+         "W1": dz1b.T @ xb, "b1": dz1.sum(0)}
+    S = {"W3": np.abs(dy)[None, :] @ np.abs(h2), "b3": np.array([np.abs(dy).sum()]),
+         "W2": np.abs(dz2).T @ np.abs(h1b), "b2": np.abs(dz2).sum(0), "W1": np.abs(dz1).T @ np.abs(xb),
+         "b1": np.abs(dz1).sum(0)}
+    return g, S
+
+
+def _entrywise(a, ref, scale):
+    """per-entry error relative to max(|ref|, the entry's error scale)"""
+    return float(np.max(np.abs(a - ref) / np.maximum(np.abs(ref), scale)))
+
+
+def propagated_scales(p, x, t):
+    """First-order running error scale of each gradient entry: the backward
+    evaluated on magnitudes, with each BF16 rounding upstream (h1 before the
+    second layer, and through it y, dy and dZ2) contributing one BF16 ulp of
+    the magnitude it rounds.  Needed where an entry is a small difference of
+    terms that the rounding of an earlier layer shifts."""
+    U = 2.0 ** -8
+    B = x.shape[0]
+    aW2, aW3 = np.abs(p["W2"]), np.abs(p["W3"])
+    z1 = x @ p["W1"].T + p["b1"]
+    h1 = M.silu(z1)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = M.silu(z2)
+    y = (h2 @ p["W3"].T)[:, 0] + p["b3"][0]
+    A2 = np.abs(h1) @ aW2.T + np.abs(p["b2"])
+    H2 = np.abs(h2) + U * A2
+    Y = (H2 @ aW3.T)[:, 0] + abs(p["b3"][0])
+    Dy = (2.0 / B) * (np.abs(y - t) + U * Y)
+    D2 = Dy[:, None] * aW3 * (np.abs(M.dsilu(z2)) + U * A2)
+    D1 = (D2 @ aW2) * np.abs(M.dsilu(z1))
+    return {"W3": Dy[None, :] @ H2, "b3": np.array([Dy.sum()]), "W2": D2.T @ np.abs(h1), "b2": D2.sum(0),
+            "W1": D1.T @ np.abs(x), "b1": D1.sum(0)}
+
+
+@pytest.mark.parametrize("n", [1000, 300, 77])
 def test_gradients_match_oracle(env, n):
-    """Tensor-core backward (BF16 operands, FP32 accumulation) against the
-    FP64 oracle's analytic backward, block by block."""
+    """Tensor-core backward (BF16 operands, FP32 accumulation), entry by entry:
+    within 1e-2 of the FP64 oracle's analytic backward for every parameter
+    block (relative to the entry, or to the sum of the magnitudes of its
+    terms where the sum cancels), and within 1e-4 of the FP64 evaluation at
+    the kernel's BF16 rounding points, which leaves only the FP32
+    accumulation and rare one-ulp differences of a BF16 rounding."""
     torch, amm = env
     rng = np.random.default_rng(100 + n)
     p = M.init_params(rng)
     for k in p:
         p[k] = (p[k] + 0.1 * rng.normal(size=p[k].shape)).astype(np.float32).astype(np.float64)
-    x = rng.normal(size=(n, 6)).astype(np.float32).astype(np.float64)
+    # weights and inputs on the BF16 grid: the network the kernel evaluates
+    # is then exactly the oracle's (the FP32 master copies only feed Adam)
+    for k in ("W1", "W2", "W3"):
+        p[k] = bf16(p[k])
+    x = bf16(rng.normal(size=(n, 6)))
     t = rng.normal(size=n).astype(np.float32).astype(np.float64)
     net = amm.amm_mlp_create(1.4)
     amm.amm_mlp_set_params(net, amm.pack_params(p))
@@ -112,9 +175,14 @@ def test_gradients_match_oracle(env, n):
     loss_ref, gref = M.loss_and_grads(p, x, t)
     assert abs(loss - loss_ref) < 2e-2 * loss_ref
     gb = _blocks(g)
+    gemu, S = backward_bf16(p, x, t)
+    Sp = propagated_scales(p, x, t)
     for k in gref:
-        err = np.linalg.norm(gb[k] - gref[k]) / max(np.linalg.norm(gref[k]), 1e-12)
-        assert err < 5e-2, (k, err)
+        assert gb[k].shape == gref[k].shape, k
+        e_oracle = _entrywise(gb[k], gref[k], np.maximum(S[k], Sp[k]))
+        assert e_oracle < 1e-2, (k, e_oracle)
+        e_emu = _entrywise(gb[k], gemu[k], S[k])
+        assert e_emu < 1e-4, (k, e_emu)
     # a permuted index list gives the same gradient (sums are per sample)
     perm = rng.permutation(n).astype(np.int32)
     idx = torch.from_numpy(perm).cuda()

@@ -91,3 +91,38 @@ def test_adam_reaches_known_minimum():
     for _ in range(3000):
         p = mlp.adam_step(p, {"w": 2 * (p["w"] - c)}, st, lr=0.01)
     assert np.allclose(p["w"], c, atol=1e-6)
+
+
+def test_bf16_rounding_model_is_within_the_gpu_tolerance():
+    """The GPU backward is held to 1e-2 (per entry, against max(|g|, its error
+    scale)) of this oracle.  The FP64 evaluation at the kernel's BF16
+    rounding points stays inside that bound on many random networks, so the
+    bound leaves room only for the FP32 accumulation; and the mistakes a
+    kernel could make (a transposed or mis-indexed block, a sign, a scale)
+    are far outside it."""
+    from oracle import mlp as M
+    from tests.test_gpu_mlp import _entrywise, backward_bf16, bf16, propagated_scales
+    worst = 0.0
+    planted = []
+    for n in (1000, 300, 77, 33):
+        for seed in range(4):
+            rng = np.random.default_rng(100 + n + 1000 * seed)
+            p = M.init_params(rng)
+            for k in p:
+                p[k] = (p[k] + 0.1 * rng.normal(size=p[k].shape)).astype(np.float32).astype(np.float64)
+            for k in ("W1", "W2", "W3"):
+                p[k] = bf16(p[k])
+            x = bf16(rng.normal(size=(n, 6)))
+            t = rng.normal(size=n).astype(np.float32).astype(np.float64)
+            _, gref = M.loss_and_grads(p, x, t)
+            gemu, S = backward_bf16(p, x, t)
+            Sp = propagated_scales(p, x, t)
+            F = {k: np.maximum(S[k], Sp[k]) for k in S}
+            worst = max(worst, max(_entrywise(gemu[k], gref[k], F[k]) for k in gref))
+            planted.append(min(_entrywise(gemu["W2"].T, gref["W2"], F["W2"]),
+                               _entrywise(gemu["W1"][::-1], gref["W1"], F["W1"]),
+                               _entrywise(-gemu["b1"], gref["b1"], F["b1"]),
+                               _entrywise(np.roll(gemu["b2"], 1), gref["b2"], F["b2"]),
+                               _entrywise(2 * gemu["W3"], gref["W3"], F["W3"])))
+    assert worst < 1e-2, worst
+    assert min(planted) > 0.1, min(planted)

@@ -56,6 +56,36 @@ def test_noalloc_timestep_matches_context_timestep_twice(env, motion):
     assert results[0] != results[1]
 
 
+@pytest.mark.parametrize("motion", ["eulerian", "explicit"])
+def test_noalloc_timestep_2d_matches_context_timestep_twice(env, motion):
+    """The 2D branch (radius sqrt(V / pi)) on the config-1 mesh: 128 x 64
+    jittered generators in [0,2] x [0,1], the Sod states with a velocity
+    field added so that |v - w| matters; two calls in a row."""
+    torch, amm = env
+    P = ics.sod_2d(128, 64, seed=1)
+    x, y = P.tess.points[:, 0], P.tess.points[:, 1]
+    results = []
+    for k, cfl in ((1, 0.3), (2, 0.45)):
+        P.vel = np.stack([0.7 * k * np.sin(2 * np.pi * y), -0.4 * k * np.cos(np.pi * x)], axis=1)
+        ctx = amm.create_from_mesh(P.tess, P.conserved(), P.gamma, precision="fp64", mesh_motion=motion)
+        w = None
+        if motion == "explicit":
+            w = np.ascontiguousarray(0.5 * P.vel[:, ::-1])
+            amm.amm_set_mesh_velocity(ctx, w)
+        ref = amm.amm_timestep(ctx, cfl)[0]
+        Wd, Vd = _device_inputs(torch, amm, ctx)
+        wd = torch.from_numpy(w).cuda() if w is not None else None
+        dt = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        s = torch.cuda.current_stream()
+        amm.amm_timestep_noalloc(2, P.n_cells, Wd.data_ptr(), Vd.data_ptr(), wd.data_ptr() if wd is not None else 0,
+                                 P.gamma, cfl, dt.data_ptr(), s.cuda_stream)
+        got = float(dt.cpu().item())
+        assert abs(got - ref) <= 1e-13 * ref, (got, ref)
+        results.append(got)
+        amm.amm_destroy(ctx)
+    assert results[0] != results[1]
+
+
 def test_noalloc_rejects_oversize_and_bad_arguments(env):
     torch, amm = env
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
