@@ -1,26 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the moving-mesh MUSCL-Hancock update on GB300.
 
-Default workload (turbulent64): a 64^3 jittered lattice (+-0.2 spacing,
-seed 2) in a periodic unit box, gamma = 5/3, rho = P = 1, a random-phase
-Gaussian velocity field with P(k) ~ k^-4 on 2 <= k <= 8 at rms Mach 2, mesh
-generators moving with the cells (Lagrangian); the Voronoi tessellation is
-built on the host before timing.  One "step" is one pass of the whole hot
-path on the device: gradients + limiter + Courant minimum, face velocities +
-fluxes (exact Riemann), signed cell update + primitives + conservation sums,
-replayed from a captured CUDA graph, with the time step kept on the device.
+Default workload (lognormal192): a 192^3 jittered lattice (+-0.2 spacing,
+seed 3, 7,077,888 cells, ~55.5 M faces) in a periodic unit box, gamma =
+5/3, log-normal density (sigma_lnrho = 1), P = rho^(5/3), a random-phase
+Gaussian velocity field with P(k) ~ k^-4 on 2 <= k <= 8 at rms Mach 3, a
+static (Eulerian) mesh; the Voronoi tessellation is built on the host
+before timing.  One "step" is one pass of the whole hot path on the device:
+gradients + limiter + Courant minimum, fluxes (exact Riemann), signed cell
+update + primitives + conservation sums, replayed from a captured CUDA
+graph, with the time step kept on the device.
 
 Metric: face-flux updates per second = faces x steps / device time.  The
 headline value is the FP32 form (FP32 bulk, exact fixed-point flux sums,
-FP64 state and sums); the FP64 form and the FP32 form with the learned
+FP64 state and sums); the plain FP64 form and the FP32 form with the learned
 Riemann-pressure proposal are measured on the same workload, each with its
-error against the FP64 CPU oracle.  Between timed steps the state is reset
-to the same input and the L2 is flushed (256 MiB write).
+error against the FP64 CPU oracle after one step, and 20 steps on the fixed
+tessellation compare the FP32 and FP64 forms.  The input (state, faces,
+cells) exceeds the L2 many times over; between timed steps the state is
+also reset to the same input and the L2 flushed (256 MiB write).
 
 Other workloads (--workload), each printed as one line of the same shape:
-  lognormal192  192^3 log-normal density (sigma 1), P = rho^5/3, Mach-3
-                velocities, Eulerian; FP32 vs FP64 GPU forms, one step and
-                20 steps on the fixed tessellation, oracle on one step
+  turbulent64   64^3 jittered lattice, gamma 5/3, rho = P = 1, the Gaussian
+                velocity field at rms Mach 2, Lagrangian mesh motion; FP32,
+                FP64 and learned forms, proposal-training throughput
   learned192    the turbulent field at 192^3 (Lagrangian): FP32 learned
                 proposal vs the standard starting value, Newton iterations
   moving64      the whole moving-mesh step at 64^3 (drift and a new Voronoi
@@ -58,7 +61,8 @@ WORKLOADS = {
                     "given tessellation"),
     "lognormal192": ("config-3 workload: 192^3 jittered lattice (+-0.2h, seed 3), log-normal density sigma_lnrho=1 "
                      "(same spectrum), P=rho^(5/3), " + FIELD + " at rms Mach 3, gamma=5/3, stationary mesh; one "
-                     "step and 20 steps on the fixed tessellation"),
+                     "step and 20 steps on the fixed tessellation; FP32 headline, plain FP64 and FP32 + learned "
+                     "p* proposal forms"),
     "learned192": ("config-4 workload: the config-2 field at 192^3 (jittered lattice +-0.2h, seed 2, rms Mach 2, "
                    "Lagrangian); FP32 flux with the learned p* proposal vs the standard starting value, Newton to "
                    "1e-6 relative in both"),
@@ -84,10 +88,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000; ensemble 50)")
     ap.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default 20; ensemble 5)")
     ap.add_argument("--impl", default="amm", choices=["amm", "reference"])
-    ap.add_argument("--workload", default="turbulent64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lognormal192", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="lattice size per dimension (single-box workloads)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle legs")
     ap.add_argument("--no-extras", action="store_true", help="headline form only (profiling runs)")
+    ap.add_argument("--form", default=None, choices=["fp32", "fp64", "fp32_learned"],
+                    help="single-box workloads: the form timed as the headline (default: the workload's own)")
     ap.add_argument("--proposal-epochs", type=int, default=4, help="training epochs of the learned p* proposal")
     ap.add_argument("--individual-host-loop", action="store_true",
                     help="sedov64: launch each tick of the individual time steps from the host (for profilers "
@@ -123,10 +129,12 @@ def peaks():
 
 
 # the sources each profiled kernel is compiled from (its DRAM traffic in
-# profiles/ncu_traffic.json holds only while these are unchanged)
+# profiles/ncu_traffic.json and its FLOP counts in profiles/ncu_alu.json hold
+# only while these are unchanged)
 _COMMON = ["amm_internal.cuh", "hydro.cuh", "riemann.cuh", "hydro_f32.cu", "../../include/amm.h"]
 KERNEL_SOURCES = {
     "gradients": _COMMON, "flux": _COMMON, "update": _COMMON,
+    "flux_fp64": ["amm_internal.cuh", "hydro.cuh", "riemann.cuh", "hydro_f64.cu", "../../include/amm.h"],
     "learned_flux": _COMMON + ["flux_learned.cu", "learned.cuh", "tc.cuh", "persistent.cuh"],
 }
 
@@ -152,6 +160,52 @@ def ncu_traffic(kernel, nf):
     if kernel not in KERNEL_SOURCES or k.get("source_hash") != source_hash(kernel):
         return None
     return k["dram_bytes"] * (nf / k["faces"])
+
+
+def ncu_flops(kernel, nf):
+    """FP32 and FP64 FLOPs per launch counted by ncu on the kernel's current
+    sources (fadd + fmul + 2 ffma, and the FP64 equivalents), scaled to this
+    launch's faces; None when the counts were taken on other sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_alu.json")
+    try:
+        with open(p) as f:
+            k = json.load(f)["kernels"][kernel]
+    except Exception:
+        return None
+    if kernel not in KERNEL_SOURCES or k.get("source_hash") != source_hash(kernel):
+        return None
+    return {"fp32": k["fp32_flop"] * nf / k["faces"], "fp64": k["fp64_flop"] * nf / k["faces"],
+            "case": k.get("case")}
+
+
+def alu_peaks(amm, stream):
+    """FP32 and FP64 fused multiply-add throughput of this device in TFLOP/s
+    (FMA-chain probe, best of 3 launches of ~30-40 ms)."""
+    out = {}
+    for name, fp64, iters in (("fp32", 0, 1000000), ("fp64", 1, 20000)):
+        amm.amm_alu_peak(fp64, max(1, iters // 50), stream)
+        best = 0.0
+        for _ in range(3):
+            flop, ms = amm.amm_alu_peak(fp64, iters, stream)
+            best = max(best, flop / (ms * 1e-3) / 1e12)
+        out[name] = best
+    return out
+
+
+def alu_roofline(kernel, ms, nf, apk, pipe):
+    """The flux kernel against the FMA pipe it computes on: counted FLOPs per
+    launch over its event time, against the probe's rate."""
+    f = ncu_flops(kernel, nf)
+    out = {"kernel": kernel, "bound": "alu", "unit": "TFLOP/s", "pipe": pipe,
+           "peak": apk.get(pipe) if apk else None, "peak_source": "FMA-chain probe in this run (amm_alu_peak)"}
+    if f is None or not apk or not ms:
+        out.update({"achieved": None, "frac": None, "note": "no ncu FLOP count for the current sources"})
+        return out
+    achieved = f[pipe] / (ms * 1e-3) / 1e12
+    out.update({"achieved": achieved, "frac": achieved / apk[pipe], "flop_per_launch": f[pipe],
+                "flop_source": "ncu thread-instruction counts of this kernel's sources (%s), scaled by faces"
+                               % f["case"]})
+    return out
 
 
 def algorithmic_bytes(kernel, n, nf, rb):
@@ -367,6 +421,12 @@ class Gpu:
         self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")   # 256 MiB > L2
         self.net = None
         self.train_stats = None
+        self._alu = None
+
+    def alu(self):
+        if self._alu is None:
+            self._alu = alu_peaks(self.amm, self.stream.cuda_stream)
+        return self._alu
 
     def proposal(self):
         if self.net is None:
@@ -565,6 +625,9 @@ def bench_box(args, g, world, rank, local):
         P, motion, head = ics.turbulent_3d(args.n, seed=2 + rank), "lagrangian", "fp32_learned"
     else:
         P, motion, head = ics.turbulent_3d(args.n, seed=2 + rank), "lagrangian", "fp32"
+    default_head = head
+    if args.form:
+        head = args.form
     n, nf = P.n_cells, P.n_faces
     Q0 = P.conserved()
     Q0d = torch.from_numpy(Q0).to("cuda")
@@ -590,20 +653,25 @@ def bench_box(args, g, world, rank, local):
     step_ms, faces_all = reduce_replicas(torch, statistics.mean(ms), nf, world, "cuda")
     value = faces_all / (step_ms * 1e-3)
     split = kernel_split(g, ctxs[head], Q0d, tuning)
-    kern = kernel_table(split or ker, n, nf, 4)
+    rb = 8 if head == "fp64" else 4
+    kern = kernel_table(split or ker, n, nf, rb)
     prefix = "learned_" if head == "fp32_learned" else ""
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[wl], "cells": n, "faces": nf,
-                   "form": head + (" (learned p* proposal, " if head == "fp32_learned" else " (")
-                   + "FP32 bulk, exact fixed-point flux sums, FP64 state and sums)",
+                   "form": head + (" (FP64 throughout)" if head == "fp64" else
+                                   (" (learned p* proposal, " if head == "fp32_learned" else " (")
+                                   + "FP32 bulk, exact fixed-point flux sums, FP64 state and sums)"),
                    "l2": "flushed between timed steps (256 MiB write); state reset to the same input",
                    "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "tuning": tuning},
         "cells_per_s": n * (faces_all / nf) / (step_ms * 1e-3),
         "roofline": roofline(kern, nf, prefix),
+        "alu_roofline": (alu_roofline("flux_fp64", kern["flux"]["ms"], nf, g.alu(), "fp64") if head == "fp64" else
+                         alu_roofline(prefix + "flux", kern["flux"]["ms"], nf, g.alu(), "fp32")),
+        "alu_peaks_tflops": g.alu(),
         "kernels": kern,
         "kernel_times_from": "per-phase launches of the same shapes" if split else "the timed steps",
         "gpu_launches": (1 if tuning["persistent"] else 4) * args.steps,
@@ -613,8 +681,9 @@ def bench_box(args, g, world, rank, local):
         return line
     from oracle import oracle as O
     forms = {head: {"value": value, "ms_per_step": step_ms, "wall_s": wall}}
-    others = {"turbulent64": ("fp64", "fp32_learned"), "lognormal192": ("fp64",),
+    others = {"turbulent64": ("fp64", "fp32_learned"), "lognormal192": ("fp64", "fp32_learned"),
               "learned192": ("fp32", "fp64")}[wl]
+    others = tuple(f for f in (default_head,) + others if f != head)
     for prec in others:
         ctxs[prec] = make(prec)
         g.tune(ctxs[prec], args.tuning, 2)
@@ -623,6 +692,10 @@ def bench_box(args, g, world, rank, local):
         msf, kerf, _ = timed_form(g, ctxs[prec], Q0d, k, min(args.warmup, 5))
         forms[prec] = {"value": nf / (statistics.mean(msf) * 1e-3), "ms_per_step": statistics.mean(msf),
                        "steps": k, "kernels_ms": kerf}
+        if prec == "fp64":
+            forms[prec]["alu_roofline"] = alu_roofline("flux_fp64", kerf["flux"], nf, g.alu(), "fp64")
+        elif prec == "fp32":
+            forms[prec]["alu_roofline"] = alu_roofline("flux", kerf["flux"], nf, g.alu(), "fp32")
     if "fp32_learned" in ctxs:
         forms["fp32_learned"]["training"] = g.train_stats
     for prec, ctx in ctxs.items():
@@ -632,8 +705,16 @@ def bench_box(args, g, world, rank, local):
         # oracle's own rate on a bounded sample is the CPU baseline
         cores = host_threads()
         rate, kcpu, secs, first = oracle_rate(P, motion, 8, budget_s=12.0, threads=cores)
-        rate1, kcpu1, _, _ = oracle_rate(P, motion, 8, budget_s=12.0, threads=1) if P.n_cells <= 300000 else \
-            (None, 0, None, None)
+        if P.n_cells <= 300000:
+            rate1, kcpu1, _, _ = oracle_rate(P, motion, 8, budget_s=12.0, threads=1)
+            sample1 = "%d full oracle step(s) of the workload, 1 host thread" % kcpu1
+        else:
+            # one thread on the whole 192^3 box would take ~30 s per step: a
+            # 64^3 box of the same recipe stands in
+            Ps = ics.lognormal_3d(64, seed=3) if wl == "lognormal192" else ics.turbulent_3d(64, seed=2)
+            rate1, kcpu1, _, _ = oracle_rate(Ps, motion, 8, budget_s=8.0, threads=1)
+            sample1 = "%d full oracle step(s) of a 64^3 box of the same recipe (%d faces), 1 host thread" % (
+                kcpu1, Ps.n_faces)
         ref, dt, geom = first
         W0 = O.primitives(O.Mesh(P.tess), Q0, geom[0], P.gamma)
         fl = floors(Q0, W0, 3, P.gamma)
@@ -645,7 +726,7 @@ def bench_box(args, g, world, rank, local):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                                 "sample": "%d full oracle step(s) of the workload (%d faces each), %d host threads"
                                           % (kcpu, nf, cores),
-                                "one_thread": {"value": rate1, "steps": kcpu1}}
+                                "one_thread": {"value": rate1, "steps": kcpu1, "sample": sample1}}
     if wl == "lognormal192":
         # 20 steps on the fixed tessellation, FP32 vs FP64 GPU forms
         res = {}

@@ -419,6 +419,17 @@ int amm_mlp_features(double gamma, int64_t n, const float* states_device, float*
 int amm_riemann_pstar(double gamma, int64_t n, const float* states_device, double tol, float* pstar_device,
                       void* stream);
 
+/* Throughput probe of the arithmetic pipes (the paper has no counterpart: it
+ * is the denominator of the ALU rooflines reported for the Riemann kernels).
+ * Runs independent fused multiply-add chains, FP32 (fp64 = 0) or FP64
+ * (fp64 = 1), on every SM of the current device: `iters` iterations of 8
+ * chains per thread, 4 CTAs of 256 threads per SM.  Blocks until done.
+ *   flop_out  host, receives the FLOPs performed (2 per FMA)
+ *   ms_out    host, receives the kernel's device time (CUDA events)
+ *   stream    cudaStream_t (NULL: the legacy default stream)
+ * Errors: AMM_ERR_INVALID_ARG (iters < 1, NULL outputs), AMM_ERR_CUDA. */
+int amm_alu_peak(int fp64, int iters, double* flop_out, float* ms_out, void* stream);
+
 /* Allocation-free Courant time step.  The paper has no counterpart to this
  * entry point: it exists for callers that cannot allocate device memory --
  * code whose device memory is owned by another allocator (for example a

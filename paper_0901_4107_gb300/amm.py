@@ -112,6 +112,7 @@ _SIGS = {
     "amm_get_tuning": (_I, [_P, _P]),
     "amm_autotune": (_I, [_P, _D, _I, _P]),
     "amm_timestep_noalloc": (_I, [_I, _I64, _P, _P, _P, _D, _D, _P, _P]),
+    "amm_alu_peak": (_I, [_I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float), _P]),
     "amm_mlp_create": (_I, [ctypes.POINTER(_P), _D, _P]),
     "amm_mlp_destroy": (None, [_P]),
     "amm_mlp_last_error": (ctypes.c_char_p, [_P]),
@@ -539,6 +540,17 @@ def amm_timestep_noalloc(dim, n_cells, W_ptr, V_ptr, wmesh_ptr, gamma, cfl, dt_p
                                     ctypes.c_void_p(int(dt_ptr)), ctypes.c_void_p(int(stream)) if stream else None)
     if rc != AMM_OK:
         raise AmmError(rc, "amm_timestep_noalloc failed")
+
+
+def amm_alu_peak(fp64, iters, stream=None):
+    """FMA-chain throughput probe of the current device: returns (FLOPs, ms)."""
+    flop = _D(0.0)
+    ms = ctypes.c_float(0.0)
+    rc = lib().amm_alu_peak(int(bool(fp64)), int(iters), ctypes.byref(flop), ctypes.byref(ms),
+                            ctypes.c_void_p(int(stream)) if stream else None)
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_alu_peak failed")
+    return flop.value, ms.value
 
 
 class Mlp:
