@@ -52,7 +52,7 @@ void free_ctx(amm_ctx* c) {
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
                   c->ftiles, c->box_first_ctile, c->fgeo, c->igA, c->igB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad,
                   c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->wcorr, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
-                  c->totals, c->stats,  c->closure, c->mlp,      c->scratch, c->counter,
+                  c->totals, c->stats,  c->closure, c->mlp,      c->defer_list, c->defer_count, c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
                   c->ind_fdt, c->ind_hist, c->ind_slot_cell, c->ind_cell_slot, c->ind_leaf_off, c->ind_level_off,
                   c->ind_rec, c->ind_rec32, c->ind_node, c->ind_loop, c->geo_ws};

@@ -63,6 +63,14 @@ struct DeviceStats {
   unsigned long long kept;
 };
 
+// The faces the plain FP32 flux kernel leaves to the learned proposal: a list
+// of {face, box} of at most `capacity` entries and its length on the device.
+struct FluxDefer {
+  int2* list = nullptr;
+  unsigned* count = nullptr;
+  unsigned capacity = 0;
+};
+
 // Ideal-gas constants in the bulk arithmetic type, derived once on the host.
 template <typename real>
 struct GasC {
@@ -271,6 +279,8 @@ struct amm_ctx {
   unsigned* box_status = nullptr;  // [nboxes]
   float* closure = nullptr;        // [n] relative closure error (creation only)
   void* mlp = nullptr;             // device copy of the proposal weights (MlpDevice)
+  int2* defer_list = nullptr;      // learned form: faces past the proposal's gate [nf_cap] {face, box}
+  unsigned* defer_count = nullptr; // and their number
   float* harvest = nullptr;        // set only during amm_harvest
   bool mlp_loaded = false;
   double* scratch = nullptr;       // layout conversions for getters/setters
@@ -370,6 +380,9 @@ cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
 // flux_learned.cu: the FP32 flux kernel with the fused proposal network, and
 // the learned form's whole step as one cooperative launch
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
+// flux_pipe.cu: the FP32 forms' flux kernel (learn: list the faces past the
+// proposal's gate in `defer` instead of solving them)
+cudaError_t launch_flux_pipe(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer);
 cudaError_t launch_step_persistent_learned(amm_ctx* c, double cfl);
 cudaError_t prepare_flux_learned();
 

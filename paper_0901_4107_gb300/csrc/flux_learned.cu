@@ -1,19 +1,18 @@
-// Face fluxes of the FP32 learned form: the flux work with the proposal
-// network fused in.  A CTA of H x 128 threads handles H x 128 faces at a
-// time: every thread extrapolates its face (face_prepare) and, if any face of
-// the CTA passes the gate, writes the normalised features as row (t mod 128)
-// of the BF16 operand of its group, one thread issues the tensor-core layers
-// of all groups (tcgen05, FP32 accumulators in tensor memory: group h owns
-// columns 64h..64h+63, reused by both layers), every thread reads its row
-// back, forms p0 = p_TS exp(y) and runs the exact Riemann solver from it
-// (face_finish).  Newton still iterates
-// to the same tolerance, so the result depends on the network only through
-// the iteration count.
+// Face fluxes of the FP32 learned form with the proposal network on the
+// tensor cores.  A CTA of H x 128 threads handles H x 128 prepared faces at a
+// time: every thread whose face passes the gate writes the normalised
+// features as row (t mod 128) of the BF16 operand of its group, one thread
+// issues the tensor-core layers of all groups (tcgen05, FP32 accumulators in
+// tensor memory: group h owns columns 64h..64h+63, reused by both layers),
+// every thread reads its row back, forms p0 = p_TS exp(y) and runs the exact
+// Riemann solver from it.  Newton still iterates to the same tolerance, so
+// the result depends on the network only through the iteration count.
 //
-// Two kernels use it: k_flux_learned (H = 1, the flux phase of the kernel
-// sequence) and k_step_persistent_learned (H = 2, the whole step as one
-// cooperative launch, the batched-ensemble form).  Both run the same per-face
-// arithmetic; compiled under different register budgets, they may contract a
+// Two kernels use it: k_flux_deferred (H = 1: the faces that the plain FP32
+// flux kernel, flux_pipe.cu, found past the gate and listed) and
+// k_step_persistent_learned (H = 2, the whole step as one cooperative
+// launch, the batched-ensemble form).  Both run the same per-face arithmetic;
+// compiled under different register budgets, they may contract a
 // multiply-add differently, so the two step modes agree to FP32 rounding.
 #include <cuda_runtime.h>
 
@@ -25,9 +24,9 @@
 namespace amm {
 
 constexpr int LT = 128;  // faces per MMA group = MMA rows
-// CTAs of k_flux_learned per SM (launch bounds and grid); their tensor memory
+// CTAs of k_flux_deferred per SM (launch bounds and grid); their tensor memory
 // (64 columns each) must fit the SM's 512
-constexpr int LEARNED_CTAS_PER_SM = 6;
+constexpr int LEARNED_CTAS_PER_SM = 4;
 static_assert(LEARNED_CTAS_PER_SM * 64 <= 512, "tensor-memory columns of the co-resident CTAs");
 
 template <int H>
@@ -83,10 +82,15 @@ __device__ __forceinline__ void learned_setup(LearnedSmem<H>& s, const MlpDevice
   if (t == 0) s.bias3 = M->b3;
 }
 
-// H x 128 faces starting at `first` (faces at or past `end` are padding)
-template <int H, bool ENT>
-__device__ __forceinline__ void learned_faces(const HydroView<float>& v, LearnedSmem<H>& s, const Tile& tile,
-                                              int first, uint32_t& phase) {
+// The proposal for the prepared face f, by all H x 128 threads of the CTA:
+// whether this face takes it (`use`) and the starting value p_TS exp(y).
+// A face takes it when its compression is strong: the linearised estimate
+// above PROPOSAL_GATE times the larger pressure (which also places it in the
+// two-shock branch of the standard guess).  If no face of the CTA does, the
+// network is skipped.
+template <int H>
+__device__ __forceinline__ void learned_guess(const HydroView<float>& v, LearnedSmem<H>& s, const FaceWork<float>& f,
+                                              uint32_t& phase, bool& use, float& guess) {
   const int t = threadIdx.x;
   const int warp = t >> 5;
   const int h = t / LT;       // MMA group of this thread
@@ -94,17 +98,6 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
   const int quad = warp & 3;  // tensor-memory lane quadrant this warp may read
   const uint32_t idesc = tc::make_idesc(LT, MLP_HID);
   const float g = v.gas.g;
-  const int k0 = first + t;
-  const bool valid = k0 < tile.end;
-  if (t == 0) s.hdt = (float)(0.5 * box_dt(v, tile.box));
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  FaceWork<float> f;
-  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, s.hdt, f);
-  // does this face's Riemann problem take the proposal?  Only strong
-  // compression: the linearised estimate above PROPOSAL_GATE times the larger
-  // pressure (which also places it in the two-shock branch of the guess)
   const float rb = 0.5f * (f.WppL[0] + f.WppR[0]);
   const float pb = 0.5f * (f.WppL[4] + f.WppR[4]);
   bool need = false;
@@ -112,14 +105,12 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
   {
     const float cL = sqrtf(g * f.WppL[4] / f.WppL[0]), cR = sqrtf(g * f.WppR[4] / f.WppR[0]);
     const float ppv = linearised_pstar(f.WppL[0], f.uL, f.WppL[4], cL, f.WppR[0], f.uR, f.WppR[4], cR);
-    need = valid && ppv > PROPOSAL_GATE * fmaxf(f.WppL[4], f.WppR[4]);
+    need = f.valid && ppv > PROPOSAL_GATE * fmaxf(f.WppL[4], f.WppR[4]);
     if (need) pts = two_shock_pstar(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], ppv, v.gas);
   }
-  if (!__syncthreads_or(need)) {
-    // no face of the CTA takes the proposal: the plain solver
-    face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), false, 0.0f);
-    return;
-  }
+  use = false;
+  guess = 0.0f;
+  if (!__syncthreads_or(need)) return;
   // normalised features (the network's input)
   const float icb = rsqrtf(g * pb / rb);
   {
@@ -177,8 +168,27 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
     for (int j = 0; j < 16; j++) y += s.w3[16 * c + j] * silu_fast(z[j] + s.bias2[16 * c + j]);
   }
   y = fminf(fmaxf(y, -30.0f), 30.0f);
-  const bool use = need && s.ok != 0;  // after a timed-out wait, fall back to the standard guess
-  face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), use, pts * __expf(y));
+  use = need && s.ok != 0;  // after a timed-out wait, fall back to the standard guess
+  guess = pts * __expf(y);
+}
+
+// H x 128 faces starting at `first` (faces at or past `end` are padding)
+template <int H, bool ENT>
+__device__ __forceinline__ void learned_faces(const HydroView<float>& v, LearnedSmem<H>& s, const Tile& tile,
+                                              int first, uint32_t& phase) {
+  const int t = threadIdx.x;
+  const int k0 = first + t;
+  const bool valid = k0 < tile.end;
+  if (t == 0) s.hdt = (float)(0.5 * box_dt(v, tile.box));
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  FaceWork<float> f;
+  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, s.hdt, f);
+  bool use;
+  float guess;
+  learned_guess<H>(v, s, f, phase, use, guess);
+  face_finish<float, H * LT, ENT>(v, f, tile.box, min(H * LT, tile.end - first), use, guess);
 }
 
 template <int H>
@@ -189,16 +199,96 @@ __device__ __forceinline__ void learned_teardown(const HydroView<float>& v, Lear
   if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, 64 * H);
 }
 
-// flux phase alone: CTAs walk the 128-face halves of the face tiles
+// The faces the plain FP32 kernel (k_flux_pipe) deferred: each list entry
+// {face, box} is prepared again from global memory, takes the proposal and
+// is solved; 128 entries per CTA at a time.  CTAs beyond the list's length
+// leave before touching tensor memory, so with an empty list the launch
+// costs only its CTAs' start.
 template <bool ENT>
-__global__ void __launch_bounds__(LT, LEARNED_CTAS_PER_SM) k_flux_learned(HydroView<float> v, int nsub) {
+__global__ void __launch_bounds__(LT, LEARNED_CTAS_PER_SM) k_flux_deferred(HydroView<float> v, FluxDefer d) {
+  const unsigned count = min(*d.count, d.capacity);
+  const unsigned groups = (count + LT - 1) / LT;
+  if (blockIdx.x >= groups) return;
   extern __shared__ uint8_t smem_raw[];
   LearnedSmem<1>& s = learned_smem_ref<1>(smem_raw);
   learned_setup<1>(s, (const MlpDevice*)v.mlp);
+  __shared__ unsigned hist[LT / 32][16];
+  __shared__ unsigned red[LT / 32][8];
+  constexpr int NM = ENT ? 6 : 5;
+  const unsigned full = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (lane < 16) hist[warp][lane] = 0u;
+  __syncwarp();
+  unsigned s_faces = 0, s_iters = 0, s_guard = 0, s_vac = 0, s_fail = 0, s_fb = 0, s_max = 0;
   uint32_t phase = 0;
-  for (int st = blockIdx.x; st < nsub; st += gridDim.x) {
-    const Tile tile = v.ftiles[st >> 1];
-    learned_faces<1, ENT>(v, s, tile, tile.begin + (st & 1) * LT, phase);
+  for (unsigned gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+    const unsigned e = gi * LT + (unsigned)t;
+    const bool valid = e < count;
+    const int2 kb = d.list[valid ? e : gi * LT];
+    const float hdt = (float)(0.5 * box_dt(v, kb.y));
+    FaceWork<float> f;
+    face_prepare<float, ENT>(v, kb.x, valid, hdt, hdt, f);
+    bool use;
+    float guess;
+    learned_guess<1>(v, s, f, phase, use, guess);
+    FaceOut o;
+    face_finish_core<float, ENT>(v, f, use, guess, o);
+    if (v.fixed_acc) {
+      // the list is filled warp by warp from one chunk, so a warp's entries
+      // normally share a box
+      const int b0 = __shfl_sync(full, kb.y, 0);
+      if (__all_sync(full, kb.y == b0)) {
+#pragma unroll
+        for (int a = 0; a < NM; a++) {
+          const unsigned r = __reduce_max_sync(full, o.m[a]);
+          if (lane == 0 && r) atomicMax(v.fmax_bits + FMAX_STRIDE * b0 + a, r);
+        }
+      } else if (valid) {
+#pragma unroll
+        for (int a = 0; a < NM; a++)
+          if (o.m[a]) atomicMax(v.fmax_bits + FMAX_STRIDE * kb.y + a, o.m[a]);
+      }
+    }
+    const unsigned act = __ballot_sync(full, valid);
+    unsigned todo = act;
+    while (todo) {
+      const unsigned val = __shfl_sync(full, o.iters, __ffs(todo) - 1);
+      const unsigned m = __ballot_sync(full, valid && o.iters == val);
+      if (lane == 0) hist[warp][val < 15u ? val : 15u] += __popc(m);
+      todo &= ~m;
+    }
+    s_faces += __popc(act);
+    s_iters += __reduce_add_sync(full, o.iters);
+    s_max = max(s_max, __reduce_max_sync(full, o.iters));
+    s_guard += __popc(__ballot_sync(full, o.guard));
+    s_vac += __popc(__ballot_sync(full, o.vacuum));
+    s_fail += __popc(__ballot_sync(full, o.fail));
+    s_fb += __popc(__ballot_sync(full, o.fallback));
+    if (o.fail) atomicOr(v.box_status + kb.y, (unsigned)ST_NEWTON_CAP);
+  }
+  if (lane == 0) {
+    red[warp][0] = s_faces;
+    red[warp][1] = s_iters;
+    red[warp][2] = s_guard;
+    red[warp][3] = s_vac;
+    red[warp][4] = s_fail;
+    red[warp][5] = s_fb;
+    red[warp][6] = s_max;
+  }
+  __syncthreads();
+  if (t < 16) {
+    unsigned h = 0;
+    for (int w = 0; w < LT / 32; w++) h += hist[w][t];
+    if (h) atomicAdd(&v.stats->hist[t], (unsigned long long)h);
+  } else if (t == 16) {
+    unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+    unsigned mx = 0;
+    for (int w = 0; w < LT / 32; w++) {
+      for (int q = 0; q < 6; q++) a[q] += red[w][q];
+      mx = max(mx, red[w][6]);
+    }
+    stats_add(v.stats, v.box_status, -1, a[0], a[1], (unsigned)a[2], (unsigned)a[3], (unsigned)a[4], (unsigned)a[5],
+              mx);
   }
   learned_teardown<1>(v, s);
 }
@@ -238,16 +328,16 @@ static_assert(4 * 64 * PL_H <= 512, "tensor-memory columns of 4 co-resident CTAs
 cudaError_t prepare_flux_learned() {
   // the largest shared-memory carveout, so that the CTAs the launches assume
   // per SM fit (the occupancy of the cooperative launch is computed with it)
-  for (const void* k : {(const void*)k_flux_learned<false>, (const void*)k_flux_learned<true>,
+  for (const void* k : {(const void*)k_flux_deferred<false>, (const void*)k_flux_deferred<true>,
                         (const void*)k_step_persistent_learned<false>, (const void*)k_step_persistent_learned<true>}) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                                (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_flux_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_flux_deferred<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)learned_smem_bytes<1>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_flux_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_flux_deferred<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)learned_smem_bytes<1>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step_persistent_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -258,17 +348,24 @@ cudaError_t prepare_flux_learned() {
   return e;
 }
 
+// the learned form's flux phase: the plain FP32 kernel, which lists the
+// faces past the gate, then the deferred kernel on the list
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
-  if (!c->mlp) return cudaErrorInvalidValue;
+  if (!c->mlp || !c->defer_list || !c->defer_count) return cudaErrorInvalidValue;
+  FluxDefer d;
+  d.list = c->defer_list;
+  d.count = c->defer_count;
+  d.capacity = (unsigned)c->nf_cap;
+  cudaError_t e = cudaMemsetAsync(c->defer_count, 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_flux_pipe(c, v, true, d)) != cudaSuccess) return e;
   int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto kern = c->opt.entropy ? k_flux_learned<true> : k_flux_learned<false>;
-  // LEARNED_CTAS_PER_SM CTAs per SM, each walking 128-face halves of the
-  // face tiles
-  const int nsub = 2 * c->n_ftiles;
-  const int grid = std::min(nsub, LEARNED_CTAS_PER_SM * sms);
-  kern<<<grid, LT, learned_smem_bytes<1>(), c->stream>>>(v, nsub);
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  auto kern = c->opt.entropy ? k_flux_deferred<true> : k_flux_deferred<false>;
+  // enough CTAs for a list of every face; the ones past its length leave
+  const int groups = (int)std::min<int64_t>((c->nf + LT - 1) / LT, (int64_t)LEARNED_CTAS_PER_SM * sms);
+  kern<<<std::max(groups, 1), LT, learned_smem_bytes<1>(), c->stream>>>(v, d);
   return cudaGetLastError();
 }
 

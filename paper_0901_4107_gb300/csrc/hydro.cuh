@@ -307,15 +307,47 @@ struct FaceStats {
   int iters, guard, vacuum, fail, fallback;
 };
 
+// A cell's record as the flux computation reads it: {rho, v}, {P, s - r},
+// the four gradient vectors and, with the entropy switch, A and grad A.
+template <typename real>
+struct CellRec {
+  R4<real> W, Pc, g0, g1, g2, g3;
+  real A;
+  R4<real> gA;
+};
+
 template <typename real, bool ENT>
-__device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real hsgn, const real* n, real sep,
-                                           const real* c, const real* w, real hdt, real* Wp, real* Wpp,
-                                           real& Aface) {
-  const R4<real> Wi = v.cw[2 * (size_t)i];
-  const R4<real> cg = v.cw[2 * (size_t)i + 1];   // {P, s - r}
-  const real P = cg.x;
+__device__ __forceinline__ CellRec<real> load_cell_rec(const HydroView<real>& v, int i) {
+  CellRec<real> r;
+  r.W = v.cw[2 * (size_t)i];
+  r.Pc = v.cw[2 * (size_t)i + 1];
   const R4<real>* gp = v.grad + 4 * (size_t)i;
-  const R4<real> g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3];
+  r.g0 = gp[0];
+  r.g1 = gp[1];
+  r.g2 = gp[2];
+  r.g3 = gp[3];
+  if constexpr (ENT) {
+    r.A = v.Aw[i];
+    r.gA = v.gradA[i];
+  }
+  return r;
+}
+
+// One side of a face: boost into the face frame, spatial extrapolation to
+// the face centroid and half-step prediction with A(W') at the cell centre
+// (gradients are frame independent).  hsgn = +1/2 for the left cell, -1/2
+// for the right one (f - s_i = hsgn |d| n + c - (s_i - r_i)).
+template <typename real, bool ENT>
+__device__ __forceinline__ void side_extrapolate(const GasC<real>& G, const CellRec<real>& rc, real hsgn,
+                                                 const real* n, real sep, const real* c, const real* w, real hdt,
+                                                 real* Wp, real* Wpp, real& Aface) {
+  const R4<real>& Wi = rc.W;
+  const R4<real>& cg = rc.Pc;   // {P, s - r}
+  const real P = cg.x;
+  const R4<real>& g0 = rc.g0;
+  const R4<real>& g1 = rc.g1;
+  const R4<real>& g2 = rc.g2;
+  const R4<real>& g3 = rc.g3;
   // f - s_i
   const real fx = hsgn * sep * n[0] + c[0] - cg.y;
   const real fy = hsgn * sep * n[1] + c[1] - cg.z;
@@ -326,19 +358,17 @@ __device__ __forceinline__ void side_state(const HydroView<real>& v, int i, real
   Wp[0] = rho; Wp[1] = ux; Wp[2] = uy; Wp[3] = uz; Wp[4] = P;
   const real divv = g1.x + g2.y + g3.z;
   const real ir = (real)1 / rho;
-  // spatial extrapolation to the face centroid plus half-step prediction with
-  // A(W') at the cell centre (gradients are frame independent)
   Wpp[0] = rho + (g0.x * fx + g0.y * fy + g0.z * fz) - hdt * (ux * g0.x + uy * g0.y + uz * g0.z + rho * divv);
   Wpp[1] = ux + (g1.x * fx + g1.y * fy + g1.z * fz) - hdt * (ux * g1.x + uy * g1.y + uz * g1.z + g0.w * ir);
   Wpp[2] = uy + (g2.x * fx + g2.y * fy + g2.z * fz) - hdt * (ux * g2.x + uy * g2.y + uz * g2.z + g1.w * ir);
   Wpp[3] = uz + (g3.x * fx + g3.y * fy + g3.z * fz) - hdt * (ux * g3.x + uy * g3.y + uz * g3.z + g2.w * ir);
   Wpp[4] = P + (g0.w * fx + g1.w * fy + g2.w * fz) -
-           hdt * (v.gas.g * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
+           hdt * (G.g * P * divv + ux * g0.w + uy * g1.w + uz * g2.w);
   if constexpr (ENT) {
     // entropic function A (Sec. 3.5): reconstructed like the primitives and
     // advected, dA/dt = -v'.grad A; the cell value if that is not positive
-    const real A = v.Aw[i];
-    const R4<real> ga = v.gradA[i];
+    const real A = rc.A;
+    const R4<real>& ga = rc.gA;
     const real Ap = A + (ga.x * fx + ga.y * fy + ga.z * fz) - hdt * (ux * ga.x + uy * ga.y + uz * ga.z);
     Aface = Ap > (real)0 ? Ap : A;
   }
@@ -361,16 +391,16 @@ struct FaceWork {
 
 // hdtL, hdtR: the time over which each side is predicted (half the step; with
 // individual time steps, the time from the side's last activation to the
-// middle of the face's step)
+// middle of the face's step).  lr, G0, G1: the face's cells and geometry
+// records; recL, recR: its cells' records (loaded by the caller).
 template <typename real, bool ENT>
-__device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdtL, real hdtR,
-                                             FaceWork<real>& f) {
+__device__ __forceinline__ void face_prepare_rec(const HydroView<real>& v, int k, bool valid, real hdtL, real hdtR,
+                                                 int2 lr, const R4<real>& G0, const R4<real>& G1,
+                                                 const CellRec<real>& recL, const CellRec<real>& recR,
+                                                 FaceWork<real>& f) {
   f.k = k;
   f.valid = valid;
-  const int2 lr = v.lr[k];
   f.lr = lr;
-  const R4<real> G0 = v.fgeo[2 * (size_t)k];
-  const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
   const real n[3] = {G0.x, G0.y, G0.z};
   const real sep = G0.w;
   const real c[3] = {G1.x, G1.y, G1.z};
@@ -387,9 +417,8 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
       wl[0] = a.x; wl[1] = a.y; wl[2] = a.z;
       wr[0] = b.x; wr[1] = b.y; wr[2] = b.z;
     } else if (v.mode == AMM_LAGRANGIAN) {
-      const R4<real> a = v.cw[2 * (size_t)lr.x], b = v.cw[2 * (size_t)lr.y];
-      wl[0] = a.y; wl[1] = a.z; wl[2] = a.w;
-      wr[0] = b.y; wr[1] = b.z; wr[2] = b.w;
+      wl[0] = recL.W.y; wl[1] = recL.W.z; wl[2] = recL.W.w;
+      wr[0] = recR.W.y; wr[1] = recR.W.z; wr[2] = recR.W.w;
     } else {
       const R4<real> a = v.wmesh[lr.x], b = v.wmesh[lr.y];
       wl[0] = a.x; wl[1] = a.y; wl[2] = a.z;
@@ -401,8 +430,8 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
   }
   real WpL[5], WpR[5];
   f.AL = f.AR = (real)0;
-  side_state<real, ENT>(v, lr.x, (real)0.5, n, sep, c, w, hdtL, WpL, f.WppL, f.AL);
-  side_state<real, ENT>(v, lr.y, (real)-0.5, n, sep, c, w, hdtR, WpR, f.WppR, f.AR);
+  side_extrapolate<real, ENT>(v.gas, recL, (real)0.5, n, sep, c, w, hdtL, WpL, f.WppL, f.AL);
+  side_extrapolate<real, ENT>(v.gas, recR, (real)-0.5, n, sep, c, w, hdtR, WpR, f.WppR, f.AR);
   f.fallback = 0;
   if (!(f.WppL[0] > (real)0) || !(f.WppL[4] > (real)0) || !(f.WppR[0] > (real)0) || !(f.WppR[4] > (real)0)) {
 #pragma unroll
@@ -411,8 +440,8 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
       f.WppR[a] = WpR[a];
     }
     if constexpr (ENT) {
-      f.AL = v.Aw[lr.x];
-      f.AR = v.Aw[lr.y];
+      f.AL = recL.A;
+      f.AR = recR.A;
     }
     f.fallback = 1;
   }
@@ -431,11 +460,34 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
   }
 }
 
-// Riemann solve, flux of the moving face, stores, and the CTA's reductions
-// (largest |A F| per component, Newton statistics).  All B threads call it.
-template <typename real, int B, bool ENT>
-__device__ __forceinline__ void face_finish(const HydroView<real>& v, const FaceWork<real>& f, int box, int nf_here,
-                                            bool have_guess, real guess) {
+// the same with every record read from global memory
+template <typename real, bool ENT>
+__device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bool valid, real hdtL, real hdtR,
+                                             FaceWork<real>& f) {
+  const int2 lr = v.lr[k];
+  const R4<real> G0 = v.fgeo[2 * (size_t)k];
+  const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
+  const CellRec<real> recL = load_cell_rec<real, ENT>(v, lr.x);
+  const CellRec<real> recR = load_cell_rec<real, ENT>(v, lr.y);
+  face_prepare_rec<real, ENT>(v, k, valid, hdtL, hdtR, lr, G0, G1, recL, recR, f);
+}
+
+// What one face contributes to the step's reductions: the magnitudes of its
+// A F components as float bits (non-negative floats order like their bits),
+// its Newton iterations and flags.
+struct FaceOut {
+  unsigned m[6];
+  unsigned iters;
+  bool guard, vacuum, fail, fallback;
+};
+
+// Riemann solve, flux of the moving face and its stores (valid faces only);
+// the face's contributions to the reductions in `o` (zero for an invalid
+// face).  have_guess: start Newton from `guess` in place of the two-shock
+// estimate.
+template <typename real, bool ENT>
+__device__ __forceinline__ void face_finish_core(const HydroView<real>& v, const FaceWork<real>& f, bool have_guess,
+                                                 real guess, FaceOut& o) {
   const GasC<real>& G = v.gas;
   const bool valid = f.valid;
   real rhoF, uF, pF, ps;
@@ -480,25 +532,56 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
       v.machf[f.k] = mach;
     }
   }
-  if (sizeof(real) == 4 && v.fixed_acc) {
-    // largest |A F| per component for the exact fixed-point sums (float bits
-    // of non-negative values order like the values)
-    constexpr int NM = ENT ? 6 : 5;
-    unsigned m[NM];
 #pragma unroll
-    for (int a = 0; a < NM; a++) m[a] = 0u;
-    if (valid) {
-      m[0] = __float_as_uint(fabsf((float)fout.x));
-      m[1] = __float_as_uint(fabsf((float)fout.y));
-      m[2] = __float_as_uint(fabsf((float)fout.z));
-      m[3] = __float_as_uint(fabsf((float)fout.w));
-      m[4] = __float_as_uint(fabsf((float)fE));
-      if constexpr (ENT) m[NM - 1] = __float_as_uint(fabsf((float)fS));
-    }
+  for (int a = 0; a < 6; a++) o.m[a] = 0u;
+  if (valid) {
+    o.m[0] = __float_as_uint(fabsf((float)fout.x));
+    o.m[1] = __float_as_uint(fabsf((float)fout.y));
+    o.m[2] = __float_as_uint(fabsf((float)fout.z));
+    o.m[3] = __float_as_uint(fabsf((float)fout.w));
+    o.m[4] = __float_as_uint(fabsf((float)fE));
+    if constexpr (ENT) o.m[5] = __float_as_uint(fabsf((float)fS));
+  }
+  o.iters = valid ? (unsigned)info.iters : 0u;
+  o.guard = valid && info.guard;
+  o.vacuum = valid && info.vacuum;
+  o.fail = valid && info.fail;
+  o.fallback = valid && f.fallback;
+}
+
+// Adds a warp's statistics to the device totals (lane 0 of a full warp
+// calls it with warp-reduced values).
+__device__ __forceinline__ void stats_add(DeviceStats* S, unsigned* box_status, int box, unsigned long long faces,
+                                          unsigned long long iters, unsigned guard, unsigned vacuum, unsigned fail,
+                                          unsigned fallback, unsigned maxit) {
+  if (faces) atomicAdd(&S->faces, faces);
+  if (iters) atomicAdd(&S->newton_iters, iters);
+  if (guard) atomicAdd(&S->guard, (unsigned long long)guard);
+  if (vacuum) atomicAdd(&S->vacuum, (unsigned long long)vacuum);
+  if (fallback) atomicAdd(&S->fallback, (unsigned long long)fallback);
+  if (fail) {
+    atomicAdd(&S->newton_fail, (unsigned long long)fail);
+    atomicOr(&S->status, (unsigned)ST_NEWTON_CAP);
+    if (box >= 0) atomicOr(box_status + box, (unsigned)ST_NEWTON_CAP);
+  }
+  if (maxit) atomicMax(&S->newton_max, maxit);
+}
+
+// Riemann solve, flux of the moving face, stores, and the CTA's reductions
+// (largest |A F| per component, Newton statistics).  All B threads call it.
+template <typename real, int B, bool ENT>
+__device__ __forceinline__ void face_finish(const HydroView<real>& v, const FaceWork<real>& f, int box, int nf_here,
+                                            bool have_guess, real guess) {
+  const bool valid = f.valid;
+  FaceOut o;
+  face_finish_core<real, ENT>(v, f, have_guess, guess, o);
+  if (sizeof(real) == 4 && v.fixed_acc) {
+    // largest |A F| per component for the exact fixed-point sums
+    constexpr int NM = ENT ? 6 : 5;
     __shared__ unsigned wm[B / 32][NM];
 #pragma unroll
     for (int a = 0; a < NM; a++) {
-      const unsigned r = __reduce_max_sync(0xffffffffu, m[a]);
+      const unsigned r = __reduce_max_sync(0xffffffffu, o.m[a]);
       if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5][a] = r;
     }
     __syncthreads();
@@ -511,16 +594,16 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
   // statistics: warp reductions (no contended shared-memory atomics), one
   // slot per warp in shared memory, then a few global atomics per CTA
   const unsigned full = 0xffffffffu;
-  const unsigned it = valid ? (unsigned)info.iters : 0u;
+  const unsigned it = o.iters;
   unsigned mine[22];
 #pragma unroll
   for (int b = 0; b < 15; b++) mine[b] = __popc(__ballot_sync(full, valid && it == (unsigned)b));
   mine[15] = __popc(__ballot_sync(full, valid && it >= 15u));
   mine[16] = __reduce_add_sync(full, it);
-  mine[17] = __popc(__ballot_sync(full, valid && info.guard));
-  mine[18] = __popc(__ballot_sync(full, valid && info.vacuum));
-  mine[19] = __popc(__ballot_sync(full, valid && info.fail));
-  mine[20] = __popc(__ballot_sync(full, valid && f.fallback));
+  mine[17] = __popc(__ballot_sync(full, o.guard));
+  mine[18] = __popc(__ballot_sync(full, o.vacuum));
+  mine[19] = __popc(__ballot_sync(full, o.fail));
+  mine[20] = __popc(__ballot_sync(full, o.fallback));
   mine[21] = __reduce_max_sync(full, it);
   __shared__ unsigned sh[B / 32][22];
   const int wid = (int)threadIdx.x >> 5;
@@ -529,32 +612,18 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
     for (int s = 0; s < 22; s++) sh[wid][s] = mine[s];
   }
   __syncthreads();
-  if (threadIdx.x < 22) {
+  if (threadIdx.x < 16) {
     unsigned tot = 0;
-    for (int w = 0; w < B / 32; w++)
-      tot = (threadIdx.x == 21) ? (sh[w][21] > tot ? sh[w][21] : tot) : tot + sh[w][threadIdx.x];
-    DeviceStats* S = v.stats;
-    const int s = (int)threadIdx.x;
-    if (s < 16) {
-      if (tot) atomicAdd(&S->hist[s], (unsigned long long)tot);
-    } else if (s == 16) {
-      atomicAdd(&S->newton_iters, (unsigned long long)tot);
-      if (nf_here > 0) atomicAdd(&S->faces, (unsigned long long)nf_here);
-    } else if (s == 17) {
-      if (tot) atomicAdd(&S->guard, (unsigned long long)tot);
-    } else if (s == 18) {
-      if (tot) atomicAdd(&S->vacuum, (unsigned long long)tot);
-    } else if (s == 19) {
-      if (tot) {
-        atomicAdd(&S->newton_fail, (unsigned long long)tot);
-        atomicOr(&S->status, (unsigned)ST_NEWTON_CAP);
-        atomicOr(v.box_status + box, (unsigned)ST_NEWTON_CAP);
-      }
-    } else if (s == 20) {
-      if (tot) atomicAdd(&S->fallback, (unsigned long long)tot);
-    } else {
-      if (tot) atomicMax(&S->newton_max, tot);
+    for (int w = 0; w < B / 32; w++) tot += sh[w][threadIdx.x];
+    if (tot) atomicAdd(&v.stats->hist[threadIdx.x], (unsigned long long)tot);
+  } else if (threadIdx.x == 16) {
+    unsigned t[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < B / 32; w++) {
+      for (int s = 0; s < 5; s++) t[s] += sh[w][16 + s];
+      t[5] = sh[w][21] > t[5] ? sh[w][21] : t[5];
     }
+    stats_add(v.stats, v.box_status, box, (unsigned long long)(nf_here > 0 ? nf_here : 0), t[0], t[1], t[2], t[3],
+              t[4], t[5]);
   }
 }
 
@@ -1052,12 +1121,11 @@ template <typename real>
 cudaError_t launch_flux(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
   const bool b128 = c->flux_block == 128;
-  if (c->opt.precision == AMM_FP32_LEARNED) {
-    if constexpr (sizeof(real) == 4) {
-      return launch_flux_learned(c, v);
-    } else {
-      return cudaErrorInvalidValue;
-    }
+  if constexpr (sizeof(real) == 4) {
+    // FP32 forms: the pipelined kernel (flux_pipe.cu); the learned form adds
+    // the deferred proposal kernel
+    if (c->opt.precision == AMM_FP32_LEARNED) return launch_flux_learned(c, v);
+    return launch_flux_pipe(c, v, false, FluxDefer());
   } else {
     const bool ent = c->opt.entropy != 0;
     if (b128 && ent)

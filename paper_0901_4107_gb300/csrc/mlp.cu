@@ -689,6 +689,13 @@ int amm_mlp_attach(amm_ctx* c, const amm_mlp* m) {
     c->err = "amm_mlp_attach: cudaMalloc failed";
     return AMM_ERR_CUDA;
   }
+  // the list of faces past the proposal's gate (room for every face)
+  if (!c->defer_list && (cudaMalloc((void**)&c->defer_list, sizeof(int2) * (size_t)std::max<int64_t>(c->nf_cap, 1)) !=
+                             cudaSuccess ||
+                         cudaMalloc((void**)&c->defer_count, sizeof(unsigned)) != cudaSuccess)) {
+    c->err = "amm_mlp_attach: cudaMalloc failed";
+    return AMM_ERR_CUDA;
+  }
   if (cudaMemcpyAsync(c->mlp, m->packed, sizeof(amm::MlpDevice), cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess ||
       cudaStreamSynchronize(m->stream) != cudaSuccess || amm::prepare_flux_learned() != cudaSuccess) {
     c->err = "amm_mlp_attach: copy failed";

@@ -187,6 +187,11 @@ int amm_retessellate(amm_ctx* c) {
     void** bufs[] = {(void**)&c->lr, (void**)&c->face_perm, (void**)&c->csr, &c->fgeo, &c->igA, &c->igB, &c->igz,
                      (void**)&c->nbr, &c->flux, &c->fluxE, &c->fluxS, &c->machf, (void**)&c->ftiles,
                      (void**)&c->ind_flist, (void**)&c->ind_fstamp, (void**)&c->ind_fdt};
+    const bool had_defer = c->defer_list != nullptr;
+    if (had_defer) {
+      cudaFree(c->defer_list);
+      c->defer_list = nullptr;
+    }
     for (void** b : bufs)
       if (*b) {
         cudaFree(*b);
@@ -207,6 +212,7 @@ int amm_retessellate(amm_ctx* c) {
       cu(cudaMalloc(&c->machf, rs * cap), "alloc");
     }
     cu(cudaMalloc(&c->ftiles, sizeof(Tile) * ((cap + FACE_TILE - 1) / FACE_TILE)), "alloc");
+    if (had_defer) cu(cudaMalloc((void**)&c->defer_list, sizeof(int2) * cap), "alloc");
     if (c->ind_ready) {
       cu(cudaMalloc(&c->ind_flist, sizeof(int) * cap), "alloc");
       cu(cudaMalloc(&c->ind_fstamp, sizeof(int) * cap), "alloc");
