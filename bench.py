@@ -133,9 +133,10 @@ def peaks():
 # only while these are unchanged)
 _COMMON = ["amm_internal.cuh", "hydro.cuh", "riemann.cuh", "hydro_f32.cu", "../../include/amm.h"]
 KERNEL_SOURCES = {
-    "gradients": _COMMON, "flux": _COMMON, "update": _COMMON,
+    "gradients": _COMMON, "update": _COMMON,
+    "flux": _COMMON + ["flux_chunks.cu", "learned.cuh"],
     "flux_fp64": ["amm_internal.cuh", "hydro.cuh", "riemann.cuh", "hydro_f64.cu", "../../include/amm.h"],
-    "learned_flux": _COMMON + ["flux_learned.cu", "learned.cuh", "tc.cuh", "persistent.cuh"],
+    "learned_flux": _COMMON + ["flux_chunks.cu", "flux_learned.cu", "learned.cuh", "tc.cuh", "persistent.cuh"],
 }
 
 

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # The FP32 forms take the fast single-precision paths (approximate division
 # and square root, denormals flushed); FP64 code is unaffected by these flags.
-PER_FILE = {f: ["--use_fast_math"] for f in ("hydro_f32.cu", "persistent_f32.cu", "flux_learned.cu", "flux_pipe.cu")}
+PER_FILE = {f: ["--use_fast_math"] for f in ("hydro_f32.cu", "persistent_f32.cu", "flux_learned.cu", "flux_chunks.cu")}
 
 
 def nvcc():

@@ -380,9 +380,9 @@ cudaError_t launch_set_wmesh(amm_ctx* c, const double* w_aos_device);
 // flux_learned.cu: the FP32 flux kernel with the fused proposal network, and
 // the learned form's whole step as one cooperative launch
 cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v);
-// flux_pipe.cu: the FP32 forms' flux kernel (learn: list the faces past the
+// flux_chunks.cu: the FP32 forms' flux kernel (learn: list the faces past the
 // proposal's gate in `defer` instead of solving them)
-cudaError_t launch_flux_pipe(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer);
+cudaError_t launch_flux_chunks(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer);
 cudaError_t launch_step_persistent_learned(amm_ctx* c, double cfl);
 cudaError_t prepare_flux_learned();
 

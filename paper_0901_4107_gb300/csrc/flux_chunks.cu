@@ -246,7 +246,7 @@ static cudaError_t launch_chunks_b(amm_ctx* c, const HydroView<float>& v, bool l
   return ent ? launch_chunks<B, true, false>(c, v, defer) : launch_chunks<B, false, false>(c, v, defer);
 }
 
-cudaError_t launch_flux_pipe(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer) {
+cudaError_t launch_flux_chunks(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer) {
   return c->flux_block == 256 ? launch_chunks_b<256>(c, v, learn, defer) : launch_chunks_b<128>(c, v, learn, defer);
 }
 

@@ -9,7 +9,7 @@
 // the result depends on the network only through the iteration count.
 //
 // Two kernels use it: k_flux_deferred (H = 1: the faces that the plain FP32
-// flux kernel, flux_pipe.cu, found past the gate and listed) and
+// flux kernel, flux_chunks.cu, found past the gate and listed) and
 // k_step_persistent_learned (H = 2, the whole step as one cooperative
 // launch, the batched-ensemble form).  Both run the same per-face arithmetic;
 // compiled under different register budgets, they may contract a
@@ -199,7 +199,7 @@ __device__ __forceinline__ void learned_teardown(const HydroView<float>& v, Lear
   if (threadIdx.x < 32) tc::tmem_dealloc(s.tmem, 64 * H);
 }
 
-// The faces the plain FP32 kernel (k_flux_pipe) deferred: each list entry
+// The faces the plain FP32 kernel (k_flux_chunks, flux_chunks.cu) deferred: each list entry
 // {face, box} is prepared again from global memory, takes the proposal and
 // is solved; 128 entries per CTA at a time.  CTAs beyond the list's length
 // leave before touching tensor memory, so with an empty list the launch
@@ -358,7 +358,7 @@ cudaError_t launch_flux_learned(amm_ctx* c, const HydroView<float>& v) {
   d.capacity = (unsigned)c->nf_cap;
   cudaError_t e = cudaMemsetAsync(c->defer_count, 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
-  if ((e = launch_flux_pipe(c, v, true, d)) != cudaSuccess) return e;
+  if ((e = launch_flux_chunks(c, v, true, d)) != cudaSuccess) return e;
   int dev = 0, sms = 148;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -1122,10 +1122,10 @@ cudaError_t launch_flux(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
   const bool b128 = c->flux_block == 128;
   if constexpr (sizeof(real) == 4) {
-    // FP32 forms: the pipelined kernel (flux_pipe.cu); the learned form adds
+    // FP32 forms: the persistent chunk kernel (flux_chunks.cu); the learned form adds
     // the deferred proposal kernel
     if (c->opt.precision == AMM_FP32_LEARNED) return launch_flux_learned(c, v);
-    return launch_flux_pipe(c, v, false, FluxDefer());
+    return launch_flux_chunks(c, v, false, FluxDefer());
   } else {
     const bool ent = c->opt.entropy != 0;
     if (b128 && ent)
