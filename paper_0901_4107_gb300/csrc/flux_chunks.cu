@@ -38,7 +38,7 @@ namespace amm {
 // CTAs per SM each shape is compiled for (launch bounds, and so registers)
 template <int B>
 constexpr int chunk_ctas_per_sm() {
-  return B == 256 ? 2 : 6;
+  return B == 256 ? 3 : 7;
 }
 
 // per warp: iteration histogram, statistics sums, running |A F| maxima
@@ -48,14 +48,6 @@ struct ChunkSmem {
   unsigned red[B / 32][8];
   unsigned fmax[B / 32][6];
 };
-
-// 32 bytes from global memory that no thread writes during the kernel (the
-// address is 32-byte aligned): one 256-bit load
-__device__ __forceinline__ void ldg256(const void* p, R4<float>& a, R4<float>& b) {
-  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-      : "l"(p));
-}
 
 // a cell's record: {rho, v}, {P, s - r} (32 bytes) and its gradients (64)
 template <bool ENT>
@@ -94,7 +86,7 @@ __device__ __forceinline__ void flush_fmax(const HydroView<float>& v, ChunkSmem<
   }
 }
 
-template <int B, bool ENT, bool LEARN>
+template <int B, bool ENT, bool LEARN, bool STATIC>
 __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(HydroView<float> v, int nchunks, int per_cta,
                                                                           FluxDefer defer) {
   constexpr int CPT = FACE_TILE / B;   // chunks per face tile
@@ -116,6 +108,10 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
   Tile T1 = (c0 + 1 < c1) ? v.ftiles[(c0 + 1) / CPT] : T0;
   bool vtmp;
   int2 L0 = v.lr[chunk_face<B>(c0, T0, vtmp)];
+  // half the box's step, in FP32 (the FP64 arithmetic of box_dt runs on the
+  // narrow FP64 pipe, so once per box, not per face)
+  int hbox = T0.box;
+  float hdt = (float)(0.5 * box_dt(v, hbox));
 
   for (int c = c0; c < c1; c++) {
     const bool more1 = c + 1 < c1;
@@ -124,14 +120,17 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
     const int2 L1 = more1 ? v.lr[chunk_face<B>(c + 1, T1, vtmp)] : L0;
     bool valid;
     const int k = chunk_face<B>(c, T0, valid);
-    const float hdt = (float)(0.5 * box_dt(v, T0.box));
+    if (T0.box != hbox) {
+      hbox = T0.box;
+      hdt = (float)(0.5 * box_dt(v, hbox));
+    }
     FaceWork<float> f;
     {
       R4<float> G0, G1;
       ldg256(v.fgeo + 2 * (size_t)k, G0, G1);
       const CellRec<float> recL = load_rec256<ENT>(v, L0.x);
       const CellRec<float> recR = load_rec256<ENT>(v, L0.y);
-      face_prepare_rec<float, ENT>(v, k, valid, hdt, hdt, L0, G0, G1, recL, recR, f);
+      face_prepare_rec<float, ENT, STATIC>(v, k, valid, hdt, hdt, L0, G0, G1, recL, recR, f);
     }
     bool mine = valid;
     if constexpr (LEARN) {
@@ -221,9 +220,9 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
   }
 }
 
-template <int B, bool ENT, bool LEARN>
+template <int B, bool ENT, bool LEARN, bool STATIC>
 static cudaError_t launch_chunks(amm_ctx* c, const HydroView<float>& v, const FluxDefer& defer) {
-  auto kern = k_flux_chunks<B, ENT, LEARN>;
+  auto kern = k_flux_chunks<B, ENT, LEARN, STATIC>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -239,11 +238,19 @@ static cudaError_t launch_chunks(amm_ctx* c, const HydroView<float>& v, const Fl
   return cudaGetLastError();
 }
 
+template <int B, bool STATIC>
+static cudaError_t launch_chunks_s(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer) {
+  const bool ent = c->opt.entropy != 0;
+  if (learn)
+    return ent ? launch_chunks<B, true, true, STATIC>(c, v, defer) : launch_chunks<B, false, true, STATIC>(c, v, defer);
+  return ent ? launch_chunks<B, true, false, STATIC>(c, v, defer) : launch_chunks<B, false, false, STATIC>(c, v, defer);
+}
+
 template <int B>
 static cudaError_t launch_chunks_b(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer) {
-  const bool ent = c->opt.entropy != 0;
-  if (learn) return ent ? launch_chunks<B, true, true>(c, v, defer) : launch_chunks<B, false, true>(c, v, defer);
-  return ent ? launch_chunks<B, true, false>(c, v, defer) : launch_chunks<B, false, false>(c, v, defer);
+  // a static mesh (no mesh velocity anywhere) has its own instantiation
+  if (c->opt.mesh_motion == AMM_EULERIAN) return launch_chunks_s<B, true>(c, v, learn, defer);
+  return launch_chunks_s<B, false>(c, v, learn, defer);
 }
 
 cudaError_t launch_flux_chunks(amm_ctx* c, const HydroView<float>& v, bool learn, const FluxDefer& defer) {

@@ -115,7 +115,7 @@ __global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad,
 // bulk-precision face and cell geometry.
 template <typename real>
 __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr, const R4<real>* fgeo,
-                                     const R4<real>* cgeo, R4<real>* igA, R4<real>* igB, real* igz, int* nbr) {
+                                     const R4<real>* cgeo, R4<real>* igAB, real* igz, int* nbr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const R4<real> cg = cgeo[i];
@@ -137,8 +137,8 @@ __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr,
     b.y = a_h * G0.z;
     b.z = hs * G0.x + G1.x - cg.y;
     b.w = hs * G0.y + G1.y - cg.z;
-    igA[q] = a;
-    igB[q] = b;
+    igAB[2 * (size_t)q] = a;
+    igAB[2 * (size_t)q + 1] = b;
     igz[q] = hs * G0.z + G1.z - cg.w;
     nbr[q] = e.y;
   }
@@ -212,15 +212,15 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
     k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad,
                                                        (R4<double>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<double><<<nbc, 256, 0, c->stream>>>(
-        (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igA,
-        (R4<double>*)c->igB, (double*)c->igz, c->nbr);
+        (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igAB,
+        (double*)c->igz, c->nbr);
   } else {
     k_cast4<float><<<(unsigned)((nfg + 255) / 256), 256, 0, c->stream>>>(fg64, (R4<float>*)c->fgeo, nfg);
     k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad,
                                                       (R4<float>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<float><<<nbc, 256, 0, c->stream>>>(
-        (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igA,
-        (R4<float>*)c->igB, (float*)c->igz, c->nbr);
+        (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igAB,
+        (float*)c->igz, c->nbr);
   }
   return cudaGetLastError();
 }

@@ -29,6 +29,21 @@ __device__ __forceinline__ double box_dt(const HydroView<real>& v, int b) {
   return v.dt_box[b];
 }
 
+// 32 bytes of FP32 data from global memory that no thread writes during the
+// kernel (32-byte aligned): one 256-bit load.  A warp's gather of 32
+// scattered records costs one L1 wavefront per record for each load
+// instruction, so one 32-byte load costs half as many as two 16-byte loads.
+__device__ __forceinline__ void ldg256(const void* p, R4<float>& a, R4<float>& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
+// the same for FP64 data: two 32-byte halves of a 64-byte record
+__device__ __forceinline__ void ldg256(const void* p, R4<double>& a) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a.x), "=d"(a.y), "=d"(a.z), "=d"(a.w) : "l"(p));
+}
+
 // ------------------------------------------------------------------ A1
 // Returns P.  The FP32 form keeps only the thermal-energy difference
 // E - |p|^2/(2m) in FP64 (it cancels when the flow is supersonic); the FP64
@@ -154,14 +169,24 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
 #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
     // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out),
-    // with the geometric weights of the incidence precomputed (igA, igB)
+    // with the geometric weights of the incidence precomputed (igAB)
     const int j = jn;
     if (q + G < q1) jn = v.nbr[q + G];
-    const R4<real> a4 = v.igA[q];
-    const R4<real> b4 = v.igB[q];
-    // the neighbour's record: both halves lie in one 32-byte sector
-    const R4<real> Wj = v.cw[2 * (size_t)j];
-    const real Pj = v.cw[2 * (size_t)j + 1].x;
+    R4<real> a4, b4, Wj;
+    real Pj;
+    if constexpr (sizeof(real) == 4) {
+      // the incidence's weights and the neighbour's record {W}, {P, s - r}:
+      // one 32-byte load each
+      ldg256(v.igAB + 2 * (size_t)q, a4, b4);
+      R4<real> Pc;
+      ldg256(v.cw + 2 * (size_t)j, Wj, Pc);
+      Pj = Pc.x;
+    } else {
+      a4 = v.igAB[2 * (size_t)q];
+      b4 = v.igAB[2 * (size_t)q + 1];
+      Wj = v.cw[2 * (size_t)j];
+      Pj = v.cw[2 * (size_t)j + 1].x;
+    }
     real phi_j[NV];
     phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = Pj;
     if constexpr (ENT) phi_j[5] = v.Aw[j];
@@ -197,7 +222,7 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
   #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
       // f - s_i of the incidence
-      const R4<real> b4 = v.igB[q];
+      const R4<real> b4 = v.igAB[2 * (size_t)q + 1];
       const real fx = b4.z, fy = b4.w, fz = v.igz[q];
 #pragma unroll
       for (int a = 0; a < NV; a++) {
@@ -393,7 +418,9 @@ struct FaceWork {
 // individual time steps, the time from the side's last activation to the
 // middle of the face's step).  lr, G0, G1: the face's cells and geometry
 // records; recL, recR: its cells' records (loaded by the caller).
-template <typename real, bool ENT>
+// STATIC: the caller knows the mesh is static (w = 0), so the face-velocity
+// work compiles away.
+template <typename real, bool ENT, bool STATIC = false>
 __device__ __forceinline__ void face_prepare_rec(const HydroView<real>& v, int k, bool valid, real hdtL, real hdtR,
                                                  int2 lr, const R4<real>& G0, const R4<real>& G1,
                                                  const CellRec<real>& recL, const CellRec<real>& recR,
@@ -408,7 +435,7 @@ __device__ __forceinline__ void face_prepare_rec(const HydroView<real>& v, int k
   // face velocity: mean of the generators' velocities plus the normal motion
   // of the face centroid from their relative motion about the midpoint
   real w[3] = {(real)0, (real)0, (real)0};
-  if (v.mode != AMM_EULERIAN) {
+  if (!STATIC && v.mode != AMM_EULERIAN) {
     real wl[3], wr[3];
     if (v.regularize) {
       // the generators' velocities with the regularity correction, from the
@@ -1051,8 +1078,7 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.fluxE = (real*)c->fluxE;
   v.csr_off = c->csr_off;
   v.csr = c->csr;
-  v.igA = (const R4<real>*)c->igA;
-  v.igB = (const R4<real>*)c->igB;
+  v.igAB = (const R4<real>*)c->igAB;
   v.igz = (const real*)c->igz;
   v.nbr = c->nbr;
   v.ctiles = c->ctiles;
