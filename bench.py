@@ -614,6 +614,60 @@ def bench_train_workload(args, g, world, rank, local):
     }
 
 
+def bench_gated(g, n=48, mach=4.0, seed=9, steps=50, warmup=5, oracle_check=True):
+    """The learned proposal where its gate fires often: a held-out turbulent
+    box (a seed the training never saw) at high Mach number and modest
+    resolution, Lagrangian.  FP32 with and without the proposal: faces/s of
+    whole steps (CUDA graph, state reset and L2 flushed between steps),
+    Newton iterations per face, the share of faces past the gate, and each
+    form's error against the oracle after one step."""
+    import numpy as np
+    from harness import ics
+    from paper_0901_4107_gb300 import learned
+    amm, torch = g.amm, g.torch
+    P = ics.turbulent_3d(n, seed=seed, mach=mach)
+    Q0 = P.conserved()
+    Q0d = torch.from_numpy(Q0).to("cuda")
+    st = learned.harvest(P.tess, Q0, P.gamma, "lagrangian", 1, torch=torch)
+    ratio = torch.empty(st.shape[0], dtype=torch.float32, device="cuda")
+    x = torch.empty((st.shape[0], 6), dtype=torch.float32, device="cuda")
+    amm.amm_mlp_features(P.gamma, st.shape[0], st.data_ptr(), x.data_ptr(), 0, 0, ratio.data_ptr())
+    torch.cuda.synchronize()
+    out = {"workload": "held-out turbulent box: %d^3 jittered lattice, seed %d (not in training), rms Mach %.1f, "
+                       "gamma 5/3, Lagrangian" % (n, seed, mach),
+           "faces": P.n_faces, "faces_past_gate": float((ratio > 1.25).float().mean().item())}
+    ref = dt = fl = None
+    if oracle_check:
+        from oracle import oracle as O
+        M = O.Mesh(P.tess)
+        geom = O.geometry(M)
+        ref, dt, _, _ = O.step(M, Q0, P.gamma, "lagrangian", cfl=CFL, geom=geom)
+        fl = floors(Q0, O.primitives(M, Q0, geom[0], P.gamma), 3, P.gamma)
+    for prec in ("fp32", "fp32_learned"):
+        ctx = amm.create_from_mesh(P.tess, Q0, P.gamma, precision=prec, mesh_motion="lagrangian",
+                                   stream=g.stream.cuda_stream)
+        if prec == "fp32_learned":
+            amm.amm_mlp_attach(ctx, g.proposal())
+        t = g.tune(ctx, None, 3)
+        # the kernel sequence (the learned form's deferred proposal kernel),
+        # not the one-launch step the autotuner may prefer for a small box
+        amm.amm_set_tuning(ctx, t["grad_lanes"], t["update_lanes"], t["flux_block"], 0)
+        ms, ker, _ = timed_form(g, ctx, Q0d, steps, warmup, kernel_steps=20)
+        r = {"value": P.n_faces / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
+             "flux_ms": ker.get("flux")}
+        r.update(newton_stats(amm, ctx, Q0))
+        if ref is not None:
+            amm.amm_set_state(ctx, Q0)
+            amm.amm_step(ctx, dt)
+            r["err_max"], r["err_p999"] = parity_errors(amm.amm_get_state(ctx), ref, fl)
+        out[prec] = r
+        amm.amm_destroy(ctx)
+    out["learned_vs_fp32"] = out["fp32_learned"]["value"] / out["fp32"]["value"]
+    out["newton_iterations_saved_per_face"] = (out["fp32"]["newton_iters_per_face"] -
+                                                out["fp32_learned"]["newton_iters_per_face"])
+    return out
+
+
 def bench_box(args, g, world, rank, local):
     """Single-box workloads: turbulent64, lognormal192, learned192."""
     import numpy as np
@@ -752,6 +806,9 @@ def bench_box(args, g, world, rank, local):
             forms[prec]["vs_fp64"] = forms[prec]["value"] / forms["fp64"]["value"]
     if wl == "turbulent64":
         line["proposal_training"] = bench_training(g, P, motion)
+    if "fp32_learned" in forms:
+        # the learned proposal where its gate fires often (a held-out field)
+        line["proposal_where_gated"] = bench_gated(g, oracle_check=not args.no_cpu)
     ke = max(3, min(args.steps, 200))
     e2e_s, nbytes = e2e_rate(g, ctxs[head], Q0, ke)
     line["e2e"] = {"value": nf / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -414,6 +414,12 @@ int amm_harvest(amm_ctx* ctx, double cfl, float* states_device);
 #define AMM_PROPOSAL_GATE 1.25
 int amm_mlp_features(double gamma, int64_t n, const float* states_device, float* x_device, float* pbar_device,
                      float* pts_device, float* ratio_device, void* stream);
+/* the training target of each face state [n]: log(p* / p_TS), with p* the
+ * exact star pressure (FP64 Newton from the standard guess to the relative
+ * tolerance tol) and p_TS the two-shock estimate in FP32 as the flux kernel
+ * forms it; NaN where the states generate vacuum or Newton did not converge */
+int amm_mlp_targets(double gamma, int64_t n, const float* states_device, double tol, float* target_device,
+                    void* stream);
 /* exact star pressure of each face state in FP64 (Newton from the standard
  * guess to the relative tolerance tol); NaN where the states generate vacuum */
 int amm_riemann_pstar(double gamma, int64_t n, const float* states_device, double tol, float* pstar_device,

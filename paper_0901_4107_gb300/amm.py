@@ -127,6 +127,7 @@ _SIGS = {
     "amm_harvest": (_I, [_P, _D, _P]),
     "amm_mlp_features": (_I, [_D, _I64, _P, _P, _P, _P, _P, _P]),
     "amm_riemann_pstar": (_I, [_D, _I64, _P, _D, _P, _P]),
+    "amm_mlp_targets": (_I, [_D, _I64, _P, _D, _P, _P]),
     "amm_get_kernel_times": (_I, [_P, _P]),
 }
 
@@ -641,6 +642,12 @@ def amm_riemann_pstar(gamma, n, states_ptr, tol, pstar_ptr, stream=None):
     rc = lib().amm_riemann_pstar(float(gamma), int(n), _ptr(states_ptr), float(tol), _ptr(pstar_ptr), _ptr(stream))
     if rc != AMM_OK:
         raise AmmError(rc, "amm_riemann_pstar failed")
+
+
+def amm_mlp_targets(gamma, n, states_ptr, tol, target_ptr, stream=None):
+    rc = lib().amm_mlp_targets(float(gamma), int(n), _ptr(states_ptr), float(tol), _ptr(target_ptr), _ptr(stream))
+    if rc != AMM_OK:
+        raise AmmError(rc, "amm_mlp_targets failed")
 
 
 def pack_params(p):

@@ -133,12 +133,14 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
       face_prepare_rec<float, ENT, STATIC>(v, k, valid, hdt, hdt, L0, G0, G1, recL, recR, f);
     }
     bool mine = valid;
+    float cs[3];   // c_L, c_R and the linearised star pressure, for the gate and the solver
     if constexpr (LEARN) {
       // faces that take the proposal go to the deferred list, warp by warp
       const float g = v.gas.g;
-      const float cL = sqrtf(g * f.WppL[4] / f.WppL[0]), cR = sqrtf(g * f.WppR[4] / f.WppR[0]);
-      const float ppv = linearised_pstar(f.WppL[0], f.uL, f.WppL[4], cL, f.WppR[0], f.uR, f.WppR[4], cR);
-      const bool need = valid && ppv > PROPOSAL_GATE * fmaxf(f.WppL[4], f.WppR[4]);
+      cs[0] = sqrtf(g * f.WppL[4] / f.WppL[0]);
+      cs[1] = sqrtf(g * f.WppR[4] / f.WppR[0]);
+      cs[2] = linearised_pstar(f.WppL[0], f.uL, f.WppL[4], cs[0], f.WppR[0], f.uR, f.WppR[4], cs[1]);
+      const bool need = valid && cs[2] > PROPOSAL_GATE * fmaxf(f.WppL[4], f.WppR[4]);
       const unsigned nb = __ballot_sync(full, need);
       if (nb) {
         unsigned base = 0;
@@ -157,10 +159,12 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
 #pragma unroll
         for (int a = 0; a < 5; a++) f.WppR[a] = f.WppL[a];
         f.uR = f.uL;
+        cs[1] = cs[0];
+        cs[2] = f.WppL[4];
       }
     }
     FaceOut o;
-    face_finish_core<float, ENT>(v, f, false, 0.0f, o);
+    face_finish_core<float, ENT>(v, f, false, 0.0f, o, LEARN, cs);
     if (fixed) {
 #pragma unroll
       for (int a = 0; a < NM; a++) {

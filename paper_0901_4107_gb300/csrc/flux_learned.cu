@@ -70,10 +70,14 @@ __device__ __forceinline__ void learned_setup(LearnedSmem<H>& s, const MlpDevice
     tc::mbar_init(&s.mbar, 1);
     s.ok = 1;
   }
-  for (int i = t; i < MLP_HID * 16; i += H * LT)
-    *reinterpret_cast<__nv_bfloat16*>(s.b1 + tc::kmajor_offset(i / 16, i % 16, 16)) = M->W1[i];
-  for (int i = t; i < MLP_HID * MLP_HID; i += H * LT)
-    *reinterpret_cast<__nv_bfloat16*>(s.b2 + tc::kmajor_offset(i / MLP_HID, i % MLP_HID, MLP_HID)) = M->W2[i];
+  // eight consecutive k of one row are one 16-byte row segment of a core
+  // matrix: 16-byte loads and stores, all independent
+  const uint4* w1 = reinterpret_cast<const uint4*>(M->W1);
+  const uint4* w2 = reinterpret_cast<const uint4*>(M->W2);
+  for (int i = t; i < MLP_HID * 16 / 8; i += H * LT)
+    *reinterpret_cast<uint4*>(s.b1 + tc::kmajor_offset(i / 2, 8 * (i % 2), 16)) = w1[i];
+  for (int i = t; i < MLP_HID * MLP_HID / 8; i += H * LT)
+    *reinterpret_cast<uint4*>(s.b2 + tc::kmajor_offset(i / 8, 8 * (i % 8), MLP_HID)) = w2[i];
   if (t < MLP_HID) {
     s.bias1[t] = M->b1[t];
     s.bias2[t] = M->b2[t];

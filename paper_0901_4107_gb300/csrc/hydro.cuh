@@ -511,16 +511,20 @@ struct FaceOut {
 // Riemann solve, flux of the moving face and its stores (valid faces only);
 // the face's contributions to the reductions in `o` (zero for an invalid
 // face).  have_guess: start Newton from `guess` in place of the two-shock
-// estimate.
+// estimate.  pre: the caller has the sides' sound speeds and the linearised
+// star pressure (cs = {c_L, c_R, p_pv}) already.
 template <typename real, bool ENT>
 __device__ __forceinline__ void face_finish_core(const HydroView<real>& v, const FaceWork<real>& f, bool have_guess,
-                                                 real guess, FaceOut& o) {
+                                                 real guess, FaceOut& o, bool pre = false, const real* cs = nullptr) {
   const GasC<real>& G = v.gas;
   const bool valid = f.valid;
   real rhoF, uF, pF, ps;
   RiemannInfo info;
-  const int side = riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.tol_r, v.maxit,
-                                  have_guess, guess, rhoF, uF, pF, info, ps);
+  const int side =
+      pre ? riemann_sample_c(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], cs[0], cs[1], cs[2], G, v.tol,
+                             v.tol_r, v.maxit, have_guess, guess, rhoF, uF, pF, info, ps)
+          : riemann_sample(f.WppL[0], f.uL, f.WppL[4], f.WppR[0], f.uR, f.WppR[4], G, v.tol, v.tol_r, v.maxit,
+                           have_guess, guess, rhoF, uF, pF, info, ps);
   const real* Wt = side ? f.WppR : f.WppL;
   const real ut = side ? f.uR : f.uL;
   real vlab[3];

@@ -494,6 +494,31 @@ __global__ void k_riemann_pstar(double gamma, int64_t m, const float* st, double
   pstar[i] = info.fail ? __int_as_float(0x7fc00000) : (float)p;
 }
 
+// training target of each face state: log(p* / p_TS), the correction of the
+// two-shock estimate (FP32, as the flux kernel forms it) that takes it to the
+// exact star pressure (FP64 Newton to tol); NaN without a star region
+__global__ void k_mlp_targets(double gamma, int64_t m, const float* st, double tol, int maxit, float* target) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const float* s = st + 6 * i;
+  const double rL = s[0], uL = s[1], pL = s[2], rR = s[3], uR = s[4], pR = s[5];
+  const GasC<double> G(gamma);
+  const double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  if (!(rL > 0.0) || !(rR > 0.0) || !(pL > 0.0) || !(pR > 0.0) || G.two_gm1 * (cL + cR) <= uR - uL) {
+    target[i] = __int_as_float(0x7fc00000);
+    return;
+  }
+  RiemannInfo info{0, 0, 0, 0};
+  NewtonTail<double> nt;
+  const double p0 = standard_guess(rL, uL, pL, cL, rR, uR, pR, cR, G);
+  const double p = newton_pstar(p0, rL, uL, pL, cL, rR, uR, pR, cR, G, tol, tol, maxit, info, nt);
+  const GasC<float> Gf(gamma);
+  const float cLf = sqrtf(Gf.g * s[2] / s[0]), cRf = sqrtf(Gf.g * s[5] / s[3]);
+  const float ppv = linearised_pstar(s[0], s[1], s[2], cLf, s[3], s[4], s[5], cRf);
+  const float pts = two_shock_pstar(s[0], s[1], s[2], s[3], s[4], s[5], ppv, Gf);
+  target[i] = (info.fail || !(pts > 0.0f)) ? __int_as_float(0x7fc00000) : (float)log(p / (double)pts);
+}
+
 }  // namespace amm
 
 // ============================================================ C ABI
@@ -714,6 +739,14 @@ int amm_mlp_features(double gamma, int64_t n, const float* states_device, float*
   if (!(gamma > 1.0) || n < 1 || !states_device || !x_device) return AMM_ERR_INVALID_ARG;
   amm::k_mlp_features<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
       gamma, n, states_device, x_device, pbar_device, pts_device, ratio_device);
+  return cudaGetLastError() == cudaSuccess ? AMM_OK : AMM_ERR_CUDA;
+}
+
+int amm_mlp_targets(double gamma, int64_t n, const float* states_device, double tol, float* target_device,
+                    void* stream) {
+  if (!(gamma > 1.0) || n < 1 || !states_device || !target_device || !(tol > 0.0)) return AMM_ERR_INVALID_ARG;
+  amm::k_mlp_targets<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(gamma, n, states_device, tol, 200,
+                                                                                   target_device);
   return cudaGetLastError() == cudaSuccess ? AMM_OK : AMM_ERR_CUDA;
 }
 

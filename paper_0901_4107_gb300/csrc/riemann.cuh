@@ -81,11 +81,10 @@ __device__ __forceinline__ real two_shock_pstar(real rhoL, real uL, real pL, rea
 // when both waves are rarefactions, and the linearised one is kept where it
 // passes its own test.
 template <typename real>
-__device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real cL, real rhoR, real uR, real pR,
-                                               real cR, const GasC<real>& G, bool have = false,
-                                               real proposal = (real)0) {
+__device__ __forceinline__ real standard_guess_ppv(real rhoL, real uL, real pL, real cL, real rhoR, real uR, real pR,
+                                                   real cR, real ppv, const GasC<real>& G, bool have = false,
+                                                   real proposal = (real)0) {
   const real du = uR - uL;
-  const real ppv = linearised_pstar(rhoL, uL, pL, cL, rhoR, uR, pR, cR);
   const real pmin = pL < pR ? pL : pR, pmax = pL > pR ? pL : pR;
   real p0;
   if (pmax / pmin <= (real)2 && ppv >= pmin && ppv <= pmax) {
@@ -101,6 +100,14 @@ __device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real
   }
   const real pfloor = (real)1e-10 * (real)0.5 * (pL + pR);
   return (p0 > pfloor) ? p0 : pfloor;
+}
+
+template <typename real>
+__device__ __forceinline__ real standard_guess(real rhoL, real uL, real pL, real cL, real rhoR, real uR, real pR,
+                                               real cR, const GasC<real>& G, bool have = false,
+                                               real proposal = (real)0) {
+  return standard_guess_ppv(rhoL, uL, pL, cL, rhoR, uR, pR, cR, linearised_pstar(rhoL, uL, pL, cL, rhoR, uR, pR, cR),
+                            G, have, proposal);
 }
 
 struct RiemannInfo {
@@ -220,17 +227,18 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
 // Returns side of the contact (0: left, 1: right) for the transverse
 // velocity; rho = P = 0 inside generated vacuum.  pstar: the star pressure
 // (0 when vacuum is generated).
+// cL, cR: the sides' sound speeds; ppv: the linearised star pressure (the
+// caller may have formed them already, for the proposal's gate).
 template <typename real>
-__device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real rhoR, real uR, real pR,
-                                              const GasC<real>& G, double tol, real tol_r, int maxit, bool have_guess,
-                                              real guess, real& rhoF, real& uF, real& pF, RiemannInfo& info,
-                                              real& pstar) {
+__device__ __forceinline__ int riemann_sample_c(real rhoL, real uL, real pL, real rhoR, real uR, real pR, real cL,
+                                                real cR, real ppv, const GasC<real>& G, double tol, real tol_r,
+                                                int maxit, bool have_guess, real guess, real& rhoF, real& uF, real& pF,
+                                                RiemannInfo& info, real& pstar) {
   pstar = (real)0;
   info.iters = 0;
   info.guard = 0;
   info.vacuum = 0;
   info.fail = 0;
-  const real cL = xsqrt(G.g * pL / rhoL), cR = xsqrt(G.g * pR / rhoR);
   if (G.two_gm1 * (cL + cR) <= uR - uL) {
     // two rarefactions with vacuum between them
     info.vacuum = 1;
@@ -263,7 +271,7 @@ __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real 
     rhoF = (real)0; uF = (real)0.5 * (frontL + frontR); pF = (real)0;
     return 0;
   }
-  const real p0 = standard_guess(rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, have_guess, guess);
+  const real p0 = standard_guess_ppv(rhoL, uL, pL, cL, rhoR, uR, pR, cR, ppv, G, have_guess, guess);
   NewtonTail<real> nt;
   const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, tol_r, maxit, info, nt);
   pstar = ps;
@@ -320,6 +328,16 @@ __device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real 
     }
   }
   return 1;
+}
+
+template <typename real>
+__device__ __forceinline__ int riemann_sample(real rhoL, real uL, real pL, real rhoR, real uR, real pR,
+                                              const GasC<real>& G, double tol, real tol_r, int maxit, bool have_guess,
+                                              real guess, real& rhoF, real& uF, real& pF, RiemannInfo& info,
+                                              real& pstar) {
+  const real cL = xsqrt(G.g * pL / rhoL), cR = xsqrt(G.g * pR / rhoR);
+  return riemann_sample_c(rhoL, uL, pL, rhoR, uR, pR, cL, cR, linearised_pstar(rhoL, uL, pL, cL, rhoR, uR, pR, cR), G,
+                          tol, tol_r, maxit, have_guess, guess, rhoF, uF, pF, info, pstar);
 }
 
 }  // namespace amm

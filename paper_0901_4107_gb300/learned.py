@@ -49,13 +49,12 @@ def dataset(states, gamma, torch, gate=TRAIN_GATE):
     without a star region (vacuum generated) are dropped."""
     m = states.shape[0]
     x = torch.empty((m, 6), dtype=torch.float32, device="cuda")
-    pts = torch.empty(m, dtype=torch.float32, device="cuda")
     ratio = torch.empty(m, dtype=torch.float32, device="cuda")
-    ps = torch.empty(m, dtype=torch.float32, device="cuda")
-    amm.amm_mlp_features(gamma, m, states.data_ptr(), x.data_ptr(), 0, pts.data_ptr(), ratio.data_ptr())
-    amm.amm_riemann_pstar(gamma, m, states.data_ptr(), 1e-12, ps.data_ptr())
+    t = torch.empty(m, dtype=torch.float32, device="cuda")
+    amm.amm_mlp_features(gamma, m, states.data_ptr(), x.data_ptr(), 0, 0, ratio.data_ptr())
+    amm.amm_mlp_targets(gamma, m, states.data_ptr(), 1e-12, t.data_ptr())
     torch.cuda.synchronize()
-    t = torch.log(ps / pts)
+    # selection only (the kernels computed features and targets)
     ok = torch.isfinite(t) & torch.isfinite(x).all(dim=1) & (ratio > gate)
     return x[ok].contiguous(), t[ok].contiguous()
 

@@ -86,6 +86,17 @@ def test_features_and_exact_pstar(env):
     assert np.all(np.isnan(p_gpu[vac]))
     ok = ~vac
     assert np.max(np.abs(p_gpu[ok] - out[ok, 3]) / out[ok, 3]) < 2e-7
+    # the training target log(p*/p_TS) against the oracle's p* and the
+    # kernel's own FP32 two-shock estimate p_TS
+    pts = torch.empty(m, dtype=torch.float32, device="cuda")
+    tg = torch.empty(m, dtype=torch.float32, device="cuda")
+    amm.amm_mlp_features(gam, m, sd.data_ptr(), xd.data_ptr(), 0, pts.data_ptr(), 0)
+    amm.amm_mlp_targets(gam, m, sd.data_ptr(), 1e-12, tg.data_ptr())
+    torch.cuda.synchronize()
+    t_gpu, pts_h = tg.cpu().numpy().astype(np.float64), pts.cpu().numpy().astype(np.float64)
+    assert np.all(np.isnan(t_gpu[vac]))
+    good = ok & (pts_h > 0)
+    assert np.max(np.abs(t_gpu[good] - np.log(out[good, 3] / pts_h[good]))) < 1e-6
 
 
 def _blocks(g):
