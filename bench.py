@@ -70,8 +70,9 @@ WORKLOADS = {
                  "(64^3), BF16 tcgen05 forward and backward of the 6-64-64-1 SiLU network, gradient reduction, Adam"),
     "ensemble": ("config-5 workload: 64 independent periodic unit boxes, n^3 cells with n=round(exp(U(ln16,ln96))) "
                  "(seed 5), each the config-2 field at rms Mach U[0.5,4], gamma=5/3, stationary mesh, per-box "
-                 "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, one persistent "
-                 "cooperative launch per step replayed from a CUDA graph"),
+                 "Courant step, entropy switch of Sec. 3.5 (Mach 1.1, alpha_S 0.01), 50 steps, each step one "
+                 "CUDA-graph replay of either one persistent cooperative launch or the kernel sequence, whichever "
+                 "the autotuner measures faster (config.step_mode; both timed in step_modes)"),
     "moving64": ("the moving-mesh cycle of Sec. 3 (Courant step, drift, MUSCL-Hancock update, new Voronoi mesh of "
                  "the moved generators) on the config-2 workload: 64^3 jittered lattice (+-0.2h, seed 2), rms Mach 2, "
                  "Lagrangian; the mesh built on the GPU (amm_retessellate) against the host tessellator and a new "
@@ -1110,6 +1111,9 @@ def bench_ensemble(args, g, world, rank, local):
                    "form": "fp32_learned (learned p* proposal, FP32 bulk, exact fixed-point flux sums)",
                    "l2": "footprint far above L2 (no flush); consecutive steps of one run",
                    "graph": "one captured CUDA graph per step", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "step_mode": ("one persistent cooperative launch per step" if tuning["persistent"] else
+                                 "kernel sequence per step (gradients, fluxes, update, totals); the persistent "
+                                 "single launch is slower here, see step_modes"),
                    "tuning": tuning},
         "cells_per_s": n * (faces_all / nf) / (step_ms * 1e-3),
         "roofline": roofline(kern, nf, "learned_"),
