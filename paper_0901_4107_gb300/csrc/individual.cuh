@@ -252,15 +252,25 @@ __global__ void __launch_bounds__(32 * BINS_WARPS) k_ind_bins(HydroView<real> v,
   const float eps = 1e-6f * (float)fmax(d.box[0], fmax(d.box[1], d.box[2]));
   for (int idx = blockIdx.x * BINS_WARPS + w; idx < count; idx += gridDim.x * BINS_WARPS) {
     const int i = d.list[idx];
-    const R4<real> wi = v.cw[2 * (size_t)i];
-    const double rho = (double)wi.x, P = (double)v.cw[2 * (size_t)i + 1].x;
-    const double vx = (double)wi.y, vy = (double)wi.z, vz = (double)wi.w;
-    const double ci = sqrt(d.gamma * P / rho);
-    const double si = sqrt(vx * vx + vy * vy + vz * vz);
+    // the cell's position, sound speed, velocity and speed in FP64: the walk
+    // record the activation kernel wrote (one thread per cell), rather than
+    // every lane of this warp repeating the FP64 square roots on the narrow
+    // FP64 pipe
+    double ci, si, vx, vy, vz, xi = 0.0, yi = 0.0, zi = 0.0;
+    if (d.signal) {
+      const int slot = d.cell_slot[i];
+      const double4 ra = d.rec[2 * (size_t)slot], rb = d.rec[2 * (size_t)slot + 1];
+      xi = ra.x; yi = ra.y; zi = ra.z; ci = ra.w;
+      vx = rb.x; vy = rb.y; vz = rb.z; si = rb.w;
+    } else {
+      const R4<real> wi = v.cw[2 * (size_t)i];
+      const double rho = (double)wi.x, P = (double)v.cw[2 * (size_t)i + 1].x;
+      vx = (double)wi.y; vy = (double)wi.z; vz = (double)wi.w;
+      ci = sqrt(d.gamma * P / rho);
+      si = sqrt(vx * vx + vy * vy + vz * vz);
+    }
     double cur = (double)v.crad[i] / (ci + si);           // R_i / (c_i + |v_i|)
     if (d.signal) {
-      const double* gi = d.gen + 3 * (size_t)i;
-      const double xi = gi[0], yi = gi[1], zi = gi[2];
       const float xf = (float)xi, yf = (float)yi, zf = (float)zi;
       const float cf = (float)ci, vxf = (float)vx, vyf = (float)vy, vzf = (float)vz;
       const float minef = (float)(ci + si);
