@@ -50,7 +50,7 @@ void free_ctx(amm_ctx* c) {
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
-                  c->ftiles, c->box_first_ctile, c->fgeo, c->igAB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad,
+                  c->ftiles, c->box_first_ctile, c->fgeo, c->igAB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad, c->cwp, c->Apw,
                   c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->wcorr, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
                   c->totals, c->stats,  c->closure, c->mlp,      c->defer_list, c->defer_count, c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
@@ -88,10 +88,14 @@ cudaError_t mark(amm_ctx* c, int k) {
                                              : cudaEventRecord(c->prof_ev[k], c->stream);
 }
 
-cudaError_t run_gradients(amm_ctx* c) {
+// the Courant minimum and the gradients of a step; cfl > 0: its step is cfl
+// times the Courant minimum, cfl == 0: dt_box (the static mesh's predicted
+// records are taken over half of it)
+cudaError_t run_gradients(amm_ctx* c, double cfl) {
   cudaError_t e = mark(c, 0);
   if (e != cudaSuccess) return e;
-  e = dispatch(c, [&] { return amm::launch_gradients<double>(c); }, [&] { return amm::launch_gradients<float>(c); });
+  e = dispatch(c, [&] { return amm::launch_gradients<double>(c, cfl); },
+               [&] { return amm::launch_gradients<float>(c, cfl); });
   if (e != cudaSuccess) return e;
   return mark(c, 1);
 }
@@ -417,6 +421,10 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   CUB(cudaMalloc(&c->crad, rs * (size_t)n));
   CUB(cudaMalloc(&c->cw, rs * 8 * (size_t)n));
   CUB(cudaMalloc(&c->grad, rs * 16 * (size_t)n));
+  if (opt.mesh_motion == AMM_EULERIAN) {
+    CUB(cudaMalloc(&c->cwp, rs * 8 * (size_t)n));
+    if (opt.entropy) CUB(cudaMalloc(&c->Apw, rs * (size_t)n));
+  }
   if (opt.mesh_motion == AMM_EXPLICIT_W) {
     CUB(cudaMalloc(&c->wmesh, rs * 4 * (size_t)n));
     CUB(cudaMemsetAsync(c->wmesh, 0, rs * 4 * (size_t)n, c->stream));
@@ -588,17 +596,16 @@ int amm_set_mesh_velocity(amm_ctx* c, const double* w) {
 
 int amm_gradients(amm_ctx* c) {
   if (!c) return AMM_ERR_INVALID_ARG;
-  CU(run_gradients(c));
+  CU(run_gradients(c, 0.0));
   c->grads_fresh = true;
   return AMM_OK;
 }
 
 int amm_timestep(amm_ctx* c, double cfl, double* dt_out) {
   if (!c || !dt_out || !(cfl > 0.0)) return fail(c, AMM_ERR_INVALID_ARG, "bad argument");
-  if (!c->grads_fresh) {
-    CU(run_gradients(c));
-    c->grads_fresh = true;
-  }
+  // the Courant minimum of the current state (and the regularity-corrected
+  // mesh velocities, which the drift takes)
+  CU(dispatch(c, [&] { return amm::launch_courant<double>(c); }, [&] { return amm::launch_courant<float>(c); }));
   std::vector<unsigned long long> bits(c->nboxes);
   CU(cudaMemcpyAsync(bits.data(), c->cour_bits, sizeof(unsigned long long) * c->nboxes, cudaMemcpyDeviceToHost,
                      c->stream));
@@ -614,7 +621,7 @@ int amm_timestep(amm_ctx* c, double cfl, double* dt_out) {
 static int step_with_dt_box(amm_ctx* c) {
   if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
     return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
-  if (!c->grads_fresh) CU(run_gradients(c));
+  CU(run_gradients(c, 0.0));   // always: the static mesh's predicted records take this dt
   CU(run_step_tail(c, 0.0));
   c->grads_fresh = false;
   c->totals_fresh = true;
@@ -661,7 +668,7 @@ int amm_advance(amm_ctx* c, double cfl, int64_t nsteps, int use_graph) {
       if (e == cudaSuccess) e = mark(c, 4);
       return e;
     }
-    cudaError_t e = run_gradients(c);
+    cudaError_t e = run_gradients(c, cfl);
     if (e == cudaSuccess) e = run_step_tail(c, cfl);
     return e;
   };
@@ -918,7 +925,7 @@ int amm_harvest(amm_ctx* c, double cfl, float* states_device) {
   if (c->opt.precision == AMM_FP32_LEARNED && !c->mlp_loaded)
     return fail(c, AMM_ERR_NOT_READY, "no proposal weights loaded");
   c->harvest = states_device;
-  cudaError_t e = run_gradients(c);
+  cudaError_t e = run_gradients(c, cfl);
   if (e == cudaSuccess) e = run_step_tail(c, cfl);
   c->harvest = nullptr;
   if (e != cudaSuccess) return cuda_fail(c, e, "harvest step");
@@ -973,7 +980,7 @@ int amm_get_primitives(amm_ctx* c, double* W) {
 int amm_get_gradients(amm_ctx* c, double* g) {
   if (!c || !g) return fail(c, AMM_ERR_INVALID_ARG, "null argument");
   if (!c->grads_fresh) {
-    CU(run_gradients(c));
+    CU(run_gradients(c, 0.0));
     c->grads_fresh = true;
   }
   const size_t cnt = (size_t)c->n * (c->dim + 2) * c->dim;
@@ -1172,7 +1179,7 @@ int amm_autotune(amm_ctx* c, double cfl, int reps, amm_tuning* out) {
         rc = cuda_fail(c, e, "autotune reset");
         break;
       }
-      e = run_gradients(c);
+      e = run_gradients(c, cfl);
       if (e == cudaSuccess) e = run_step_tail(c, cfl);
       if (e != cudaSuccess) {
         rc = cuda_fail(c, e, "autotune step");

@@ -127,6 +127,12 @@ struct HydroView {
   double* Q;                  // 5 planes of n
   R4<real>* cw;                // [n][2] {rho, v}, {P, s - r}
   R4<real>* grad;
+  // static mesh: each cell's state predicted over half the step in the lab
+  // frame, W - (dt/2) A(W) grad W, written by the gradient kernel:
+  // {rho, v}, {P, s - r} per cell, and A likewise with the entropy switch
+  int pred;
+  R4<real>* cwp;
+  real* Apw;
   const R4<real>* wmesh;
   const R4<real>* cgeo;        // {1/V, s - r}
   const real* crad;            // effective radius R_i of eq. (EqnTiStep)
@@ -250,6 +256,8 @@ struct amm_ctx {
   amm::R4<double>* cgeo64 = nullptr;
   void* cw = nullptr;              // [n][2] R4<real> cell records
   void* grad = nullptr;
+  void* cwp = nullptr;             // [n][2] R4<real>: half-step predicted records (static mesh)
+  void* Apw = nullptr;             // [n] real: predicted entropic function (entropy switch)
   void* wmesh = nullptr;
   void* flux = nullptr;
   void* fluxE = nullptr;
@@ -355,8 +363,13 @@ template <typename real>
 HydroView<real> make_view(amm_ctx* c, double cfl);
 template <typename real>
 cudaError_t launch_primitives(amm_ctx* c);
+// the Courant minimum (and the regularity-corrected mesh velocities) of the
+// current state, then the gradients; cfl > 0: the step is cfl times the
+// Courant minimum, else dt_box (the predicted records need it)
 template <typename real>
-cudaError_t launch_gradients(amm_ctx* c);
+cudaError_t launch_courant(amm_ctx* c);
+template <typename real>
+cudaError_t launch_gradients(amm_ctx* c, double cfl);
 template <typename real>
 cudaError_t launch_flux(amm_ctx* c, double cfl);
 template <typename real>

@@ -22,6 +22,12 @@
 // warp in shared memory, the maxima flushed when the box changes, the
 // statistics added to the device totals once per CTA.
 //
+// Static mesh (STATIC): the face frame is the lab frame, so a cell's
+// half-step prediction W - (dt/2) A(W) grad W is the same for all its faces;
+// the gradient kernel writes it once per cell (cwp) and a face only
+// extrapolates the two predicted records to its centroid, instead of
+// repeating the prediction on each of a cell's ~15 faces.
+//
 // Learned form (LEARN): a face whose Riemann problem would take the proposal
 // (the linearised star pressure above PROPOSAL_GATE times the larger side
 // pressure) is not solved here; it is appended, warp by warp, to a list that
@@ -49,15 +55,17 @@ struct ChunkSmem {
   unsigned fmax[B / 32][6];
 };
 
-// a cell's record: {rho, v}, {P, s - r} (32 bytes) and its gradients (64)
+// a cell's record: {rho, v}, {P, s - r} (32 bytes: from cw, or the
+// predicted record from cwp) and its gradients (64); A from Aw or Apw
 template <bool ENT>
-__device__ __forceinline__ CellRec<float> load_rec256(const HydroView<float>& v, int i) {
+__device__ __forceinline__ CellRec<float> load_rec256(const HydroView<float>& v, const R4<float>* rec,
+                                                     const float* A, int i) {
   CellRec<float> r;
-  ldg256(v.cw + 2 * (size_t)i, r.W, r.Pc);
+  ldg256(rec + 2 * (size_t)i, r.W, r.Pc);
   ldg256(v.grad + 4 * (size_t)i, r.g0, r.g1);
   ldg256(v.grad + 4 * (size_t)i + 2, r.g2, r.g3);
   if constexpr (ENT) {
-    r.A = v.Aw[i];
+    r.A = A[i];
     r.gA = v.gradA[i];
   }
   return r;
@@ -128,9 +136,21 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
     {
       R4<float> G0, G1;
       ldg256(v.fgeo + 2 * (size_t)k, G0, G1);
-      const CellRec<float> recL = load_rec256<ENT>(v, L0.x);
-      const CellRec<float> recR = load_rec256<ENT>(v, L0.y);
-      face_prepare_rec<float, ENT, STATIC>(v, k, valid, hdt, hdt, L0, G0, G1, recL, recR, f);
+      if constexpr (STATIC) {
+        // the cells' half-step predicted records (gradient kernel)
+        const CellRec<float> pL = load_rec256<ENT>(v, v.cwp, v.Apw, L0.x);
+        const CellRec<float> pR = load_rec256<ENT>(v, v.cwp, v.Apw, L0.y);
+        float AL = 0.0f, AR = 0.0f;
+        if constexpr (ENT) {
+          AL = v.Aw[L0.x];
+          AR = v.Aw[L0.y];
+        }
+        face_prepare_pred<float, ENT>(v, k, valid, L0, G0, G1, pL, pR, AL, AR, f);
+      } else {
+        const CellRec<float> recL = load_rec256<ENT>(v, v.cw, v.Aw, L0.x);
+        const CellRec<float> recR = load_rec256<ENT>(v, v.cw, v.Aw, L0.y);
+        face_prepare_rec<float, ENT>(v, k, valid, hdt, hdt, L0, G0, G1, recL, recR, f);
+      }
     }
     bool mine = valid;
     float cs[3];   // c_L, c_R and the linearised star pressure, for the gate and the solver

@@ -188,7 +188,7 @@ __device__ __forceinline__ void learned_faces(const HydroView<float>& v, Learned
   __syncthreads();
   tc::fence_after_sync();
   FaceWork<float> f;
-  face_prepare<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, s.hdt, f);
+  face_prepare_step<float, ENT>(v, valid ? k0 : tile.begin, valid, s.hdt, f);
   bool use;
   float guess;
   learned_guess<H>(v, s, f, phase, use, guess);
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(LT, LEARNED_CTAS_PER_SM) k_flux_deferred(Hydro
     const int2 kb = d.list[valid ? e : gi * LT];
     const float hdt = (float)(0.5 * box_dt(v, kb.y));
     FaceWork<float> f;
-    face_prepare<float, ENT>(v, kb.x, valid, hdt, hdt, f);
+    face_prepare_step<float, ENT>(v, kb.x, valid, hdt, f);
     bool use;
     float guess;
     learned_guess<1>(v, s, f, phase, use, guess);
@@ -307,6 +307,8 @@ __global__ void __launch_bounds__(CELL_TILE) k_step_persistent_learned(HydroView
   extern __shared__ uint8_t smem_raw[];
   LearnedSmem<PL_H>& s = learned_smem_ref<PL_H>(smem_raw);
   learned_setup<PL_H>(s, (const MlpDevice*)v.mlp);
+  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) courant_item<float>(v, wi);
+  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
   const int n_grad = v.n_ctiles * 4;
   for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<float, 4, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);

@@ -134,9 +134,12 @@ __device__ __forceinline__ void mesh_velocity(const HydroView<real>& v, int i, c
 // ENT: the entropy switch is on, so the entropic function A is a sixth
 // limited variable and the largest kinetic energy around the cell is kept
 // for the cold-flow criterion.
+// pred: also write the cell's record predicted over hdt (static mesh, lab
+// frame: W - hdt A(W) grad W with the limited gradients; Sec. 3.3's
+// half-step prediction, which on a static mesh does not depend on the face).
 template <typename real, int G, bool ENT = false>
 __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int ii, bool valid, int lane, R4<real>& Wi,
-                                          real& Pi, R4<real>& cg) {
+                                          real& Pi, R4<real>& cg, bool pred = false, real hdt = (real)0) {
   constexpr int UNR = 1;                               // incidences in flight per lane
   constexpr int NV = ENT ? 6 : 5;
   Wi = v.cw[2 * (size_t)ii];
@@ -260,6 +263,26 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
         v.gradA[i] = ga;
       }
     }
+    if (pred && lane == 0) {
+      // dW/dt = -A(W) grad W in the lab frame (the face-frame boost of a
+      // static mesh is zero): d rho/dt = -(v.grad rho + rho div v),
+      // dv/dt = -(v.grad) v - grad P / rho, dP/dt = -(gamma P div v + v.grad P)
+      // (explicitly rounded: the persistent step kernel must round alike)
+      const real rho = phi_i[0], vx = phi_i[1], vy = phi_i[2], vz = phi_i[3], P = phi_i[4];
+      const real divv = rn_add(rn_add(g[1][0], g[2][1]), g[3][2]);
+      const real ir = (real)1 / rho;
+      const real mh = -hdt;
+      R4<real> a, b;
+      a.x = rn_fma(mh, rn_fma(rho, divv, rn_dot3(vx, vy, vz, g[0][0], g[0][1], g[0][2])), rho);
+      a.y = rn_fma(mh, rn_fma(g[4][0], ir, rn_dot3(vx, vy, vz, g[1][0], g[1][1], g[1][2])), vx);
+      a.z = rn_fma(mh, rn_fma(g[4][1], ir, rn_dot3(vx, vy, vz, g[2][0], g[2][1], g[2][2])), vy);
+      a.w = rn_fma(mh, rn_fma(g[4][2], ir, rn_dot3(vx, vy, vz, g[3][0], g[3][1], g[3][2])), vz);
+      b.x = rn_fma(mh, rn_fma(rn_mul(v.gas.g, P), divv, rn_dot3(vx, vy, vz, g[4][0], g[4][1], g[4][2])), P);
+      b.y = cg.y; b.z = cg.z; b.w = cg.w;       // s - r
+      v.cwp[2 * (size_t)i] = a;
+      v.cwp[2 * (size_t)i + 1] = b;
+      if constexpr (ENT) v.Apw[i] = rn_fma(mh, rn_dot3(vx, vy, vz, g[5][0], g[5][1], g[5][2]), phi_i[5]);
+    }
   }
   if (cold) {
     ekm = group_max<G>(ekm);
@@ -268,43 +291,44 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
   Pi = phi_i[4];
 }
 
-// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads):
-// gradients, limiter and the per-box Courant minimum
-template <typename real, int G, bool ENT = false>
-__device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
-  constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
-  const Tile t = v.ctiles[wi / G];
-  const int lane = (int)threadIdx.x % G;
-  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
+// work item wi: cells of tile wi (one thread per cell): the per-box Courant
+// minimum (eq. EqnTiStep) and, with the regularity correction, the
+// corrected mesh velocities of the step
+template <typename real>
+__device__ __forceinline__ void courant_item(const HydroView<real>& v, int wi) {
+  const Tile t = v.ctiles[wi];
+  const int i = t.begin + (int)threadIdx.x;
   const bool valid = i < t.end;
-  const int ii = valid ? i : t.begin;
-  R4<real> Wi, cg;
-  real Pi;
-  grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg);
-  // Courant time R_i / (c_i + |v_i - w_i|), one lane per cell
+  // Courant time R_i / (c_i + |v_i - w_i|)
   real tc = (real)3.0e38;
-  if (valid && lane == 0) {
+  if (valid) {
+    const R4<real> Wi = v.cw[2 * (size_t)i];
+    const real Pi = v.cw[2 * (size_t)i + 1].x;
     real w3[3];
     mesh_velocity(v, i, Wi, w3);
-    const real cs = xsqrt(v.gas.g * Pi / Wi.x);
+    // (explicitly rounded: the persistent step kernel must round alike)
+    const real cs = xsqrt(rn_mul(v.gas.g, Pi) / Wi.x);
     const real Ri = v.crad[i];
     if (v.regularize) {
       // Sec. 4.1, eq. (EqnShapeCorrVel): towards the centre of mass at the
       // sound speed once the generator is off it by more than eta R_i
+      const R4<real> cg = v.cgeo[i];
       const real sx = cg.y, sy = cg.z, sz = cg.w;   // s - r
-      const real d = xsqrt(sx * sx + sy * sy + sz * sz);
-      const real er = v.eta_r * Ri;
-      const real ramp = d >= (real)1.1 * er ? (real)1 : (d >= (real)0.9 * er ? (d - (real)0.9 * er) / ((real)0.2 * er) : (real)0);
+      const real d = xsqrt(rn_dot3(sx, sy, sz, sx, sy, sz));
+      const real er = rn_mul(v.eta_r, Ri);
+      const real ramp = d >= rn_mul((real)1.1, er)
+                            ? (real)1
+                            : (d >= rn_mul((real)0.9, er) ? rn_fma((real)-0.9, er, d) / rn_mul((real)0.2, er) : (real)0);
       if (ramp > (real)0) {
-        const real f = v.chi_r * cs * ramp / d;
-        w3[0] += f * sx; w3[1] += f * sy; w3[2] += f * sz;
+        const real f = rn_mul(rn_mul(v.chi_r, cs), ramp) / d;
+        w3[0] = rn_fma(f, sx, w3[0]); w3[1] = rn_fma(f, sy, w3[1]); w3[2] = rn_fma(f, sz, w3[2]);
       }
       R4<real> wc;
       wc.x = w3[0]; wc.y = w3[1]; wc.z = w3[2]; wc.w = (real)0;
       v.wcorr[i] = wc;
     }
     const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
-    tc = Ri / (cs + xsqrt(dx * dx + dy * dy + dz * dz));
+    tc = Ri / rn_add(cs, xsqrt(rn_dot3(dx, dy, dz, dx, dy, dz)));
   }
   // block minimum, then one integer atomic per CTA (positive doubles order
   // like their bit patterns; min is order independent, so this is exact)
@@ -320,6 +344,35 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
       atomicMin(v.cour_bits + t.box, (unsigned long long)__double_as_longlong(md));
   }
   __syncthreads();   // `wmin` is reused by the next work item of a persistent CTA
+}
+
+template <typename real>
+__global__ void __launch_bounds__(CELL_TILE) k_courant(HydroView<real> v) {
+  courant_item<real>(v, blockIdx.x);
+}
+
+// work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads):
+// gradients and limiter; on a static mesh also the half-step predicted
+// records, over half of the box's step (its Courant minimum is complete:
+// courant_item ran before)
+template <typename real, int G, bool ENT = false>
+__device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
+  constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
+  const Tile t = v.ctiles[wi / G];
+  const int lane = (int)threadIdx.x % G;
+  const int i = t.begin + (int)(wi % G) * CELLS + (int)threadIdx.x / G;
+  const bool valid = i < t.end;
+  const int ii = valid ? i : t.begin;
+  R4<real> Wi, cg;
+  real Pi;
+  // half the box's step, by one thread (the FP64 arithmetic of box_dt runs
+  // on the narrow FP64 pipe)
+  __shared__ real s_hdt;
+  if (threadIdx.x == 0) s_hdt = v.pred ? (real)(0.5 * box_dt(v, t.box)) : (real)0;
+  __syncthreads();
+  const real hdt = s_hdt;
+  __syncthreads();   // `s_hdt` is rewritten by the next work item of a persistent CTA
+  grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg, v.pred != 0, hdt);
 }
 
 template <typename real, int G, bool ENT>
@@ -499,6 +552,123 @@ __device__ __forceinline__ void face_prepare(const HydroView<real>& v, int k, bo
   face_prepare_rec<real, ENT>(v, k, valid, hdtL, hdtR, lr, G0, G1, recL, recR, f);
 }
 
+// Static mesh: a side's face state from its cell's predicted record (the
+// gradient kernel's W - hdt A(W) grad W; with w = 0 the face frame is the lab
+// frame, so the prediction does not depend on the face), extrapolated to the
+// face centroid: W_p + grad W . (f - s_i).  Equal in exact arithmetic to
+// side_extrapolate with w = 0.  A_raw: the cell's entropic function, taken
+// where the extrapolated one is not positive.
+template <typename real, bool ENT>
+__device__ __forceinline__ void side_from_pred(const CellRec<real>& rp, real A_raw, real hsgn, const real* n, real sep,
+                                               const real* c, real* Wpp, real& Aface) {
+  const R4<real>& Wq = rp.W;    // predicted {rho, v}
+  const R4<real>& cg = rp.Pc;   // {predicted P, s - r}
+  const R4<real>& g0 = rp.g0;
+  const R4<real>& g1 = rp.g1;
+  const R4<real>& g2 = rp.g2;
+  const R4<real>& g3 = rp.g3;
+  // (explicitly rounded: the persistent step kernel must round alike)
+  const real hs = rn_mul(hsgn, sep);
+  const real fx = rn_add(rn_fma(hs, n[0], c[0]), -cg.y);
+  const real fy = rn_add(rn_fma(hs, n[1], c[1]), -cg.z);
+  const real fz = rn_add(rn_fma(hs, n[2], c[2]), -cg.w);
+  Wpp[0] = rn_add(Wq.x, rn_dot3(g0.x, g0.y, g0.z, fx, fy, fz));
+  Wpp[1] = rn_add(Wq.y, rn_dot3(g1.x, g1.y, g1.z, fx, fy, fz));
+  Wpp[2] = rn_add(Wq.z, rn_dot3(g2.x, g2.y, g2.z, fx, fy, fz));
+  Wpp[3] = rn_add(Wq.w, rn_dot3(g3.x, g3.y, g3.z, fx, fy, fz));
+  Wpp[4] = rn_add(cg.x, rn_dot3(g0.w, g1.w, g2.w, fx, fy, fz));
+  if constexpr (ENT) {
+    const R4<real>& ga = rp.gA;
+    const real Ap = rn_add(rp.A, rn_dot3(ga.x, ga.y, ga.z, fx, fy, fz));
+    Aface = Ap > (real)0 ? Ap : A_raw;
+  }
+}
+
+// face_prepare_rec for a static mesh from the cells' predicted records
+// (pL, pR; their A is the predicted entropic function, AL_raw / AR_raw the
+// cells' own).  A face whose extrapolated state is not positive falls back
+// to the cells' current states (read here, from cw).
+template <typename real, bool ENT>
+__device__ __forceinline__ void face_prepare_pred(const HydroView<real>& v, int k, bool valid, int2 lr,
+                                                  const R4<real>& G0, const R4<real>& G1, const CellRec<real>& pL,
+                                                  const CellRec<real>& pR, real AL_raw, real AR_raw,
+                                                  FaceWork<real>& f) {
+  f.k = k;
+  f.valid = valid;
+  f.lr = lr;
+  const real n[3] = {G0.x, G0.y, G0.z};
+  const real sep = G0.w;
+  const real c[3] = {G1.x, G1.y, G1.z};
+  f.A = G1.w;
+  f.AL = f.AR = (real)0;
+  side_from_pred<real, ENT>(pL, AL_raw, (real)0.5, n, sep, c, f.WppL, f.AL);
+  side_from_pred<real, ENT>(pR, AR_raw, (real)-0.5, n, sep, c, f.WppR, f.AR);
+  f.fallback = 0;
+  if (!(f.WppL[0] > (real)0) || !(f.WppL[4] > (real)0) || !(f.WppR[0] > (real)0) || !(f.WppR[4] > (real)0)) {
+    const R4<real> WL = v.cw[2 * (size_t)lr.x], PL = v.cw[2 * (size_t)lr.x + 1];
+    const R4<real> WR = v.cw[2 * (size_t)lr.y], PR = v.cw[2 * (size_t)lr.y + 1];
+    f.WppL[0] = WL.x; f.WppL[1] = WL.y; f.WppL[2] = WL.z; f.WppL[3] = WL.w; f.WppL[4] = PL.x;
+    f.WppR[0] = WR.x; f.WppR[1] = WR.y; f.WppR[2] = WR.z; f.WppR[3] = WR.w; f.WppR[4] = PR.x;
+    if constexpr (ENT) {
+      f.AL = AL_raw;
+      f.AR = AR_raw;
+    }
+    f.fallback = 1;
+  }
+  f.uL = rn_dot3(f.WppL[1], f.WppL[2], f.WppL[3], n[0], n[1], n[2]);
+  f.uR = rn_dot3(f.WppR[1], f.WppR[2], f.WppR[3], n[0], n[1], n[2]);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    f.n[d] = n[d];
+    f.w[d] = (real)0;
+  }
+  if (v.harvest && valid) {
+    float* h = v.harvest + 6 * (size_t)k;
+    h[0] = (float)f.WppL[0]; h[1] = (float)f.uL; h[2] = (float)f.WppL[4];
+    h[3] = (float)f.WppR[0]; h[4] = (float)f.uR; h[5] = (float)f.WppR[4];
+  }
+}
+
+// a cell's predicted record from global memory (static mesh)
+template <typename real, bool ENT>
+__device__ __forceinline__ CellRec<real> load_pred_rec(const HydroView<real>& v, int i) {
+  CellRec<real> r;
+  r.W = v.cwp[2 * (size_t)i];
+  r.Pc = v.cwp[2 * (size_t)i + 1];
+  const R4<real>* gp = v.grad + 4 * (size_t)i;
+  r.g0 = gp[0];
+  r.g1 = gp[1];
+  r.g2 = gp[2];
+  r.g3 = gp[3];
+  if constexpr (ENT) {
+    r.A = v.Apw[i];
+    r.gA = v.gradA[i];
+  }
+  return r;
+}
+
+// A face of a step (hdt: half the box's step): from the predicted records on
+// a static mesh, else with the face-frame prediction of face_prepare.
+template <typename real, bool ENT>
+__device__ __forceinline__ void face_prepare_step(const HydroView<real>& v, int k, bool valid, real hdt,
+                                                  FaceWork<real>& f) {
+  if (v.pred) {
+    const int2 lr = v.lr[k];
+    const R4<real> G0 = v.fgeo[2 * (size_t)k];
+    const R4<real> G1 = v.fgeo[2 * (size_t)k + 1];
+    const CellRec<real> pL = load_pred_rec<real, ENT>(v, lr.x);
+    const CellRec<real> pR = load_pred_rec<real, ENT>(v, lr.y);
+    real AL = (real)0, AR = (real)0;
+    if constexpr (ENT) {
+      AL = v.Aw[lr.x];
+      AR = v.Aw[lr.y];
+    }
+    face_prepare_pred<real, ENT>(v, k, valid, lr, G0, G1, pL, pR, AL, AR, f);
+  } else {
+    face_prepare<real, ENT>(v, k, valid, hdt, hdt, f);
+  }
+}
+
 // What one face contributes to the step's reductions: the magnitudes of its
 // A F components as float bits (non-negative floats order like their bits),
 // its Newton iterations and flags.
@@ -670,7 +840,7 @@ __device__ __forceinline__ void flux_item(const HydroView<real>& v, int wi) {
   if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
   __syncthreads();
   FaceWork<real> f;
-  face_prepare<real, ENT>(v, valid ? k0 : t.begin, valid, s_hdt, s_hdt, f);
+  face_prepare_step<real, ENT>(v, valid ? k0 : t.begin, valid, s_hdt, f);
   face_finish<real, B, ENT>(v, f, t.box, min(B, t.end - first), false, (real)0);
 }
 
@@ -1071,6 +1241,9 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.Q = c->Q;
   v.cw = (R4<real>*)c->cw;
   v.grad = (R4<real>*)c->grad;
+  v.pred = (c->opt.mesh_motion == AMM_EULERIAN && c->cwp) ? 1 : 0;
+  v.cwp = (R4<real>*)c->cwp;
+  v.Apw = (real*)c->Apw;
   v.wmesh = (const R4<real>*)c->wmesh;
   v.cgeo = (const R4<real>*)c->cgeo;
   v.crad = (const real*)c->crad;
@@ -1123,9 +1296,18 @@ cudaError_t launch_primitives(amm_ctx* c) {
 }
 
 template <typename real>
-cudaError_t launch_gradients(amm_ctx* c) {
+cudaError_t launch_courant(amm_ctx* c) {
   auto v = make_view<real>(c, 0.0);
   cudaError_t e = cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
+  if (e != cudaSuccess) return e;
+  k_courant<real><<<c->n_ctiles, CELL_TILE, 0, c->stream>>>(v);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_gradients(amm_ctx* c, double cfl) {
+  auto v = make_view<real>(c, cfl);
+  cudaError_t e = launch_courant<real>(c);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * FMAX_STRIDE * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
@@ -1248,7 +1430,8 @@ cudaError_t launch_set_wmesh(amm_ctx* c, const double* wa) {
 #define AMM_INSTANTIATE(real)                                                        \
   template HydroView<real> make_view<real>(amm_ctx*, double);                        \
   template cudaError_t launch_primitives<real>(amm_ctx*);                            \
-  template cudaError_t launch_gradients<real>(amm_ctx*);                             \
+  template cudaError_t launch_courant<real>(amm_ctx*);                               \
+  template cudaError_t launch_gradients<real>(amm_ctx*, double);                     \
   template cudaError_t launch_flux<real>(amm_ctx*, double);                          \
   template cudaError_t launch_update<real>(amm_ctx*, double);                        \
   template cudaError_t launch_finish<real>(amm_ctx*, double);                        \

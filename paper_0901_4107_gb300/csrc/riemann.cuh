@@ -37,6 +37,25 @@ __device__ __forceinline__ float xsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double xrsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ float xrsqrt(float a) { return rsqrtf(a); }
 
+// Explicitly rounded products, sums and fused multiply-adds: the compiler
+// neither fuses nor splits them, so a formula written with them rounds the
+// same in every kernel it is inlined into.  Whether a plain a * b + c is
+// fused depends on where the compiler places the product relative to the
+// branches of an inlined FP64 division or square root, which differs
+// between kernels.  The per-phase kernels and the persistent step kernel
+// must agree bit for bit.
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a . b of two 3-vectors, x first
+template <typename real>
+__device__ __forceinline__ real rn_dot3(real ax, real ay, real az, real bx, real by, real bz) {
+  return rn_fma(az, bz, rn_fma(ay, by, rn_mul(ax, bx)));
+}
+
 // f_K(p) and f_K'(p)
 template <typename real>
 __device__ __forceinline__ void wave_curve(real p, real rhoK, real pK, real cK, const GasC<real>& G, real& f,
