@@ -210,17 +210,22 @@ def alu_roofline(kernel, ms, nf, apk, pipe):
     return out
 
 
-def algorithmic_bytes(kernel, n, nf, rb):
+def algorithmic_bytes(kernel, n, nf, rb, static=False):
     """Bytes each kernel must move per launch (each array touched once; the
     gathered neighbour data counted once per cell).  rb = bytes of the bulk
-    real type (4 FP32 form, 8 FP64 form)."""
+    real type (4 FP32 form, 8 FP64 form); static: a static mesh, whose
+    gradient stage also runs the Courant pass and writes the predicted
+    records."""
     inc = 2 * nf                                  # cell->face incidences
     if kernel == "gradients":
         # per cell: W, P, 1/V and R read, CSR offset, the gradients written;
-        # per incidence: its precomputed weights and lever arm (2 vectors of
-        # 4 reals and 1 real) and the neighbour index streamed; the gathered
-        # neighbour W, P counted once per cell
-        return n * (5 * rb + 4 * rb + rb + 4 + 16 * rb) + n * 5 * rb + inc * (9 * rb + 4)
+        # per incidence: its precomputed record streamed (A c / |d|, A / |d|,
+        # the lever arm and the neighbour index: 8 reals); the gathered
+        # neighbour W, P counted once per cell.  Static mesh: W, P and R read
+        # again by the Courant pass before the gradients, and the predicted
+        # record ({rho, v}, {P, s - r}) written
+        b = n * (5 * rb + 4 * rb + rb + 4 + 16 * rb) + n * 5 * rb + inc * (8 * rb)
+        return b + (n * (6 * rb + 8 * rb) if static else 0)
     if kernel == "flux":
         # left/right indices and face geometry read; 5-component flux written;
         # per cell: W, P, gradients, cell geometry read once
@@ -232,7 +237,7 @@ def algorithmic_bytes(kernel, n, nf, rb):
     if kernel == "finish":
         return 0
     if kernel == "step":
-        return sum(algorithmic_bytes(k, n, nf, rb) for k in ("gradients", "flux", "update"))
+        return sum(algorithmic_bytes(k, n, nf, rb, static) for k in ("gradients", "flux", "update"))
     raise KeyError(kernel)
 
 
@@ -501,11 +506,11 @@ def kernel_split(g, ctx, Q0d, tuning, steps=50):
     return ker
 
 
-def kernel_table(ker, n, nf, rb):
+def kernel_table(ker, n, nf, rb, static=False):
     tot = sum(ker.values())
     out = {}
     for k, t in ker.items():
-        b = algorithmic_bytes(k, n, nf, rb)
+        b = algorithmic_bytes(k, n, nf, rb, static)
         out[k] = {"ms": t, "share": t / tot if tot else None, "algorithmic_bytes": b,
                   "gbs": (b / (t * 1e-3) / 1e9) if t > 0 else None}
     return out
@@ -710,7 +715,7 @@ def bench_box(args, g, world, rank, local):
     value = faces_all / (step_ms * 1e-3)
     split = kernel_split(g, ctxs[head], Q0d, tuning)
     rb = 8 if head == "fp64" else 4
-    kern = kernel_table(split or ker, n, nf, rb)
+    kern = kernel_table(split or ker, n, nf, rb, motion == "eulerian")
     prefix = "learned_" if head == "fp32_learned" else ""
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1101,7 +1106,7 @@ def bench_ensemble(args, g, world, rank, local):
         amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 0)
         _, ker = run(ctxs[head], min(args.steps, 20), 2, True)
         amm.amm_set_tuning(ctxs[head], tuning["grad_lanes"], tuning["update_lanes"], tuning["flux_block"], 1)
-    kern = kernel_table(ker, n, nf, 4)
+    kern = kernel_table(ker, n, nf, 4, True)   # static mesh
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

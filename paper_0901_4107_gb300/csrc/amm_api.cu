@@ -50,7 +50,7 @@ void free_ctx(amm_ctx* c) {
   for (cudaEvent_t ev : c->prof_ev)
     if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->gen,   c->box,     c->Q,       c->lr,       c->csr_off, c->csr,     c->ctiles,
-                  c->ftiles, c->box_first_ctile, c->fgeo, c->igAB, c->igz, c->nbr, c->cgeo64, c->cw,     c->grad, c->cwp, c->Apw,
+                  c->ftiles, c->box_first_ctile, c->fgeo, c->igAB, c->cgeo64, c->cw,     c->grad, c->cwp, c->Apw,
                   c->wmesh, c->cgeo, c->crad, c->flux,    c->fluxE,   c->cour_bits, c->fmax_bits, c->wcorr, c->S, c->Aw, c->gradA, c->fluxS, c->machf, c->ekmax, c->kept, c->cell_perm, c->face_perm, c->barrier, c->box_status, c->dt_box, c->dt_used, c->partial,
                   c->totals, c->stats,  c->closure, c->mlp,      c->defer_list, c->defer_count, c->scratch, c->counter,
                   c->ind_bin, c->ind_act, c->ind_list, c->ind_flist, c->ind_count, c->ind_fstamp, c->ind_cstamp,
@@ -414,8 +414,6 @@ int amm_create(amm_ctx** out, int dim, int64_t n, const double* gen, int64_t nf,
   CUB(dalloc(&c->box_first_ctile, (size_t)nb + 1));
   CUB(cudaMalloc(&c->fgeo, rs * 4 * 2 * (size_t)nf));
   CUB(cudaMalloc(&c->igAB, rs * 4 * 4 * (size_t)nf));
-  CUB(cudaMalloc(&c->igz, rs * 2 * (size_t)nf));
-  CUB(dalloc(&c->nbr, (size_t)2 * nf));
   CUB(dalloc(&c->cgeo64, (size_t)n));
   CUB(cudaMalloc(&c->cgeo, rs * 4 * (size_t)n));
   CUB(cudaMalloc(&c->crad, rs * (size_t)n));

@@ -16,10 +16,9 @@
 //   cell->face csr_off int [n+1], csr int2 {face << 1 | side, neighbour}
 //              (side 0: the cell is the face's left cell), in face order.
 //   per incidence (csr order; the gradient kernel streams them):
-//              igAB 2 x R4<real>: {A c / |d|, A s n_x / 2},
-//                   {A s n_y / 2, A s n_z / 2, (f - s_i)_x, (f - s_i)_y}
-//                   (one 32-byte record in the FP32 forms)
-//              igz real (f - s_i)_z     nbr int  the neighbour j
+//              igAB 2 x R4<real>: {A c / |d|, A / |d|}, {f - s_i, j}
+//                   (one 32-byte record in the FP32 forms; the neighbour j
+//                   as the bits of the last real)
 //              (s = +1 for the face's left cell, -1 for its right cell)
 //   numbering  cells are renumbered along a Morton curve per box and faces
 //              sorted by their new left cell; cell_perm / face_perm map back
@@ -144,8 +143,6 @@ struct HydroView {
   const int* csr_off;
   const int2* csr;
   const R4<real>* igAB;        // [2 q], [2 q + 1]
-  const real* igz;
-  const int* nbr;
   const Tile* ctiles;
   const Tile* ftiles;
   const int* cell_perm;        // internal -> caller numbering
@@ -248,9 +245,7 @@ struct amm_ctx {
   int* face_perm = nullptr;        // [nf] internal face -> caller's face
   std::vector<int> perm_h;         // host copy of cell_perm
   void* fgeo = nullptr;            // [nf][2] R4<real>
-  void* igAB = nullptr;            // [2 nf][2] R4<real> per-incidence gradient weights
-  void* igz = nullptr;             // [2 nf] real
-  int* nbr = nullptr;              // [2 nf]
+  void* igAB = nullptr;            // [2 nf][2] R4<real> per-incidence records
   void* cgeo = nullptr;            // [n] R4<real> {1/V, s - r}
   void* crad = nullptr;            // [n] real, effective radius
   amm::R4<double>* cgeo64 = nullptr;

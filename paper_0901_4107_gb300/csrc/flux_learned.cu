@@ -307,8 +307,10 @@ __global__ void __launch_bounds__(CELL_TILE) k_step_persistent_learned(HydroView
   extern __shared__ uint8_t smem_raw[];
   LearnedSmem<PL_H>& s = learned_smem_ref<PL_H>(smem_raw);
   learned_setup<PL_H>(s, (const MlpDevice*)v.mlp);
-  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) courant_item<float>(v, wi);
-  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  if (v.pred) {
+    for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) courant_item<float>(v, wi);
+    grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  }
   const int n_grad = v.n_ctiles * 4;
   for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<float, 4, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);

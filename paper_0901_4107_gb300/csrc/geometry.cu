@@ -106,16 +106,22 @@ __global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad,
   crad[i] = (real)((dim == 3) ? cbrt(3.0 * a.x / (4.0 * M_PI)) : sqrt(a.x / M_PI));
 }
 
-// Per-incidence weights of the gradient (eq. eqngrad2) and of the limiter,
-// in the order of the cell->face lists: for incidence q of cell i through
-// face k (sign s = +1 if i is the face's left cell, else -1, so s n points
-// out of i), A c / |d| and A s n / 2 multiply [phi_j - phi_i] and
-// (phi_i + phi_j) in the gradient sum, and f - s_i = s |d|/2 n + c - (s_i - r_i)
-// is the limiter's lever arm.  Computed once per tessellation from the
-// bulk-precision face and cell geometry.
+// Per-incidence record of the gradient (eq. eqngrad2) and of the limiter, in
+// the order of the cell->face lists: for incidence q of cell i through face
+// k (sign s = +1 if i is the face's left cell, else -1, so s n points out of
+// i) and neighbour j, {A c / |d|, a_r = A / |d|} and {f - s_i, j}, where
+// f - s_i = s |d|/2 n + c - (s_i - r_i) is the limiter's lever arm.  The
+// weight A s n / 2 of (phi_i + phi_j) is not stored: it equals
+// a_r (f - s_i + (s_i - r_i)) - A c / |d|, three FMAs in the gradient
+// kernel, which so streams one 32-byte record per incidence in the FP32
+// forms.  j is kept as the bits of the last real.  Computed once per
+// tessellation from the bulk-precision face and cell geometry.
+__device__ __forceinline__ float int_bits_real(int j, float) { return __int_as_float(j); }
+__device__ __forceinline__ double int_bits_real(int j, double) { return __longlong_as_double((long long)j); }
+
 template <typename real>
 __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr, const R4<real>* fgeo,
-                                     const R4<real>* cgeo, R4<real>* igAB, real* igz, int* nbr) {
+                                     const R4<real>* cgeo, R4<real>* igAB) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const R4<real> cg = cgeo[i];
@@ -126,21 +132,18 @@ __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr,
     const R4<real> G0 = fgeo[2 * (size_t)k];
     const R4<real> G1 = fgeo[2 * (size_t)k + 1];
     const real a_r = G1.w / G0.w;
-    const real a_h = (real)0.5 * G1.w * sg;
     const real hs = (real)0.5 * sg * G0.w;
     R4<real> a, b;
     a.x = a_r * G1.x;
     a.y = a_r * G1.y;
     a.z = a_r * G1.z;
-    a.w = a_h * G0.x;
-    b.x = a_h * G0.y;
-    b.y = a_h * G0.z;
-    b.z = hs * G0.x + G1.x - cg.y;
-    b.w = hs * G0.y + G1.y - cg.z;
+    a.w = a_r;
+    b.x = hs * G0.x + G1.x - cg.y;
+    b.y = hs * G0.y + G1.y - cg.z;
+    b.z = hs * G0.z + G1.z - cg.w;
+    b.w = int_bits_real(e.y, (real)0);
     igAB[2 * (size_t)q] = a;
     igAB[2 * (size_t)q + 1] = b;
-    igz[q] = hs * G0.z + G1.z - cg.w;
-    nbr[q] = e.y;
   }
 }
 
@@ -212,15 +215,13 @@ cudaError_t launch_face_geometry(amm_ctx* c, const double* area, const double* c
     k_cell_derived<double><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<double>*)c->cgeo, (double*)c->crad,
                                                        (R4<double>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<double><<<nbc, 256, 0, c->stream>>>(
-        (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igAB,
-        (double*)c->igz, c->nbr);
+        (int)c->n, c->csr_off, c->csr, (const R4<double>*)c->fgeo, (const R4<double>*)c->cgeo, (R4<double>*)c->igAB);
   } else {
     k_cast4<float><<<(unsigned)((nfg + 255) / 256), 256, 0, c->stream>>>(fg64, (R4<float>*)c->fgeo, nfg);
     k_cell_derived<float><<<nbc, 256, 0, c->stream>>>(c->cgeo64, (R4<float>*)c->cgeo, (float*)c->crad,
                                                       (R4<float>*)c->cw, (int)c->n, c->dim);
     k_incidence_geometry<float><<<nbc, 256, 0, c->stream>>>(
-        (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igAB,
-        (float*)c->igz, c->nbr);
+        (int)c->n, c->csr_off, c->csr, (const R4<float>*)c->fgeo, (const R4<float>*)c->cgeo, (R4<float>*)c->igAB);
   }
   return cudaGetLastError();
 }

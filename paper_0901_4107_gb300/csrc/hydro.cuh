@@ -126,6 +126,14 @@ __device__ __forceinline__ void mesh_velocity(const HydroView<real>& v, int i, c
   }
 }
 
+// the neighbour j of incidence q: the bits of the last real of its record
+__device__ __forceinline__ int incidence_nbr(const HydroView<float>& v, int q) {
+  return __float_as_int(__ldg(&v.igAB[2 * (size_t)q + 1].w));
+}
+__device__ __forceinline__ int incidence_nbr(const HydroView<double>& v, int q) {
+  return (int)__double_as_longlong(__ldg(&v.igAB[2 * (size_t)q + 1].w));
+}
+
 // The limited gradient of cell i (valid) by the G lanes of its group: lane
 // `lane` takes the incidences lane, lane+G, ...; the results are stored.
 // ii is a valid cell index for the lanes of an invalid group (their loads
@@ -166,19 +174,20 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
     const real dx = Wi.y - wi3[0], dy = Wi.z - wi3[1], dz = Wi.w - wi3[2];
     ekm = (real)0.5 * (real)v.Q[ii] * (dx * dx + dy * dy + dz * dz);
   }
-  // the neighbour index of the next incidence is loaded one iteration ahead,
-  // so the neighbour's state load does not wait behind its index load
-  int jn = (q0 + lane < q1) ? v.nbr[q0 + lane] : 0;
+  // the neighbour index of the next incidence (the last word of its record)
+  // is loaded one iteration ahead, so the neighbour's state load does not
+  // wait behind the record
+  int jn = (q0 + lane < q1) ? incidence_nbr(v, q0 + lane) : 0;
 #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
     // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out),
     // with the geometric weights of the incidence precomputed (igAB)
     const int j = jn;
-    if (q + G < q1) jn = v.nbr[q + G];
+    if (q + G < q1) jn = incidence_nbr(v, q + G);
     R4<real> a4, b4, Wj;
     real Pj;
     if constexpr (sizeof(real) == 4) {
-      // the incidence's weights and the neighbour's record {W}, {P, s - r}:
+      // the incidence's record and the neighbour's record {W}, {P, s - r}:
       // one 32-byte load each
       ldg256(v.igAB + 2 * (size_t)q, a4, b4);
       R4<real> Pc;
@@ -190,6 +199,11 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
       Wj = v.cw[2 * (size_t)j];
       Pj = v.cw[2 * (size_t)j + 1].x;
     }
+    // A s n / 2 = a_r (f - s_i + (s_i - r_i)) - A c / |d|, with a_r = A / |d|
+    // (explicitly rounded: the persistent step kernel must round alike)
+    const real wn0 = rn_fma(a4.w, rn_add(b4.x, cg.y), -a4.x);
+    const real wn1 = rn_fma(a4.w, rn_add(b4.y, cg.z), -a4.y);
+    const real wn2 = rn_fma(a4.w, rn_add(b4.z, cg.w), -a4.z);
     real phi_j[NV];
     phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = Pj;
     if constexpr (ENT) phi_j[5] = v.Aw[j];
@@ -202,9 +216,9 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
     for (int a = 0; a < NV; a++) {
       const real d = phi_j[a] - phi_i[a];
       const real s = phi_i[a] + phi_j[a];
-      g[a][0] += d * a4.x + s * a4.w;
-      g[a][1] += d * a4.y + s * b4.x;
-      g[a][2] += d * a4.z + s * b4.y;
+      g[a][0] += d * a4.x + s * wn0;
+      g[a][1] += d * a4.y + s * wn1;
+      g[a][2] += d * a4.z + s * wn2;
       mx[a] = phi_j[a] > mx[a] ? phi_j[a] : mx[a];
       mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
     }
@@ -226,7 +240,7 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
   for (int q = q0 + lane; q < q1; q += G) {
       // f - s_i of the incidence
       const R4<real> b4 = v.igAB[2 * (size_t)q + 1];
-      const real fx = b4.z, fy = b4.w, fz = v.igz[q];
+      const real fx = b4.x, fy = b4.y, fz = b4.z;
 #pragma unroll
       for (int a = 0; a < NV; a++) {
         const real dphi = g[a][0] * fx + g[a][1] * fy + g[a][2] * fz;
@@ -291,47 +305,43 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
   Pi = phi_i[4];
 }
 
-// work item wi: cells of tile wi (one thread per cell): the per-box Courant
-// minimum (eq. EqnTiStep) and, with the regularity correction, the
-// corrected mesh velocities of the step
+// Cell i's Courant time R_i / (c_i + |v_i - w_i|) (eq. EqnTiStep), from its
+// record {rho, v} and pressure; with the regularity correction also its
+// corrected mesh velocity of the step (written to wcorr).
 template <typename real>
-__device__ __forceinline__ void courant_item(const HydroView<real>& v, int wi) {
-  const Tile t = v.ctiles[wi];
-  const int i = t.begin + (int)threadIdx.x;
-  const bool valid = i < t.end;
-  // Courant time R_i / (c_i + |v_i - w_i|)
-  real tc = (real)3.0e38;
-  if (valid) {
-    const R4<real> Wi = v.cw[2 * (size_t)i];
-    const real Pi = v.cw[2 * (size_t)i + 1].x;
-    real w3[3];
-    mesh_velocity(v, i, Wi, w3);
-    // (explicitly rounded: the persistent step kernel must round alike)
-    const real cs = xsqrt(rn_mul(v.gas.g, Pi) / Wi.x);
-    const real Ri = v.crad[i];
-    if (v.regularize) {
-      // Sec. 4.1, eq. (EqnShapeCorrVel): towards the centre of mass at the
-      // sound speed once the generator is off it by more than eta R_i
-      const R4<real> cg = v.cgeo[i];
-      const real sx = cg.y, sy = cg.z, sz = cg.w;   // s - r
-      const real d = xsqrt(rn_dot3(sx, sy, sz, sx, sy, sz));
-      const real er = rn_mul(v.eta_r, Ri);
-      const real ramp = d >= rn_mul((real)1.1, er)
-                            ? (real)1
-                            : (d >= rn_mul((real)0.9, er) ? rn_fma((real)-0.9, er, d) / rn_mul((real)0.2, er) : (real)0);
-      if (ramp > (real)0) {
-        const real f = rn_mul(rn_mul(v.chi_r, cs), ramp) / d;
-        w3[0] = rn_fma(f, sx, w3[0]); w3[1] = rn_fma(f, sy, w3[1]); w3[2] = rn_fma(f, sz, w3[2]);
-      }
-      R4<real> wc;
-      wc.x = w3[0]; wc.y = w3[1]; wc.z = w3[2]; wc.w = (real)0;
-      v.wcorr[i] = wc;
+__device__ __forceinline__ real courant_time(const HydroView<real>& v, int i, const R4<real>& Wi, real Pi) {
+  real w3[3];
+  mesh_velocity(v, i, Wi, w3);
+  // (explicitly rounded: the persistent step kernel must round alike)
+  const real cs = xsqrt(rn_mul(v.gas.g, Pi) / Wi.x);
+  const real Ri = v.crad[i];
+  if (v.regularize) {
+    // Sec. 4.1, eq. (EqnShapeCorrVel): towards the centre of mass at the
+    // sound speed once the generator is off it by more than eta R_i
+    const R4<real> cg = v.cgeo[i];
+    const real sx = cg.y, sy = cg.z, sz = cg.w;   // s - r
+    const real d = xsqrt(rn_dot3(sx, sy, sz, sx, sy, sz));
+    const real er = rn_mul(v.eta_r, Ri);
+    const real ramp = d >= rn_mul((real)1.1, er)
+                          ? (real)1
+                          : (d >= rn_mul((real)0.9, er) ? rn_fma((real)-0.9, er, d) / rn_mul((real)0.2, er) : (real)0);
+    if (ramp > (real)0) {
+      const real f = rn_mul(rn_mul(v.chi_r, cs), ramp) / d;
+      w3[0] = rn_fma(f, sx, w3[0]); w3[1] = rn_fma(f, sy, w3[1]); w3[2] = rn_fma(f, sz, w3[2]);
     }
-    const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
-    tc = Ri / rn_add(cs, xsqrt(rn_dot3(dx, dy, dz, dx, dy, dz)));
+    R4<real> wc;
+    wc.x = w3[0]; wc.y = w3[1]; wc.z = w3[2]; wc.w = (real)0;
+    v.wcorr[i] = wc;
   }
-  // block minimum, then one integer atomic per CTA (positive doubles order
-  // like their bit patterns; min is order independent, so this is exact)
+  const real dx = Wi.y - w3[0], dy = Wi.z - w3[1], dz = Wi.w - w3[2];
+  return Ri / rn_add(cs, xsqrt(rn_dot3(dx, dy, dz, dx, dy, dz)));
+}
+
+// The CTA's minimum of tc folded into box b's Courant minimum: one integer
+// atomic per CTA (positive doubles order like their bit patterns; min is
+// order independent, so this is exact).  Every thread of the CTA calls it.
+template <typename real>
+__device__ __forceinline__ void courant_block_min(const HydroView<real>& v, real tc, int b) {
   tc = group_min<32>(tc);
   __shared__ real wmin[CELL_TILE / 32];
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = tc;
@@ -341,9 +351,20 @@ __device__ __forceinline__ void courant_item(const HydroView<real>& v, int wi) {
     for (int w = 1; w < CELL_TILE / 32; w++) m = wmin[w] < m ? wmin[w] : m;
     const double md = (double)m;
     if (md > 0.0 && md < 1.0e300)
-      atomicMin(v.cour_bits + t.box, (unsigned long long)__double_as_longlong(md));
+      atomicMin(v.cour_bits + b, (unsigned long long)__double_as_longlong(md));
   }
   __syncthreads();   // `wmin` is reused by the next work item of a persistent CTA
+}
+
+// work item wi: cells of tile wi (one thread per cell): the per-box Courant
+// minimum of a static mesh's step, which its gradient kernel needs
+template <typename real>
+__device__ __forceinline__ void courant_item(const HydroView<real>& v, int wi) {
+  const Tile t = v.ctiles[wi];
+  const int i = t.begin + (int)threadIdx.x;
+  real tc = (real)3.0e38;
+  if (i < t.end) tc = courant_time(v, i, v.cw[2 * (size_t)i], v.cw[2 * (size_t)i + 1].x);
+  courant_block_min(v, tc, t.box);
 }
 
 template <typename real>
@@ -352,9 +373,10 @@ __global__ void __launch_bounds__(CELL_TILE) k_courant(HydroView<real> v) {
 }
 
 // work item wi: cells of tile wi/G, sub-block wi%G (CELL_TILE threads):
-// gradients and limiter; on a static mesh also the half-step predicted
-// records, over half of the box's step (its Courant minimum is complete:
-// courant_item ran before)
+// gradients and limiter.  Static mesh: also the half-step predicted records,
+// over half of the box's step (courant_item ran before, so the box's Courant
+// minimum is complete).  Moving mesh: also the Courant minimum, one lane per
+// cell.
 template <typename real, int G, bool ENT = false>
 __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   constexpr int CELLS = CELL_TILE / G;                 // cells per CTA
@@ -365,14 +387,21 @@ __device__ __forceinline__ void grad_item(const HydroView<real>& v, int wi) {
   const int ii = valid ? i : t.begin;
   R4<real> Wi, cg;
   real Pi;
-  // half the box's step, by one thread (the FP64 arithmetic of box_dt runs
-  // on the narrow FP64 pipe)
-  __shared__ real s_hdt;
-  if (threadIdx.x == 0) s_hdt = v.pred ? (real)(0.5 * box_dt(v, t.box)) : (real)0;
-  __syncthreads();
-  const real hdt = s_hdt;
-  __syncthreads();   // `s_hdt` is rewritten by the next work item of a persistent CTA
-  grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg, v.pred != 0, hdt);
+  if (v.pred) {
+    // half the box's step, by one thread (the FP64 arithmetic of box_dt runs
+    // on the narrow FP64 pipe)
+    __shared__ real s_hdt;
+    if (threadIdx.x == 0) s_hdt = (real)(0.5 * box_dt(v, t.box));
+    __syncthreads();
+    const real hdt = s_hdt;
+    __syncthreads();   // `s_hdt` is rewritten by the next work item of a persistent CTA
+    grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg, true, hdt);
+  } else {
+    grad_cell<real, G, ENT>(v, i, ii, valid, lane, Wi, Pi, cg);
+    real tc = (real)3.0e38;
+    if (valid && lane == 0) tc = courant_time(v, i, Wi, Pi);
+    courant_block_min(v, tc, t.box);
+  }
 }
 
 template <typename real, int G, bool ENT>
@@ -1020,15 +1049,31 @@ __device__ __forceinline__ void update_item(const HydroView<real>& v, int wi) {
     const real P = prims_from_Q(v, i, q[0], q[1], q[2], q[3], q[4]);
     nonpos = (!(q[0] > 0.0) || !(P > (real)0)) ? 1u : 0u;
   }
-  // per-block FP64 sums in a fixed order (bit reproducible): the cells' lane
-  // 0 values are combined across the warp, then across the warps
+  // per-block FP64 sums in a fixed order (bit reproducible).  Within a warp,
+  // a butterfly that halves the components each lane carries at each of the
+  // first three levels (5 components padded to 8): 9 FP64 adds per lane, where
+  // a shuffle tree per component takes 25 on GB300's narrow FP64 pipe.  Lane
+  // 4c then holds the warp's sum of component c; the warps' sums are added in
+  // warp order.
   __shared__ double red[CELL_TILE / 32][5];
+  {
+    const int l = (int)threadIdx.x & 31;
+    const bool b4 = (l & 16) != 0, b3 = (l & 8) != 0, b2 = (l & 4) != 0;
+    double w4[4];
 #pragma unroll
-  for (int a = 0; a < 5; a++) {
-    double s = q[a];
+    for (int j = 0; j < 4; j++) {
+      const double lo = q[j], hi = (j == 0) ? q[4] : 0.0;   // components j and 4 + j
+      w4[j] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    }
+    double w2[2];
 #pragma unroll
-    for (int o = 16; o >= G; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][a] = s;
+    for (int j = 0; j < 2; j++)
+      w2[j] = (b3 ? w4[2 + j] : w4[j]) + __shfl_xor_sync(0xffffffffu, b3 ? w4[j] : w4[2 + j], 8);
+    double w1 = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w2[0] : w2[1], 4);
+    w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
+    w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
+    const int c = l >> 2;   // 4 b4 + 2 b3 + b2
+    if ((l & 3) == 0 && c < 5) red[threadIdx.x >> 5][c] = w1;
   }
   const unsigned nbad = __syncthreads_count(nonpos);
   if constexpr (ENT) {
@@ -1256,8 +1301,6 @@ HydroView<real> make_view(amm_ctx* c, double cfl) {
   v.csr_off = c->csr_off;
   v.csr = c->csr;
   v.igAB = (const R4<real>*)c->igAB;
-  v.igz = (const real*)c->igz;
-  v.nbr = c->nbr;
   v.ctiles = c->ctiles;
   v.ftiles = c->ftiles;
   v.cell_perm = c->cell_perm;
@@ -1307,7 +1350,10 @@ cudaError_t launch_courant(amm_ctx* c) {
 template <typename real>
 cudaError_t launch_gradients(amm_ctx* c, double cfl) {
   auto v = make_view<real>(c, cfl);
-  cudaError_t e = launch_courant<real>(c);
+  // a static mesh's gradient kernel needs the step (k_courant); on a moving
+  // mesh it finds the Courant minimum itself
+  cudaError_t e = v.pred ? launch_courant<real>(c)
+                         : cudaMemsetAsync(c->cour_bits, 0xff, sizeof(unsigned long long) * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(c->fmax_bits, 0, sizeof(unsigned) * FMAX_STRIDE * c->nboxes, c->stream);
   if (e != cudaSuccess) return e;

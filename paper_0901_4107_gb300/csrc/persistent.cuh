@@ -1,8 +1,9 @@
-// One persistent launch per step: every phase of the update (per-box Courant
-// minimum, gradients + limiter (+ the predicted records of a static mesh),
-// face fluxes, cell update + conservation sums, per-box totals) runs in a
-// single cooperative kernel whose CTAs walk the work items of each phase and
-// meet at a grid barrier between phases.
+// One persistent launch per step: every phase of the update (gradients +
+// limiter, with the per-box Courant minimum on a moving mesh; on a static
+// mesh the Courant minimum first and the predicted records with the
+// gradients; face fluxes; cell update + conservation sums; per-box totals)
+// runs in a single cooperative kernel whose CTAs walk the work items of each
+// phase and meet at a grid barrier between phases.
 // The batched ensemble (many independent boxes of uneven size, each with its
 // own Courant step) is advanced with one such launch per step, replayed from
 // a CUDA graph.
@@ -52,8 +53,11 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, volatile unsigned*
 // gradient and update phases (measured 0.33 -> 0.27 ms per 64^3 step)
 template <typename real, int GG, bool ENT>
 __global__ void __launch_bounds__(CELL_TILE, 3) k_step_persistent(HydroView<real> v, unsigned* bar) {
-  for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) courant_item<real>(v, wi);
-  grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  if (v.pred) {
+    // static mesh: the step before the gradients (v.pred is the same for all CTAs)
+    for (int wi = blockIdx.x; wi < v.n_ctiles; wi += gridDim.x) courant_item<real>(v, wi);
+    grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);
+  }
   const int n_grad = v.n_ctiles * GG;
   for (int wi = blockIdx.x; wi < n_grad; wi += gridDim.x) grad_item<real, GG, ENT>(v, wi);
   grid_barrier(bar, bar + 1, gridDim.x, &v.stats->status);

@@ -184,8 +184,7 @@ int amm_retessellate(amm_ctx* c) {
   c->ind_graph = nullptr;
   if (nf > c->nf_cap) {
     const int64_t cap = nf + nf / 8;
-    void** bufs[] = {(void**)&c->lr, (void**)&c->face_perm, (void**)&c->csr, &c->fgeo, &c->igAB, &c->igz,
-                     (void**)&c->nbr, &c->flux, &c->fluxE, &c->fluxS, &c->machf, (void**)&c->ftiles,
+    void** bufs[] = {(void**)&c->lr, (void**)&c->face_perm, (void**)&c->csr, &c->fgeo, &c->igAB, &c->flux, &c->fluxE, &c->fluxS, &c->machf, (void**)&c->ftiles,
                      (void**)&c->ind_flist, (void**)&c->ind_fstamp, (void**)&c->ind_fdt};
     const bool had_defer = c->defer_list != nullptr;
     if (had_defer) {
@@ -202,8 +201,6 @@ int amm_retessellate(amm_ctx* c) {
     cu(cudaMalloc(&c->csr, sizeof(int2) * 2 * cap), "alloc");
     cu(cudaMalloc(&c->fgeo, rs * 8 * cap), "alloc");
     cu(cudaMalloc(&c->igAB, rs * 16 * cap), "alloc");
-    cu(cudaMalloc(&c->igz, rs * 2 * cap), "alloc");
-    cu(cudaMalloc(&c->nbr, sizeof(int) * 2 * cap), "alloc");
     cu(cudaMalloc(&c->flux, rs * 4 * cap), "alloc");
     cu(cudaMalloc(&c->fluxE, rs * cap), "alloc");
     if (c->opt.entropy) {
