@@ -192,15 +192,14 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
         if (lane == 0 && r > sm.fmax[warp][a]) sm.fmax[warp][a] = r;
       }
     }
-    // Newton statistics of the warp: the iteration histogram over the
-    // distinct counts present, sums and flags
+    // Newton statistics of the warp: the iteration histogram (the lanes with
+    // equal counts found by one match; the lowest of them adds their number,
+    // so the lanes that write hold distinct bins), sums and flags
     const unsigned act = __ballot_sync(full, mine);
-    unsigned todo = act;
-    while (todo) {
-      const unsigned val = __shfl_sync(full, o.iters, __ffs(todo) - 1);
-      const unsigned m = __ballot_sync(full, mine && o.iters == val);
-      if (lane == 0) sm.hist[warp][val < 15u ? val : 15u] += __popc(m);
-      todo &= ~m;
+    {
+      const unsigned key = mine ? (o.iters < 15u ? o.iters : 15u) : 0xffffffffu;
+      const unsigned m = __match_any_sync(full, key);
+      if (mine && lane == __ffs(m) - 1) sm.hist[warp][key] += __popc(m);
     }
     const unsigned sit = __reduce_add_sync(full, o.iters);
     const unsigned smx = __reduce_max_sync(full, o.iters);

@@ -254,12 +254,11 @@ __global__ void __launch_bounds__(LT, LEARNED_CTAS_PER_SM) k_flux_deferred(Hydro
       }
     }
     const unsigned act = __ballot_sync(full, valid);
-    unsigned todo = act;
-    while (todo) {
-      const unsigned val = __shfl_sync(full, o.iters, __ffs(todo) - 1);
-      const unsigned m = __ballot_sync(full, valid && o.iters == val);
-      if (lane == 0) hist[warp][val < 15u ? val : 15u] += __popc(m);
-      todo &= ~m;
+    {
+      // the lanes with equal counts by one match; the lowest adds their number
+      const unsigned key = valid ? (o.iters < 15u ? o.iters : 15u) : 0xffffffffu;
+      const unsigned m = __match_any_sync(full, key);
+      if (valid && lane == __ffs(m) - 1) hist[warp][key] += __popc(m);
     }
     s_faces += __popc(act);
     s_iters += __reduce_add_sync(full, o.iters);

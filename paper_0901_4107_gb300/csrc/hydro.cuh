@@ -233,9 +233,19 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
     mn[a] = group_min<G>(mn[a]);
   }
   if (v.limit) {
-    real alpha[NV];
+    // alpha = min(1, min over incidences of psi), psi = (max - phi_i) / dphi
+    // for dphi > 0 and (min - phi_i) / dphi for dphi < 0, taken branch-free
+    // as 1 / max(1, max of dphi / (max - phi_i) or dphi / (min - phi_i)): the
+    // two reciprocals once per cell and variable, one product per incidence.
+    // (An extremal cell's reciprocal is infinite, so a dphi towards it gives
+    // alpha = 0; a dphi of 0 gives NaN, which fmax ignores.)
+    real bmax[NV], rmx[NV], rmn[NV];
 #pragma unroll
-    for (int a = 0; a < NV; a++) alpha[a] = (real)1;
+    for (int a = 0; a < NV; a++) {
+      bmax[a] = (real)0;
+      rmx[a] = (real)1 / (mx[a] - phi_i[a]);
+      rmn[a] = (real)-1 / (phi_i[a] - mn[a]);
+    }
   #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
       // f - s_i of the incidence
@@ -244,17 +254,12 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
 #pragma unroll
       for (int a = 0; a < NV; a++) {
         const real dphi = g[a][0] * fx + g[a][1] * fy + g[a][2] * fz;
-        real psi = (real)1;
-        if (dphi > (real)0)
-          psi = (mx[a] - phi_i[a]) / dphi;
-        else if (dphi < (real)0)
-          psi = (mn[a] - phi_i[a]) / dphi;
-        alpha[a] = psi < alpha[a] ? psi : alpha[a];
+        bmax[a] = fmax(bmax[a], dphi * (dphi > (real)0 ? rmx[a] : rmn[a]));
       }
     }
 #pragma unroll
     for (int a = 0; a < NV; a++) {
-      const real al = group_min<G>(alpha[a]);
+      const real al = (real)1 / fmax((real)1, group_max<G>(bmax[a]));
       g[a][0] *= al;
       g[a][1] *= al;
       g[a][2] *= al;
@@ -825,21 +830,27 @@ __device__ __forceinline__ void face_finish(const HydroView<real>& v, const Face
   // slot per warp in shared memory, then a few global atomics per CTA
   const unsigned full = 0xffffffffu;
   const unsigned it = o.iters;
-  unsigned mine[22];
-#pragma unroll
-  for (int b = 0; b < 15; b++) mine[b] = __popc(__ballot_sync(full, valid && it == (unsigned)b));
-  mine[15] = __popc(__ballot_sync(full, valid && it >= 15u));
-  mine[16] = __reduce_add_sync(full, it);
-  mine[17] = __popc(__ballot_sync(full, o.guard));
-  mine[18] = __popc(__ballot_sync(full, o.vacuum));
-  mine[19] = __popc(__ballot_sync(full, o.fail));
-  mine[20] = __popc(__ballot_sync(full, o.fallback));
-  mine[21] = __reduce_max_sync(full, it);
+  unsigned mine[6];
+  mine[0] = __reduce_add_sync(full, it);
+  mine[1] = __popc(__ballot_sync(full, o.guard));
+  mine[2] = __popc(__ballot_sync(full, o.vacuum));
+  mine[3] = __popc(__ballot_sync(full, o.fail));
+  mine[4] = __popc(__ballot_sync(full, o.fallback));
+  mine[5] = __reduce_max_sync(full, it);
   __shared__ unsigned sh[B / 32][22];
-  const int wid = (int)threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
+  const int wid = (int)threadIdx.x >> 5, ln = (int)threadIdx.x & 31;
+  // the iteration histogram: the lanes with equal counts by one match, the
+  // lowest of them writes their number (distinct bins; absent bins stay 0)
+  if (ln < 16) sh[wid][ln] = 0u;
+  __syncwarp();
+  {
+    const unsigned key = valid ? (it < 15u ? it : 15u) : 0xffffffffu;
+    const unsigned m = __match_any_sync(full, key);
+    if (valid && ln == __ffs(m) - 1) sh[wid][key] = __popc(m);
+  }
+  if (ln == 0) {
 #pragma unroll
-    for (int s = 0; s < 22; s++) sh[wid][s] = mine[s];
+    for (int s = 0; s < 6; s++) sh[wid][16 + s] = mine[s];
   }
   __syncthreads();
   if (threadIdx.x < 16) {
