@@ -60,7 +60,23 @@ __device__ __forceinline__ real rn_dot3(real ax, real ay, real az, real bx, real
 template <typename real>
 __device__ __forceinline__ void wave_curve(real p, real rhoK, real pK, real cK, const GasC<real>& G, real& f,
                                            real& df) {
-  if (p > pK) {
+  if constexpr (sizeof(real) == 4) {
+    // FP32: both branches, selected.  The sides of a warp's faces split
+    // between shocks and rarefactions, so a branch would run both anyway;
+    // unconditional, the per-side constants leave the Newton loop.
+    const real A = G.two_gp1 / rhoK;
+    const real id = (real)1 / (p + G.gm1_gp1 * pK);
+    const real q = xsqrt(A * id);
+    const real fs = (p - pK) * q;
+    const real dfs = q * ((real)1 - (real)0.5 * (p - pK) * id);
+    const real pr = p / pK;
+    const real prz = xpow(pr, G.z);
+    const real fr = G.two_gm1 * cK * (prz - (real)1);
+    const real dfr = prz / (pr * rhoK * cK);
+    const bool shock = p > pK;
+    f = shock ? fs : fr;
+    df = shock ? dfs : dfr;
+  } else if (p > pK) {
     const real A = G.two_gp1 / rhoK;
     const real B = G.gm1_gp1 * pK;
     const real q = xsqrt(A / (p + B));
@@ -198,10 +214,11 @@ __device__ __forceinline__ real newton_pstar(real p, real rhoL, real uL, real pL
       real pn = p - (fL + fR + du) / (dL + dR);
       if (!(pn > (real)0)) pn = (real)1e-3 * p;
       it++;
-      const real ch = (real)2 * fabsf((float)(pn - p)) / (pn + p);
+      // 2 |dp| / (p_new + p_old) < tol, without the division
+      const bool done = (real)2 * fabsf((float)(pn - p)) < tol_f * (pn + p);
       tail.fL = fL; tail.dL = dL; tail.fR = fR; tail.dR = dR; tail.dp = pn - p;
       p = pn;
-      if (ch < tol_f) {
+      if (done) {
         conv = true;
         break;
       }
@@ -295,58 +312,37 @@ __device__ __forceinline__ int riemann_sample_c(real rhoL, real uL, real pL, rea
   const real ps = newton_pstar(p0, rhoL, uL, pL, cL, rhoR, uR, pR, cR, G, tol, tol_r, maxit, info, nt);
   pstar = ps;
   const real us = (real)0.5 * (uL + uR) + (real)0.5 * ((nt.fR - nt.fL) + (nt.dR - nt.dL) * nt.dp);
-  if ((real)0 <= us) {
-    const real r = ps / pL;
-    if (ps > pL) {
-      const real SL = uL - cL * xsqrt(G.shock_a * r + G.shock_b);
-      if ((real)0 <= SL) {
-        rhoF = rhoL; uF = uL; pF = pL;
-      } else {
-        rhoF = rhoL * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1); uF = us; pF = ps;
-      }
+  // the side the face sees (the contact's upwind side): s = +1 left, -1
+  // right; the right side's formulas are the left side's with the velocity
+  // signs flipped (products with s are exact), so one path serves both
+  const int side = ((real)0 <= us) ? 0 : 1;
+  const real s = side ? (real)-1 : (real)1;
+  const real rhoK = side ? rhoR : rhoL, uK = side ? uR : uL, pK = side ? pR : pL, cK = side ? cR : cL;
+  const real r = ps / pK;
+  if (ps > pK) {
+    const real SK = uK - s * cK * xsqrt(G.shock_a * r + G.shock_b);
+    if ((real)0 <= s * SK) {
+      rhoF = rhoK; uF = uK; pF = pK;
     } else {
-      if ((real)0 <= uL - cL) {
-        rhoF = rhoL; uF = uL; pF = pL;
-      } else {
-        const real tail = us - cL * xpow(r, G.z);
-        if ((real)0 > tail) {
-          rhoF = rhoL * xpow(r, G.inv_g); uF = us; pF = ps;
-        } else {
-          const real c = G.two_gp1 * cL + G.gm1_gp1 * uL;
-          const real q = c / cL;
-          uF = c;
-          rhoF = rhoL * xpow(q, G.fan_rho);
-          pF = pL * xpow(q, G.fan_p);
-        }
-      }
-    }
-    return 0;
-  }
-  const real r = ps / pR;
-  if (ps > pR) {
-    const real SR = uR + cR * xsqrt(G.shock_a * r + G.shock_b);
-    if ((real)0 >= SR) {
-      rhoF = rhoR; uF = uR; pF = pR;
-    } else {
-      rhoF = rhoR * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1); uF = us; pF = ps;
+      rhoF = rhoK * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1); uF = us; pF = ps;
     }
   } else {
-    if ((real)0 >= uR + cR) {
-      rhoF = rhoR; uF = uR; pF = pR;
+    if ((real)0 <= s * (uK - s * cK)) {
+      rhoF = rhoK; uF = uK; pF = pK;
     } else {
-      const real tail = us + cR * xpow(r, G.z);
-      if ((real)0 < tail) {
-        rhoF = rhoR * xpow(r, G.inv_g); uF = us; pF = ps;
+      const real tail = us - s * cK * xpow(r, G.z);
+      if ((real)0 > s * tail) {
+        rhoF = rhoK * xpow(r, G.inv_g); uF = us; pF = ps;
       } else {
-        const real c = G.two_gp1 * cR - G.gm1_gp1 * uR;
-        const real q = c / cR;
-        uF = -c;
-        rhoF = rhoR * xpow(q, G.fan_rho);
-        pF = pR * xpow(q, G.fan_p);
+        const real c = G.two_gp1 * cK + s * G.gm1_gp1 * uK;
+        const real q = c / cK;
+        uF = s * c;
+        rhoF = rhoK * xpow(q, G.fan_rho);
+        pF = pK * xpow(q, G.fan_p);
       }
     }
   }
-  return 1;
+  return side;
 }
 
 template <typename real>
