@@ -16,7 +16,7 @@
 //   cell->face csr_off int [n+1], csr int2 {face << 1 | side, neighbour}
 //              (side 0: the cell is the face's left cell), in face order.
 //   per incidence (csr order; the gradient kernel streams them):
-//              igAB 2 x R4<real>: {A c / |d|, A / |d|}, {f - s_i, j}
+//              igAB 2 x R4<real>: {A (c / |d| + s n / 2), 0}, {f - s_i, j}
 //                   (one 32-byte record in the FP32 forms; the neighbour j
 //                   as the bits of the last real)
 //              (s = +1 for the face's left cell, -1 for its right cell)

@@ -109,13 +109,14 @@ __global__ void k_cell_derived(const R4<double>* cg64, R4<real>* cg, real* crad,
 // Per-incidence record of the gradient (eq. eqngrad2) and of the limiter, in
 // the order of the cell->face lists: for incidence q of cell i through face
 // k (sign s = +1 if i is the face's left cell, else -1, so s n points out of
-// i) and neighbour j, {A c / |d|, a_r = A / |d|} and {f - s_i, j}, where
+// i) and neighbour j, {w = A (c / |d| + s n / 2), 0} and {f - s_i, j}, where
 // f - s_i = s |d|/2 n + c - (s_i - r_i) is the limiter's lever arm.  The
-// weight A s n / 2 of (phi_i + phi_j) is not stored: it equals
-// a_r (f - s_i + (s_i - r_i)) - A c / |d|, three FMAs in the gradient
-// kernel, which so streams one 32-byte record per incidence in the FP32
-// forms.  j is kept as the bits of the last real.  Computed once per
-// tessellation from the bulk-precision face and cell geometry.
+// paper's sum over the faces of A ([phi_j - phi_i] c / |d| + (phi_i + phi_j)
+// s n / 2) equals the sum of (phi_j - phi_i) w, because a closed cell's
+// vector area sum of A s n vanishes: one weight vector per incidence, and a
+// uniform field gives exactly zero whatever the rounding.  j is kept as the
+// bits of the last real.  Computed once per tessellation from the
+// bulk-precision face and cell geometry.
 __device__ __forceinline__ float int_bits_real(int j, float) { return __int_as_float(j); }
 __device__ __forceinline__ double int_bits_real(int j, double) { return __longlong_as_double((long long)j); }
 
@@ -134,10 +135,11 @@ __global__ void k_incidence_geometry(int n, const int* csr_off, const int2* csr,
     const real a_r = G1.w / G0.w;
     const real hs = (real)0.5 * sg * G0.w;
     R4<real> a, b;
-    a.x = a_r * G1.x;
-    a.y = a_r * G1.y;
-    a.z = a_r * G1.z;
-    a.w = a_r;
+    const real a_h = (real)0.5 * G1.w * sg;
+    a.x = a_r * G1.x + a_h * G0.x;
+    a.y = a_r * G1.y + a_h * G0.y;
+    a.z = a_r * G1.z + a_h * G0.z;
+    a.w = (real)0;
     b.x = hs * G0.x + G1.x - cg.y;
     b.y = hs * G0.y + G1.y - cg.z;
     b.z = hs * G0.z + G1.z - cg.w;

@@ -180,8 +180,9 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
   int jn = (q0 + lane < q1) ? incidence_nbr(v, q0 + lane) : 0;
 #pragma unroll UNR
   for (int q = q0 + lane; q < q1; q += G) {
-    // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out),
-    // with the geometric weights of the incidence precomputed (igAB)
+    // V grad = sum A ([phi_j - phi_i] c / r_ij + (phi_i + phi_j)/2 n_out)
+    //        = sum (phi_j - phi_i) w,  w = A (c / r_ij + n_out / 2)
+    // (a closed cell's sum of A n_out vanishes), w precomputed per incidence
     const int j = jn;
     if (q + G < q1) jn = incidence_nbr(v, q + G);
     R4<real> a4, b4, Wj;
@@ -201,9 +202,6 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
     }
     // A s n / 2 = a_r (f - s_i + (s_i - r_i)) - A c / |d|, with a_r = A / |d|
     // (explicitly rounded: the persistent step kernel must round alike)
-    const real wn0 = rn_fma(a4.w, rn_add(b4.x, cg.y), -a4.x);
-    const real wn1 = rn_fma(a4.w, rn_add(b4.y, cg.z), -a4.y);
-    const real wn2 = rn_fma(a4.w, rn_add(b4.z, cg.w), -a4.z);
     real phi_j[NV];
     phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = Pj;
     if constexpr (ENT) phi_j[5] = v.Aw[j];
@@ -215,10 +213,9 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
 #pragma unroll
     for (int a = 0; a < NV; a++) {
       const real d = phi_j[a] - phi_i[a];
-      const real s = phi_i[a] + phi_j[a];
-      g[a][0] += d * a4.x + s * wn0;
-      g[a][1] += d * a4.y + s * wn1;
-      g[a][2] += d * a4.z + s * wn2;
+      g[a][0] += d * a4.x;
+      g[a][1] += d * a4.y;
+      g[a][2] += d * a4.z;
       mx[a] = phi_j[a] > mx[a] ? phi_j[a] : mx[a];
       mn[a] = phi_j[a] < mn[a] ? phi_j[a] : mn[a];
     }

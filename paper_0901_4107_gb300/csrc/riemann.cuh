@@ -122,7 +122,16 @@ __device__ __forceinline__ real standard_guess_ppv(real rhoL, real uL, real pL, 
   const real du = uR - uL;
   const real pmin = pL < pR ? pL : pR, pmax = pL > pR ? pL : pR;
   real p0;
-  if (pmax / pmin <= (real)2 && ppv >= pmin && ppv <= pmax) {
+  if constexpr (sizeof(real) == 4) {
+    // FP32: every estimate, selected (a warp's faces take all three, so
+    // branches would run them all anyway)
+    const bool pv = pmax <= (real)2 * pmin && ppv >= pmin && ppv <= pmax;
+    const real num = cL + cR - (real)0.5 * G.gm1 * du;
+    const real den = cL / xpow(pL, G.z) + cR / xpow(pR, G.z);
+    const real ptr = xpow(num / den, G.inv_z);
+    const real pts = have ? proposal : two_shock_pstar(rhoL, uL, pL, rhoR, uR, pR, ppv, G);
+    p0 = pv ? ppv : (ppv < pmin ? ptr : pts);
+  } else if (pmax / pmin <= (real)2 && ppv >= pmin && ppv <= pmax) {
     p0 = ppv;
   } else if (ppv < pmin) {
     const real num = cL + cR - (real)0.5 * G.gm1 * du;
