@@ -17,10 +17,10 @@
 // inside one face tile, so inside one box), one face per thread and chunk.
 // The chunk's tile record is read two chunks ahead and the face's cell
 // indices one chunk ahead, so the cell gathers do not wait behind index
-// loads.  There is no barrier inside the loop: the Newton statistics and the
-// running maxima of |A F| per component (of the current box) are kept per
-// warp in shared memory, the maxima flushed when the box changes, the
-// statistics added to the device totals once per CTA.
+// loads.  There is no barrier inside the loop: the Newton statistics are
+// kept per warp in shared memory and added to the device totals once per
+// CTA; the running maxima of |A F| per component (of the current box) are
+// kept per thread and reduced over the warp when the box changes.
 //
 // Static mesh (STATIC): the face frame is the lab frame, so a cell's
 // half-step prediction W - (dt/2) A(W) grad W is the same for all its faces;
@@ -47,12 +47,11 @@ constexpr int chunk_ctas_per_sm() {
   return B == 256 ? 3 : 7;
 }
 
-// per warp: iteration histogram, statistics sums, running |A F| maxima
+// per warp: iteration histogram, statistics sums
 template <int B>
 struct ChunkSmem {
   unsigned hist[B / 32][16];
   unsigned red[B / 32][8];
-  unsigned fmax[B / 32][6];
 };
 
 // a cell's record: {rho, v}, {P, s - r} (32 bytes: from cw, or the
@@ -81,19 +80,6 @@ __device__ __forceinline__ int chunk_face(int c, const Tile& T, bool& valid) {
   return valid ? k : T.begin;
 }
 
-// the warp's running |A F| maxima to the box's slots (lane 0)
-template <int B, int NM>
-__device__ __forceinline__ void flush_fmax(const HydroView<float>& v, ChunkSmem<B>& sm, int warp, int box) {
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int a = 0; a < NM; a++) {
-      const unsigned r = sm.fmax[warp][a];
-      if (r) atomicMax(v.fmax_bits + FMAX_STRIDE * box + a, r);
-      sm.fmax[warp][a] = 0u;
-    }
-  }
-}
-
 template <int B, bool ENT, bool LEARN, bool STATIC>
 __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(HydroView<float> v, int nchunks, int per_cta,
                                                                           FluxDefer defer) {
@@ -107,9 +93,13 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
   if (c0 >= c1) return;   // the whole CTA leaves together
   if (lane < 16) sm.hist[warp][lane] = 0u;
   if (lane < 8) sm.red[warp][lane] = 0u;
-  if (lane < 6) sm.fmax[warp][lane] = 0u;
   __syncwarp();
   const bool fixed = v.fixed_acc != 0;
+  // each thread's running maxima of |A F| per component (of the current box),
+  // reduced over the warp when the box changes
+  unsigned fm[NM];
+#pragma unroll
+  for (int a = 0; a < NM; a++) fm[a] = 0u;
 
   // tiles of chunks c0 and c0+1, cell indices of c0
   Tile T0 = v.ftiles[c0 / CPT];
@@ -185,13 +175,8 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
     }
     FaceOut o;
     face_finish_core<float, ENT>(v, f, false, 0.0f, o, LEARN, cs);
-    if (fixed) {
 #pragma unroll
-      for (int a = 0; a < NM; a++) {
-        const unsigned r = __reduce_max_sync(full, o.m[a]);
-        if (lane == 0 && r > sm.fmax[warp][a]) sm.fmax[warp][a] = r;
-      }
-    }
+    for (int a = 0; a < NM; a++) fm[a] = max(fm[a], o.m[a]);
     // Newton statistics of the warp: the iteration histogram (the lanes with
     // equal counts found by one match; the lowest of them adds their number,
     // so the lanes that write hold distinct bins), sums and flags
@@ -220,7 +205,14 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
       if (o.fail) atomicOr(v.box_status + T0.box, (unsigned)ST_NEWTON_CAP);
     }
     // the box's maxima at its last chunk of this CTA
-    if (fixed && (!more1 || T1.box != T0.box)) flush_fmax<B, NM>(v, sm, warp, T0.box);
+    if (fixed && (!more1 || T1.box != T0.box)) {
+#pragma unroll
+      for (int a = 0; a < NM; a++) {
+        const unsigned r = __reduce_max_sync(full, fm[a]);
+        if (lane == 0 && r) atomicMax(v.fmax_bits + FMAX_STRIDE * T0.box + a, r);
+        fm[a] = 0u;
+      }
+    }
     T0 = T1;
     T1 = T2;
     L0 = L1;

@@ -328,7 +328,27 @@ __device__ __forceinline__ int riemann_sample_c(real rhoL, real uL, real pL, rea
   const real s = side ? (real)-1 : (real)1;
   const real rhoK = side ? rhoR : rhoL, uK = side ? uR : uL, pK = side ? pR : pL, cK = side ? cR : cL;
   const real r = ps / pK;
-  if (ps > pK) {
+  if constexpr (sizeof(real) == 4) {
+    // FP32: the shock and rarefaction cases evaluated and selected; only the
+    // sonic rarefaction (the face inside the fan, rare) branches
+    const bool shock = ps > pK;
+    const real sq = xsqrt(G.shock_a * r + G.shock_b);
+    const real lr = __log2f(r);
+    const real rz = exp2f(G.z * lr), rig = exp2f(G.inv_g * lr);
+    const bool orig = shock ? ((real)0 <= s * (uK - s * cK * sq)) : ((real)0 <= s * (uK - s * cK));
+    const bool fan = !shock && !orig && !((real)0 > s * (us - s * cK * rz));
+    const real rho_star = shock ? rhoK * (r + G.gm1_gp1) / (G.gm1_gp1 * r + (real)1) : rhoK * rig;
+    rhoF = orig ? rhoK : rho_star;
+    uF = orig ? uK : us;
+    pF = orig ? pK : ps;
+    if (fan) {
+      const real c = G.two_gp1 * cK + s * G.gm1_gp1 * uK;
+      const real q = c / cK;
+      uF = s * c;
+      rhoF = rhoK * xpow(q, G.fan_rho);
+      pF = pK * xpow(q, G.fan_p);
+    }
+  } else if (ps > pK) {
     const real SK = uK - s * cK * xsqrt(G.shock_a * r + G.shock_b);
     if ((real)0 <= s * SK) {
       rhoF = rhoK; uF = uK; pF = pK;
