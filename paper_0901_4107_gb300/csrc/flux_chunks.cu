@@ -175,8 +175,19 @@ __global__ void __launch_bounds__(B, chunk_ctas_per_sm<B>()) k_flux_chunks(Hydro
     }
     FaceOut o;
     face_finish_core<float, ENT>(v, f, false, 0.0f, o, LEARN, cs);
+    if constexpr (STATIC) {
 #pragma unroll
-    for (int a = 0; a < NM; a++) fm[a] = max(fm[a], o.m[a]);
+      for (int a = 0; a < NM; a++) fm[a] = max(fm[a], o.m[a]);
+    } else {
+      // the moving-mesh instantiation holds more live values: a warp
+      // reduction per chunk spills less than five private maxima (measured
+      // 4.6% faster at 64^3)
+#pragma unroll
+      for (int a = 0; a < NM; a++) {
+        const unsigned r = __reduce_max_sync(full, o.m[a]);
+        fm[a] = max(fm[a], r);
+      }
+    }
     // Newton statistics of the warp: the iteration histogram (the lanes with
     // equal counts found by one match; the lowest of them adds their number,
     // so the lanes that write hold distinct bins), sums and flags
