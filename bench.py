@@ -141,12 +141,38 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++ source without comments, trailing blanks and blank lines: a
+    change to comments alone leaves the kernel, and so the hash, unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    lines = (l.rstrip() for l in "".join(out).split("\n"))
+    return "\n".join(l for l in lines if l)
+
+
 def source_hash(kernel):
+    """Hash of the code (comments excluded) of the sources a kernel is built
+    from: the committed ncu counters count only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0901_4107_gb300", "csrc")
     for fn in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(d, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
+        with open(os.path.join(d, fn), encoding="utf-8") as f:
+            h.update(fn.encode() + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

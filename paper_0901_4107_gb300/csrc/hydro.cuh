@@ -200,8 +200,6 @@ __device__ __forceinline__ void grad_cell(const HydroView<real>& v, int i, int i
       Wj = v.cw[2 * (size_t)j];
       Pj = v.cw[2 * (size_t)j + 1].x;
     }
-    // A s n / 2 = a_r (f - s_i + (s_i - r_i)) - A c / |d|, with a_r = A / |d|
-    // (explicitly rounded: the persistent step kernel must round alike)
     real phi_j[NV];
     phi_j[0] = Wj.x; phi_j[1] = Wj.y; phi_j[2] = Wj.z; phi_j[3] = Wj.w; phi_j[4] = Pj;
     if constexpr (ENT) phi_j[5] = v.Aw[j];
