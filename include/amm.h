@@ -187,13 +187,15 @@ int amm_set_mesh_velocity(amm_ctx* ctx, const double* w);
 int amm_gradients(amm_ctx* ctx);
 
 /* Sec. 7.1, eq. (EqnTiStep): dt_out[b] = cfl * min_i R_i / (c_i + |v_i - w_i|)
- * over the cells of box b; host array of n_boxes.  Runs amm_gradients first if
- * the gradients are stale.  Synchronises. */
+ * over the cells of box b; host array of n_boxes.  One pass over the current
+ * state's cells (with the mesh-regularity correction it also sets the
+ * corrected mesh velocities that amm_drift takes).  Synchronises. */
 int amm_timestep(amm_ctx* ctx, double cfl, double* dt_out);
 
-/* Sec. 3, steps 6-7: face velocities, fluxes, conservative update with time
- * step dt (every box), then the primitives of the new state and the
- * conservation sums.  Runs amm_gradients first if the gradients are stale. */
+/* Sec. 3, steps 3-7: gradients and limiter of the current state (on a static
+ * mesh also each cell's state predicted over dt/2, which this dt sets), face
+ * velocities, fluxes, conservative update with time step dt (every box), then
+ * the primitives of the new state and the conservation sums. */
 int amm_step(amm_ctx* ctx, double dt);
 /* Same with one time step per box, host [n_boxes]. */
 int amm_step_boxes(amm_ctx* ctx, const double* dt);
