@@ -81,3 +81,19 @@ def test_reference_arm_other_workloads(workload):
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["config"]["workload"].startswith(("point explosion", "the moving-mesh cycle"))
     assert d["cpu_baseline"]["kind"] == "oracle" and str(d["config"]["sample_lattice"]) in d["cpu_baseline"]["sample"]
+
+
+def test_counter_hash_ignores_comments_and_sees_code():
+    """The committed ncu counters are keyed by a hash of the kernels' code
+    without comments: a comment edit keeps them, a code edit retires them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = 'int a = 1; // one\n/* two\n   lines */\nconst char* s = "// kept";\n\nfloat b = a * 2.0f;\n'
+    code = bench._code_only(src)
+    assert code == 'int a = 1;\nconst char* s = "// kept";\nfloat b = a * 2.0f;'
+    assert bench._code_only(src.replace("// one", "// changed comment")) == code
+    assert bench._code_only(src.replace("/* two", "/* other")) == code
+    assert bench._code_only(src.replace("2.0f", "3.0f")) != code
+    assert bench._code_only(src.replace('"// kept"', '"// other"')) != code
+    for k in bench.KERNEL_SOURCES:
+        assert len(bench.source_hash(k)) == 16
