@@ -97,3 +97,25 @@ def test_counter_hash_ignores_comments_and_sees_code():
     assert bench._code_only(src.replace('"// kept"', '"// other"')) != code
     for k in bench.KERNEL_SOURCES:
         assert len(bench.source_hash(k)) == 16
+
+
+def test_algorithmic_bytes_per_unit():
+    """The byte model of the roofline: per face and per cell, as the kernel
+    table states it (rb = 4 in the FP32 forms, 8 in the FP64 form)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for rb in (4, 8):
+        # gradients: n (16 rb + 4) + n 5 rb + 2F 8 rb, and on a static mesh
+        # n 14 rb more (the Courant pass's reads, the predicted record)
+        assert bench.algorithmic_bytes("gradients", 1, 0, rb) == 16 * rb + 4 + 5 * rb
+        assert bench.algorithmic_bytes("gradients", 0, 1, rb) == 2 * 8 * rb
+        assert bench.algorithmic_bytes("gradients", 1, 0, rb, True) - \
+            bench.algorithmic_bytes("gradients", 1, 0, rb) == 14 * rb
+        # flux: F (8 + 13 rb) + n 25 rb
+        assert bench.algorithmic_bytes("flux", 0, 1, rb) == 8 + 13 * rb
+        assert bench.algorithmic_bytes("flux", 1, 0, rb) == 25 * rb
+        # update: 2F 8 + F 5 rb + n (92 + 5 rb)
+        assert bench.algorithmic_bytes("update", 0, 1, rb) == 16 + 5 * rb
+        assert bench.algorithmic_bytes("update", 1, 0, rb) == 92 + 5 * rb
+    # the 64^3 Lagrangian gradient stage: 165 MB
+    assert abs(bench.algorithmic_bytes("gradients", 262144, 2054914, 4) / 1e6 - 165.1) < 0.1
