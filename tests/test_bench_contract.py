@@ -105,9 +105,12 @@ def test_algorithmic_bytes_per_unit():
     sys.path.insert(0, ROOT)
     import bench
     for rb in (4, 8):
-        # gradients: n (16 rb + 4) + n 5 rb + 2F 8 rb, and on a static mesh
-        # n 14 rb more (the Courant pass's reads, the predicted record)
-        assert bench.algorithmic_bytes("gradients", 1, 0, rb) == 16 * rb + 4 + 5 * rb
+        # gradients: n (26 rb + 4) + n 5 rb + 2F 8 rb (per cell W, P, 1/V,
+        # s - r, R, the CSR offset and the 16 gradient reals written; the
+        # gathered neighbours' W, P once per cell; the 8-real incidence
+        # record), and on a static mesh n 14 rb more (the Courant pass's
+        # reads, the predicted record)
+        assert bench.algorithmic_bytes("gradients", 1, 0, rb) == 26 * rb + 4 + 5 * rb
         assert bench.algorithmic_bytes("gradients", 0, 1, rb) == 2 * 8 * rb
         assert bench.algorithmic_bytes("gradients", 1, 0, rb, True) - \
             bench.algorithmic_bytes("gradients", 1, 0, rb) == 14 * rb
